@@ -1,0 +1,506 @@
+/*
+ * sre_oracle.c -- plain, slow, FP64 reference for the FWHT Pauli-spectrum
+ * method of Xiao & Ryu, "Exponentially Accelerated Sampling of Pauli Strings
+ * for Nonstabilizerness" (arXiv 2601.00761).
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the library's product path may call,
+ * link or load this file: only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference leg of bench.py use it. It shares no code,
+ * header, table or constant with the CUDA path.
+ *
+ * Every function follows a definition or an algorithm of the paper, in the
+ * paper's order, with no blocking, fusion or reordering:
+ *   - c_P = <psi|P|psi> for P_{x,z} = i^{x.z} X^x Z^z       (Eq. Pxz-def / Pxz-corr)
+ *   - one Walsh-Hadamard transform per X-mask x              (Eq. Z-FWHT, Algorithm 1)
+ *   - M_alpha and the stabilizer nullity                      (Eq. SRE-def, nullity def.)
+ *   - the MC estimator with x = 0 forced                      (SM Sec. I)
+ *   - the x-marginal p(x) and the sampling of (x, z) ~ c^2/d  (SM Sec. III target pi(P))
+ *   - H, S, S^dag, CNOT, T, T^dag gates on a state vector     (Clifford preconditioning, T doping)
+ *   - Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+ *
+ * Readings of the paper that this file fixes (the paper is silent or
+ * inconsistent on them):
+ *   - conjugation order and phase: c_{x,z} = s i^{popcount(x&z)}
+ *     sum_b conj(psi(b^x)) (-1)^{popcount(z&b)} psi(b), s = 1/sum|psi|^2,
+ *     so P is Hermitian and c is real; qubit j is bit j of b.
+ *   - logs are base 2; M_1 is the Shannon limit of Eq. SRE-def, 0 log 0 = 0.
+ *   - the nullity counts P with | |c_P| - 1 | < eps.
+ *   - the estimator under pi(P) = c_P^2/d (SM Sec. III) is
+ *     M_alpha = log2(E_pi[c^{2 alpha - 2}]) / (1 - alpha) with no "- N"
+ *     (the SM's extra "- N" contradicts Eq. SRE-def by d^{alpha-1});
+ *     M_1 = -E_pi[log2 c^2].
+ *   - inverse-CDF draws: the smallest index i with C(i) > u * C(last), C the
+ *     inclusive running sum in natural index order; u = (w >> 11) * 2^-53.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+/* Test hook: a nonzero value plants one known mistake (see or_set_mutation). */
+static int g_mutation = 0;
+void or_set_mutation(int m) { g_mutation = m; }
+
+static int popc(uint64_t v) { return __builtin_popcountll(v); }
+
+static cplx amp(const float *psi, uint64_t b) {
+    return (double)psi[2 * b] + I * (double)psi[2 * b + 1];
+}
+
+/* i^k */
+static cplx ipow(int k) {
+    switch (k & 3) {
+    case 0: return 1.0;
+    case 1: return I;
+    case 2: return -1.0;
+    default: return -I;
+    }
+}
+
+/* Neumaier compensated summation. */
+typedef struct { double s, c; } ksum;
+static void kadd(ksum *k, double v) {
+    double t = k->s + v;
+    if (fabs(k->s) >= fabs(v)) k->c += (k->s - t) + v;
+    else k->c += (v - t) + k->s;
+    k->s = t;
+}
+static double kval(const ksum *k) { return k->s + k->c; }
+
+/* ------------------------------------------------------------------ Philox */
+/* Philox4x64-10: ten rounds of the 4x64 S-box with Weyl key schedule. */
+static void mulhilo64(uint64_t a, uint64_t b, uint64_t *hi, uint64_t *lo) {
+    unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
+    *hi = (uint64_t)(p >> 64);
+    *lo = (uint64_t)p;
+}
+
+void or_philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2], uint64_t out[4]) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+    uint64_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint64_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        uint64_t hi0, lo0, hi1, lo1;
+        mulhilo64(M0, c0, &hi0, &lo0);
+        mulhilo64(M1, c2, &hi1, &lo1);
+        uint64_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+double or_u01(uint64_t w) { return (double)(w >> 11) * 0x1.0p-53; }
+
+/* The draw streams of sre_mc: word 0 of Philox(ctr = (ctr0 + i, lane, 0, 0),
+ * key = (seed, 0)). lane 0 draws x for family i, lane 1 + k draws the k-th z. */
+double or_mc_uniform_draw(uint64_t seed, uint64_t ctr0, uint64_t i, uint64_t lane) {
+    uint64_t ctr[4] = {ctr0 + i, lane, 0, 0}, key[2] = {seed, 0}, out[4];
+    or_philox4x64_10(ctr, key, out);
+    return or_u01(out[0]);
+}
+
+/* ----------------------------------------------------------- basic pieces */
+/* sum_b |psi(b)|^2 (normalisation, "Tr rho^2 = 1" in the SRE section). */
+double or_norm2(const float *psi, int N) {
+    ksum k = {0, 0};
+    uint64_t d = 1ULL << N;
+    for (uint64_t b = 0; b < d; ++b) {
+        cplx a = amp(psi, b);
+        kadd(&k, creal(a) * creal(a) + cimag(a) * cimag(a));
+    }
+    return kval(&k);
+}
+
+/* Brute force, Eq. Pxz-corr: one correlator in O(d). Returns the real part;
+ * *im receives the imaginary residue (zero for Hermitian P up to rounding). */
+double or_pauli_expectation(const float *psi, int N, uint64_t x, uint64_t z, double *im) {
+    uint64_t d = 1ULL << N;
+    double s = 1.0 / or_norm2(psi, N);
+    ksum kr = {0, 0}, ki = {0, 0};
+    for (uint64_t b = 0; b < d; ++b) {
+        cplx t = conj(amp(psi, b ^ x)) * amp(psi, b);
+        if (g_mutation == 2) t = conj(amp(psi, b)) * amp(psi, b ^ x);
+        if (popc(z & b) & 1) t = -t;
+        kadd(&kr, creal(t));
+        kadd(&ki, cimag(t));
+    }
+    int k = popc(x & z);
+    if (g_mutation == 1) k = 0;
+    cplx c = s * ipow(k) * (kval(&kr) + I * kval(&ki));
+    if (im) *im = cimag(c);
+    return creal(c);
+}
+
+/* In-place Walsh-Hadamard transform by pairwise sum/difference over n bits:
+ * one application of (sqrt2 H) per bit, as in Eq. Z-FWHT and its iteration. */
+static void fwht_complex(cplx *a, int n) {
+    uint64_t len = 1ULL << n;
+    for (uint64_t h = 1; h < len; h <<= 1)
+        for (uint64_t i = 0; i < len; i += 2 * h)
+            for (uint64_t j = i; j < i + h; ++j) {
+                cplx u = a[j], v = a[j + h];
+                a[j] = u + v;
+                a[j + h] = u - v;
+            }
+}
+
+static void fwht_real(double *a, int n) {
+    uint64_t len = 1ULL << n;
+    for (uint64_t h = 1; h < len; h <<= 1)
+        for (uint64_t i = 0; i < len; i += 2 * h)
+            for (uint64_t j = i; j < i + h; ++j) {
+                double u = a[j], v = a[j + h];
+                a[j] = u + v;
+                a[j + h] = u - v;
+            }
+}
+
+void or_fwht_real(double *a, int n) { fwht_real(a, n); }
+
+/* One family (Algorithm 1, body of the loop over x): f_x(b) for every b,
+ * one FWHT over b, then the phase i^{popcount(x&z)} and the normalisation.
+ * c[z] receives the real c_{x,z}; *imag_max the largest |Im| residue.
+ * work: caller buffer of d complex doubles (or NULL to allocate). */
+int or_family_spectrum(const float *psi, int N, uint64_t x, double s,
+                       double *c, double *imag_max, cplx *work) {
+    uint64_t d = 1ULL << N;
+    cplx *f = work ? work : (cplx *)malloc(d * sizeof(cplx));
+    if (!f) return -1;
+    for (uint64_t b = 0; b < d; ++b) {
+        f[b] = conj(amp(psi, b ^ x)) * amp(psi, b);
+        if (g_mutation == 2) f[b] = conj(amp(psi, b)) * amp(psi, b ^ x);
+    }
+    fwht_complex(f, N);
+    double im = 0.0;
+    for (uint64_t z = 0; z < d; ++z) {
+        int k = popc(x & z);
+        if (g_mutation == 1) k = 0;
+        cplx v = s * ipow(k) * f[z];
+        if (g_mutation == 3) v = s * ipow(k) * f[z ^ 1];   /* a wrong output index */
+        c[z] = creal(v);
+        if (fabs(cimag(v)) > im) im = fabs(cimag(v));
+    }
+    if (imag_max) *imag_max = im;
+    if (!work) free(f);
+    return 0;
+}
+
+/* Per-family partial sums of one spectrum: [sum c^2, sum c^4, sum c^6,
+ * sum c^2 log2 c^2] and the count of | |c| - 1 | < eps. */
+static void family_moments(const double *c, uint64_t d, double eps, double out[4], long long *cnt) {
+    ksum k2 = {0, 0}, k4 = {0, 0}, k6 = {0, 0}, kl = {0, 0};
+    long long n = 0;
+    for (uint64_t z = 0; z < d; ++z) {
+        double c2 = c[z] * c[z];
+        kadd(&k2, c2);
+        kadd(&k4, c2 * c2);
+        kadd(&k6, c2 * c2 * c2);
+        if (c2 > 0.0) kadd(&kl, c2 * log2(c2));
+        if (fabs(fabs(c[z]) - 1.0) < eps) ++n;
+    }
+    out[0] = kval(&k2); out[1] = kval(&k4); out[2] = kval(&k6); out[3] = kval(&kl);
+    *cnt = n;
+}
+
+/* From the totals T = [sum c^2, sum c^4, sum c^6, sum c^2 log2 c^2] over all
+ * 4^N strings: Eq. SRE-def for alpha = 2, 3 and its Shannon limit for
+ * alpha = 1.  M[0..2] = M_1, M_2, M_3;  S[0] = Shannon entropy H of pi in
+ * bits, S[1] = sum c^4/d^2, S[2] = sum c^6/d^3. */
+static void finalize_moments(const double T[4], int N, double M[3], double S[3]) {
+    double d = ldexp(1.0, N);
+    double H = N * (T[0] / d) - T[3] / d;      /* -sum (c^2/d) log2(c^2/d) */
+    S[0] = H;
+    S[1] = T[1] / (d * d);
+    S[2] = T[2] / (d * d * d);
+    M[0] = H - N;
+    M[1] = -log2(S[1]) - N;                    /* 1/(1-2) log2(S_2) - N */
+    M[2] = -0.5 * log2(S[2]) - N;              /* 1/(1-3) log2(S_3) - N */
+    if (g_mutation == 4) M[1] = -log2(S[1]);   /* dropped "- N" */
+}
+
+/* Algorithm 1: exact sweep over all x.
+ * out: M[3], S[3]; stab_count = #{P : ||c|-1| < eps}; nullity = N - log2(count)
+ * (-1 if the count is not a power of two). fam (optional, d x 4) receives the
+ * per-family partial sums of family_moments. Returns 0, or -1 on allocation
+ * failure. */
+int or_sre_exact(const float *psi, int N, double eps, double *M, double *S,
+                 long long *stab_count, int *nullity, double *fam) {
+    uint64_t d = 1ULL << N;
+    double s = 1.0 / or_norm2(psi, N);
+    double *c = (double *)malloc(d * sizeof(double));
+    cplx *w = (cplx *)malloc(d * sizeof(cplx));
+    if (!c || !w) { free(c); free(w); return -1; }
+    ksum tot[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    long long count = 0;
+    for (uint64_t x = 0; x < d; ++x) {
+        or_family_spectrum(psi, N, x, s, c, NULL, w);
+        double m[4];
+        long long cnt;
+        family_moments(c, d, eps, m, &cnt);
+        for (int a = 0; a < 4; ++a) kadd(&tot[a], m[a]);
+        count += cnt;
+        if (fam) memcpy(fam + 4 * x, m, sizeof m);
+    }
+    double T[4] = {kval(&tot[0]), kval(&tot[1]), kval(&tot[2]), kval(&tot[3])};
+    finalize_moments(T, N, M, S);
+    *stab_count = count;
+    *nullity = -1;
+    if (count > 0 && (count & (count - 1)) == 0) *nullity = N - (63 - __builtin_clzll((uint64_t)count));
+    free(c); free(w);
+    return 0;
+}
+
+/* Same sums by brute force over all (x, z): O(8^N), small N only. */
+int or_sre_bruteforce(const float *psi, int N, double eps, double *M, double *S,
+                      long long *stab_count) {
+    uint64_t d = 1ULL << N;
+    ksum tot[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    long long count = 0;
+    for (uint64_t x = 0; x < d; ++x)
+        for (uint64_t z = 0; z < d; ++z) {
+            double c = or_pauli_expectation(psi, N, x, z, NULL);
+            double c2 = c * c;
+            kadd(&tot[0], c2); kadd(&tot[1], c2 * c2); kadd(&tot[2], c2 * c2 * c2);
+            if (c2 > 0.0) kadd(&tot[3], c2 * log2(c2));
+            if (fabs(fabs(c) - 1.0) < eps) ++count;
+        }
+    double T[4] = {kval(&tot[0]), kval(&tot[1]), kval(&tot[2]), kval(&tot[3])};
+    finalize_moments(T, N, M, S);
+    *stab_count = count;
+    return 0;
+}
+
+/* ------------------------------------------------------------ x-marginal */
+/* p(x) = sum_z c_{x,z}^2 / d, the marginal of pi(P) = c_P^2/d over x.
+ * Direct route: by Parseval on f_x, p(x) = s^2 sum_b |psi(b^x)|^2 |psi(b)|^2. */
+void or_x_marginal_direct(const float *psi, int N, double *p) {
+    uint64_t d = 1ULL << N;
+    double s = 1.0 / or_norm2(psi, N);
+    for (uint64_t x = 0; x < d; ++x) {
+        ksum k = {0, 0};
+        for (uint64_t b = 0; b < d; ++b) {
+            cplx u = amp(psi, b), v = amp(psi, b ^ x);
+            kadd(&k, (creal(u) * creal(u) + cimag(u) * cimag(u)) *
+                         (creal(v) * creal(v) + cimag(v) * cimag(v)));
+        }
+        p[x] = s * s * kval(&k);
+    }
+}
+
+/* WHT route: q = s|psi|^2, Q = WHT(q) (the x = 0 family, Eq. Z-FWHT), and the
+ * XOR autocorrelation q*q = WHT(Q^2)/d. */
+int or_x_marginal_wht(const float *psi, int N, double *p) {
+    uint64_t d = 1ULL << N;
+    double s = 1.0 / or_norm2(psi, N);
+    for (uint64_t b = 0; b < d; ++b) {
+        cplx a = amp(psi, b);
+        p[b] = s * (creal(a) * creal(a) + cimag(a) * cimag(a));
+    }
+    fwht_real(p, N);
+    for (uint64_t z = 0; z < d; ++z) p[z] = p[z] * p[z];
+    fwht_real(p, N);
+    for (uint64_t x = 0; x < d; ++x) p[x] /= (double)d;
+    return 0;
+}
+
+/* Inverse-CDF draw: the smallest i with C(i) > u * C(n-1), C the inclusive
+ * running sum of w in index order. */
+uint64_t or_inverse_cdf(const double *w, uint64_t n, double u) {
+    double total = 0.0;
+    for (uint64_t i = 0; i < n; ++i) total += w[i];
+    double t = u * total;
+    double run = 0.0;
+    for (uint64_t i = 0; i < n; ++i) {
+        run += w[i];
+        if (run > t) return i;
+    }
+    for (uint64_t i = n; i-- > 0;)
+        if (w[i] > 0.0) return i;
+    return 0;
+}
+
+/* ------------------------------------------------------------------- MC */
+/* SM Sec. I estimator: x = 0 always, n_x - 1 further x uniform on
+ * {1, ..., d-1}; S_hat = m_0 + (d-1)/(n_x-1) sum m_x, M = log2(S_hat)/(1-a) - N.
+ * For alpha = 1 the same estimator is applied to the per-family Shannon parts
+ * h_x = -sum_z (c^2/d) log2(c^2/d).  err[a] is Eq. stdM with the Std and mean
+ * estimated from the drawn families. xs (optional) receives the x's. */
+int or_mc_uniform(const float *psi, int N, long long n_x, uint64_t seed, uint64_t ctr0,
+                  double *M, double *err, uint64_t *xs) {
+    if (n_x < 2) return -1;
+    uint64_t d = 1ULL << N;
+    double dd = (double)d;
+    double s = 1.0 / or_norm2(psi, N);
+    double *c = (double *)malloc(d * sizeof(double));
+    cplx *w = (cplx *)malloc(d * sizeof(cplx));
+    if (!c || !w) { free(c); free(w); return -1; }
+    /* per-alpha family values: h_x (alpha=1), m_{2;x}, m_{3;x} */
+    double m0[3];
+    ksum sum[3] = {{0, 0}, {0, 0}, {0, 0}}, sum2[3] = {{0, 0}, {0, 0}, {0, 0}};
+    for (long long i = 0; i < n_x; ++i) {
+        uint64_t x = 0;
+        if (i > 0) {
+            double u = or_mc_uniform_draw(seed, ctr0, (uint64_t)i, 0);
+            x = 1 + (uint64_t)(u * (double)(d - 1));
+        }
+        if (xs) xs[i] = x;
+        or_family_spectrum(psi, N, x, s, c, NULL, w);
+        double m[4];
+        long long cnt;
+        family_moments(c, d, 0.0, m, &cnt);
+        double v[3];
+        v[0] = N * (m[0] / dd) - m[3] / dd;
+        v[1] = m[1] / (dd * dd);
+        v[2] = m[2] / (dd * dd * dd);
+        for (int a = 0; a < 3; ++a) {
+            if (i == 0) m0[a] = v[a];
+            else { kadd(&sum[a], v[a]); kadd(&sum2[a], v[a] * v[a]); }
+        }
+    }
+    double nm = (double)(n_x - 1);
+    for (int a = 0; a < 3; ++a) {
+        double mean = kval(&sum[a]) / nm;
+        double Shat = m0[a] + (dd - 1.0) * mean;
+        double var = kval(&sum2[a]) / nm - mean * mean;
+        if (var < 0) var = 0;
+        double Ex = Shat / dd;                  /* E_x over all x */
+        double r = sqrt(var) / Ex;
+        if (a == 0) {
+            M[0] = Shat - N;
+            err[0] = (dd - 1.0) * sqrt(var) / sqrt(nm);   /* sigma of H_hat, bits */
+        } else {
+            double alpha = (double)(a + 1);
+            M[a] = log2(Shat) / (1.0 - alpha) - N;
+            err[a] = r / (fabs(1.0 - alpha) * log(2.0) * sqrt((double)n_x));
+        }
+    }
+    free(c); free(w);
+    return 0;
+}
+
+/* Sampling of P ~ pi(P) = c_P^2/d through its x-marginal: x ~ p(x) by the
+ * inverse CDF of p in natural x order, then z ~ c_{x,z}^2/(d p(x)) by the
+ * inverse CDF of c_{x,.}^2 in natural z order.  The estimators:
+ *   z-sample:  S_a = mean of c^{2a-2} over all drawn (x, z); M_a = log2 S_a/(1-a),
+ *              M_1 = -mean log2 c^2;  err from the spread of the per-x means.
+ *   per-family (Rao-Blackwell): the same, with the mean over z|x replaced by
+ *              its exact value sum_z c^{2a}/sum_z c^2.
+ * M, err, M_rb, err_rb: [3]. xs: [n_x]; zs: [n_x * z_per_x]; c_s: the drawn
+ * c values [n_x * z_per_x]. Any of xs, zs, c_s may be NULL. */
+int or_mc_marginal(const float *psi, int N, long long n_x, int z_per_x, uint64_t seed,
+                   uint64_t ctr0, double *M, double *err, double *M_rb, double *err_rb,
+                   uint64_t *xs, uint64_t *zs, double *c_s) {
+    if (n_x < 2 || z_per_x < 1) return -1;
+    uint64_t d = 1ULL << N;
+    double s = 1.0 / or_norm2(psi, N);
+    double *p = (double *)malloc(d * sizeof(double));
+    double *c = (double *)malloc(d * sizeof(double));
+    double *w2 = (double *)malloc(d * sizeof(double));
+    cplx *w = (cplx *)malloc(d * sizeof(cplx));
+    if (!p || !c || !w || !w2) { free(p); free(c); free(w); free(w2); return -1; }
+    or_x_marginal_wht(psi, N, p);
+    ksum zs_sum[3] = {{0, 0}, {0, 0}, {0, 0}}, zs_sq[3] = {{0, 0}, {0, 0}, {0, 0}};
+    ksum rb_sum[3] = {{0, 0}, {0, 0}, {0, 0}}, rb_sq[3] = {{0, 0}, {0, 0}, {0, 0}};
+    for (long long i = 0; i < n_x; ++i) {
+        double ux = or_mc_uniform_draw(seed, ctr0, (uint64_t)i, 0);
+        uint64_t x = or_inverse_cdf(p, d, ux);
+        if (xs) xs[i] = x;
+        or_family_spectrum(psi, N, x, s, c, NULL, w);
+        for (uint64_t z = 0; z < d; ++z) w2[z] = c[z] * c[z];
+        double fam[3] = {0, 0, 0};
+        for (int k = 0; k < z_per_x; ++k) {
+            double uz = or_mc_uniform_draw(seed, ctr0, (uint64_t)i, 1 + (uint64_t)k);
+            uint64_t z = or_inverse_cdf(w2, d, uz);
+            double c2 = w2[z];
+            if (zs) zs[(uint64_t)i * z_per_x + k] = z;
+            if (c_s) c_s[(uint64_t)i * z_per_x + k] = c[z];
+            fam[0] += -log2(c2);
+            fam[1] += c2;
+            fam[2] += c2 * c2;
+        }
+        double m[4];
+        long long cnt;
+        family_moments(c, d, 0.0, m, &cnt);
+        double rb[3] = {-m[3] / m[0], m[1] / m[0], m[2] / m[0]};
+        for (int a = 0; a < 3; ++a) {
+            double y = fam[a] / z_per_x;
+            kadd(&zs_sum[a], y); kadd(&zs_sq[a], y * y);
+            kadd(&rb_sum[a], rb[a]); kadd(&rb_sq[a], rb[a] * rb[a]);
+        }
+    }
+    double n = (double)n_x;
+    for (int a = 0; a < 3; ++a) {
+        for (int which = 0; which < 2; ++which) {
+            ksum *su = which ? &rb_sum[a] : &zs_sum[a];
+            ksum *sq = which ? &rb_sq[a] : &zs_sq[a];
+            double mean = kval(su) / n;
+            double var = kval(sq) / n - mean * mean;
+            if (var < 0) var = 0;
+            double se = sqrt(var / n);
+            double Mv, ev;
+            if (a == 0) { Mv = mean; ev = se; }
+            else {
+                double alpha = (double)(a + 1);
+                Mv = log2(mean) / (1.0 - alpha);
+                ev = se / (mean * fabs(1.0 - alpha) * log(2.0));
+            }
+            if (which) { M_rb[a] = Mv; err_rb[a] = ev; }
+            else { M[a] = Mv; err[a] = ev; }
+        }
+    }
+    free(p); free(c); free(w); free(w2);
+    return 0;
+}
+
+/* ----------------------------------------------------------------- gates */
+/* Gate opcodes of the gate-list rows (op, q0, q1). */
+enum { OR_H = 0, OR_S = 1, OR_SDG = 2, OR_CNOT = 3, OR_T = 4, OR_TDG = 5 };
+
+/* Apply a gate list to a complex128 state (interleaved re, im) in place.
+ * H = (1/sqrt2)[[1,1],[1,-1]], S = diag(1, i), T = diag(1, e^{i pi/4}),
+ * CNOT(q0 -> q1) flips q1 where q0 = 1. Returns -1 on a bad row. */
+int or_apply_gates(double *psi_c128, int N, const uint8_t *gates, long long n_gates) {
+    uint64_t d = 1ULL << N;
+    cplx *a = (cplx *)psi_c128;
+    const double r2 = 1.0 / sqrt(2.0);
+    for (long long g = 0; g < n_gates; ++g) {
+        int op = gates[3 * g], q0 = gates[3 * g + 1], q1 = gates[3 * g + 2];
+        if (q0 >= N || (op == OR_CNOT && (q1 >= N || q1 == q0))) return -1;
+        uint64_t m0 = 1ULL << q0;
+        switch (op) {
+        case OR_H:
+            for (uint64_t b = 0; b < d; ++b)
+                if (!(b & m0)) {
+                    cplx u = a[b], v = a[b | m0];
+                    a[b] = r2 * (u + v);
+                    a[b | m0] = r2 * (u - v);
+                }
+            break;
+        case OR_S: case OR_SDG: case OR_T: case OR_TDG: {
+            cplx ph = op == OR_S ? I : op == OR_SDG ? -I
+                    : op == OR_T ? r2 * (1.0 + I) : r2 * (1.0 - I);   /* e^{+-i pi/4} */
+            for (uint64_t b = 0; b < d; ++b)
+                if (b & m0) a[b] *= ph;
+            break;
+        }
+        case OR_CNOT: {
+            uint64_t m1 = 1ULL << q1;
+            for (uint64_t b = 0; b < d; ++b)
+                if ((b & m0) && !(b & m1)) {
+                    cplx t = a[b];
+                    a[b] = a[b | m1];
+                    a[b | m1] = t;
+                }
+            break;
+        }
+        default:
+            return -1;
+        }
+    }
+    return 0;
+}

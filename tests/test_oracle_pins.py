@@ -1,0 +1,413 @@
+"""Pins of the FP64 oracle against facts other than itself: closed forms the
+paper prints or derives, invariants, special cases that reduce to a library
+routine (numpy's Philox, dense Kronecker matrices), and brute force on tiny
+inputs. Each plausible mistake planted in the oracle (see test_mutations)
+fails at least one of these."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_00761_gb300 import inputs
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "closed_forms.json")))
+
+
+# ------------------------------------------------------------------ Philox
+@pytest.mark.parametrize("key,ctr", [((0, 0), (0, 0, 0, 0)), ((123, 456), (7, 8, 9, 10)),
+                                     ((2**64 - 1, 1), (2**64 - 2, 5, 0, 0)),
+                                     ((0xDEADBEEF, 0), (41, 0, 3, 2**63))])
+def test_philox_matches_numpy(key, ctr):
+    """numpy's Philox (4x64-10) generates block(counter + 1) first."""
+    g = np.random.Philox(key=np.array(key, dtype=np.uint64), counter=np.array(ctr, dtype=np.uint64))
+    ref = g.random_raw(4)
+    c = list(ctr)
+    c[0] = (c[0] + 1) % 2**64
+    if ctr[0] == 2**64 - 1:
+        c[1] += 1
+    assert np.array_equal(oracle.philox4x64_10(c, key), ref)
+
+
+def test_u01_range():
+    assert oracle.u01(0) == 0.0
+    assert oracle.u01(2**64 - 1) == 1.0 - 2.0**-53
+    assert oracle.u01(1 << 63) == 0.5
+
+
+# ------------------------------------------------- single-qubit closed forms
+def _bloch(a0, a1):
+    """<I>, <Z>, <X>, <Y> of a one-qubit state from its amplitudes."""
+    n = abs(a0) ** 2 + abs(a1) ** 2
+    a0, a1 = a0 / np.sqrt(n), a1 / np.sqrt(n)
+    X = 2 * (np.conj(a0) * a1).real
+    Y = 2 * (np.conj(a0) * a1).imag
+    Z = abs(a0) ** 2 - abs(a1) ** 2
+    return {(0, 0): 1.0, (0, 1): Z, (1, 0): X, (1, 1): Y}
+
+
+ONE_QUBIT = {"0": (1, 0), "1": (0, 1), "+": (1 / np.sqrt(2), 1 / np.sqrt(2)),
+             "-": (1 / np.sqrt(2), -1 / np.sqrt(2)), "+i": (1 / np.sqrt(2), 1j / np.sqrt(2)),
+             "T": inputs.T_QUBIT}
+EXPECTED_ONE_QUBIT = {  # (x, z) -> c: I=(0,0), Z=(0,1), X=(1,0), Y=(1,1)
+    "0": {(0, 0): 1, (0, 1): 1, (1, 0): 0, (1, 1): 0},
+    "1": {(0, 0): 1, (0, 1): -1, (1, 0): 0, (1, 1): 0},
+    "+": {(0, 0): 1, (0, 1): 0, (1, 0): 1, (1, 1): 0},
+    "-": {(0, 0): 1, (0, 1): 0, (1, 0): -1, (1, 1): 0},
+    "+i": {(0, 0): 1, (0, 1): 0, (1, 0): 0, (1, 1): 1},
+    "T": {(0, 0): 1, (0, 1): 0, (1, 0): 1 / np.sqrt(2), (1, 1): 1 / np.sqrt(2)},
+}
+
+
+@pytest.mark.parametrize("name", list(ONE_QUBIT))
+def test_single_qubit_expectations(name):
+    psi = np.array(ONE_QUBIT[name], dtype=np.complex64)
+    for (x, z), want in EXPECTED_ONE_QUBIT[name].items():
+        assert abs(oracle.pauli_expectation(psi, x, z) - want) < 1e-7
+        assert abs(oracle.family_spectrum(psi, x)[z] - want) < 1e-7
+
+
+def test_product_state_factorises():
+    """c_{x,z} of a product state is the product of one-qubit expectations."""
+    g = np.random.default_rng(7)
+    N = 5
+    qs = []
+    for _ in range(N):
+        a = g.standard_normal(2) + 1j * g.standard_normal(2)
+        a /= np.linalg.norm(a)
+        qs.append((a[0], a[1]))
+    psi = inputs.product_state(qs)
+    bl = [_bloch(*q) for q in qs]
+    c_bf = oracle.all_expectations_bruteforce(psi)
+    for x in range(1 << N):
+        c_fw = oracle.family_spectrum(psi, x)
+        for z in range(1 << N):
+            want = np.prod([bl[j][((x >> j) & 1, (z >> j) & 1)] for j in range(N)])
+            assert abs(c_bf[x, z] - want) < 2e-6
+            assert abs(c_fw[z] - want) < 2e-6
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6])
+def test_fwht_route_equals_bruteforce(N):
+    psi = inputs.haar_state(N, 11 + N)
+    c_bf = oracle.all_expectations_bruteforce(psi)
+    for x in range(1 << N):
+        c, im = oracle.family_spectrum(psi, x, return_imag=True)
+        assert np.max(np.abs(c - c_bf[x])) < 1e-12
+        assert im < 1e-12
+
+
+def test_bell_state_stabilizers():
+    """(|00> + |11>)/sqrt2 is stabilised by XX, -YY, ZZ and II."""
+    psi = np.zeros(4, dtype=np.complex64)
+    psi[0] = psi[3] = 1 / np.sqrt(2)
+    want = {(0, 0): 1, (0b11, 0): 1, (0, 0b11): 1, (0b11, 0b11): -1}
+    c = oracle.all_expectations_bruteforce(psi)
+    for x in range(4):
+        for z in range(4):
+            assert abs(c[x, z] - want.get((x, z), 0.0)) < 1e-7
+
+
+def test_parseval_identity_and_imag():
+    for N in (3, 6, 8):
+        psi = inputs.unnormalised_gaussian_state(N, N)
+        tot = 0.0
+        for x in range(1 << N):
+            c, im = oracle.family_spectrum(psi, x, return_imag=True)
+            tot += np.sum(c * c)
+            assert im < 1e-12
+            if x == 0:
+                assert abs(c[0] - 1.0) < 1e-12
+        assert abs(tot / (1 << N) - 1.0) < 1e-12   # sum_P c^2/d = 1
+
+
+# ------------------------------------------------------------- SRE pins
+@pytest.mark.parametrize("case", [c for c in GOLDEN["t_product_state"] if c["N"] <= 7])
+def test_t_product_state(case):
+    psi = inputs.t_product_state(case["N"], case["k"])
+    r = oracle.sre_exact(psi)
+    assert abs(r["M"][0] - case["M1"]) < 1e-6
+    assert abs(r["M"][1] - case["M2"]) < 1e-6
+    assert abs(r["M"][2] - case["M3"]) < 1e-6
+    assert r["nullity"] == case["nullity"]
+
+
+@pytest.mark.parametrize("case", GOLDEN["psi_m_family_m2"])
+def test_psi_m_family_moments(case):
+    """SM Eqs. S4-S6 for |T>^{N/2}|0>^{N/2}."""
+    N = case["N"]
+    psi = inputs.t_product_state(N, N // 2)
+    fam = oracle.sre_exact(psi, per_family=True)["family"]
+    d = 1 << N
+    m2 = fam[:, 1] / d**2
+    assert np.allclose(m2, case["m2_x"], rtol=1e-6, atol=1e-15)
+    assert abs(m2.mean() / case["E_x"] - 1) < 1e-6
+    r2 = m2[1:].std() / m2.mean()
+    assert abs(r2 / case["r2"] - 1) < 1e-6
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5])
+def test_exact_equals_bruteforce_sums(N):
+    psi = inputs.haar_state(N, 100 + N)
+    a = oracle.sre_exact(psi)
+    b = oracle.sre_bruteforce(psi)
+    assert np.allclose(a["M"], b["M"], atol=1e-12)
+    assert np.allclose(a["S"], b["S"], rtol=1e-12)
+
+
+@pytest.mark.parametrize("N,seed", [(2, 1), (3, 2), (5, 3), (6, 4), (7, 5)])
+def test_stabilizer_states(N, seed):
+    gates = inputs.random_clifford_gates(N, 12 * N, seed)
+    psi = oracle.circuit_state(N, gates)
+    r = oracle.sre_exact(psi)
+    assert np.max(np.abs(r["M"])) < 1e-6
+    assert r["stab_count"] == 1 << N
+    assert r["nullity"] == 0
+
+
+def test_ghz_state():
+    N = 6
+    psi = np.zeros(1 << N, dtype=np.complex64)
+    psi[0] = psi[-1] = 1 / np.sqrt(2)
+    r = oracle.sre_exact(psi)
+    assert r["nullity"] == 0 and np.max(np.abs(r["M"])) < 1e-6
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_clifford_invariance(seed):
+    N = 6
+    base = inputs.random_clifford_tdoped_gates(N, 30, 5, seed)
+    psi = oracle.circuit_state(N, base)
+    C = inputs.random_clifford_gates(N, 40, 1000 + seed)
+    psi2 = oracle.circuit_state(N, np.concatenate([base, C]))
+    a, b = oracle.sre_exact(psi), oracle.sre_exact(psi2)
+    assert np.allclose(a["M"], b["M"], atol=2e-6)
+    assert a["nullity"] == b["nullity"]
+    assert a["nullity"] <= int(np.sum(base[:, 0] == inputs.GATE_T))
+
+
+def test_renyi_monotone():
+    for seed in range(5):
+        N = 6
+        psi = oracle.circuit_state(N, inputs.random_clifford_tdoped_gates(N, 40, 4, seed))
+        M = oracle.sre_exact(psi)["M"]
+        assert M[0] >= M[1] - 1e-9 >= -1e-6 and M[1] >= M[2] - 1e-9 and M[2] >= -1e-6
+
+
+@pytest.mark.parametrize("N", [4, 6])
+def test_haar_average(N):
+    """E[(1/d) sum_P c^4] = 4/(d+3) over Haar states (SM, long-time limit)."""
+    d = 1 << N
+    vals = []
+    for seed in range(200):
+        S2 = oracle.sre_exact(inputs.haar_state(N, 5000 + seed))["S"][1]   # sum c^4/d^2
+        vals.append(S2 * d)                                                  # (1/d) sum c^4
+    vals = np.array(vals)
+    want = [h for h in GOLDEN["haar"] if h["N"] == N][0]["E_sum_c4_over_d"]
+    se = vals.std() / np.sqrt(len(vals))
+    assert abs(vals.mean() - want) < 4 * se
+
+
+def test_sm_normalisation_reading():
+    """Under pi(P) = c^2/d, E_pi[c^2] = (1/d) sum c^4 = d S_2; the reading
+    M_2 = -log2 E_pi[c^2] (no "- N") gives 0 for a stabilizer state and
+    k log2(4/3) for |T>^k, matching Eq. SRE-def."""
+    N, k = 5, 3
+    for psi, want in [(oracle.circuit_state(N, inputs.random_clifford_gates(N, 40, 9)), 0.0),
+                      (inputs.t_product_state(N, k), k * math.log2(4 / 3))]:
+        S2 = oracle.sre_exact(psi)["S"][1]
+        assert abs(-math.log2(S2 * (1 << N)) - want) < 1e-6
+
+
+# ----------------------------------------------------------------- gates
+def _dense(op, q0, q1, N):
+    I2 = np.eye(2)
+    one = {inputs.GATE_H: np.array([[1, 1], [1, -1]]) / np.sqrt(2),
+           inputs.GATE_S: np.diag([1, 1j]), inputs.GATE_SDG: np.diag([1, -1j]),
+           inputs.GATE_T: np.diag([1, np.exp(1j * np.pi / 4)]),
+           inputs.GATE_TDG: np.diag([1, np.exp(-1j * np.pi / 4)])}
+    if op != inputs.GATE_CNOT:
+        U = np.array([[1.0]])
+        for j in reversed(range(N)):          # qubit N-1 is the most significant factor
+            U = np.kron(U, one[op] if j == q0 else I2)
+        return U
+    d = 1 << N
+    U = np.zeros((d, d))
+    for b in range(d):
+        U[b ^ (1 << q1) if (b >> q0) & 1 else b, b] = 1
+    return U
+
+
+def test_gates_match_dense_matrices():
+    N = 4
+    g = np.random.default_rng(3)
+    rows = []
+    for _ in range(60):
+        op = int(g.integers(0, 6))
+        q0 = int(g.integers(0, N))
+        q1 = int((q0 + 1 + g.integers(0, N - 1)) % N) if op == inputs.GATE_CNOT else 0
+        rows.append((op, q0, q1))
+    gates = np.array(rows, dtype=np.uint8)
+    psi = inputs.haar_state(N, 3).astype(np.complex128)
+    want = psi.copy()
+    for op, q0, q1 in rows:
+        want = _dense(op, q0, q1, N) @ want
+    got = oracle.apply_gates(psi, gates)
+    assert np.max(np.abs(got - want)) < 1e-12
+
+
+def test_bad_gate_rejected():
+    with pytest.raises(ValueError):
+        oracle.apply_gates(np.ones(4, np.complex64), np.array([[inputs.GATE_CNOT, 1, 1]]))
+    with pytest.raises(ValueError):
+        oracle.apply_gates(np.ones(4, np.complex64), np.array([[9, 0, 0]]))
+
+
+# -------------------------------------------------------------- marginal
+@pytest.mark.parametrize("N", [1, 3, 6, 9])
+def test_marginal_routes(N):
+    psi = inputs.unnormalised_gaussian_state(N, 40 + N)
+    p1 = oracle.x_marginal(psi, "direct")
+    p2 = oracle.x_marginal(psi, "wht")
+    assert np.max(np.abs(p1 - p2)) < 1e-14
+    assert abs(p2.sum() - 1.0) < 1e-12
+    if N <= 6:
+        for x in range(1 << N):
+            c = oracle.family_spectrum(psi, x)
+            assert abs(np.sum(c * c) / (1 << N) - p2[x]) < 1e-13
+
+
+def test_fwht_real_is_hadamard_matrix():
+    n = 5
+    H = np.array([[1.0]])
+    for _ in range(n):
+        H = np.block([[H, H], [H, -H]])
+    v = np.random.default_rng(1).standard_normal(1 << n)
+    assert np.allclose(oracle.fwht_real(v), H @ v, atol=1e-12)
+
+
+# -------------------------------------------------------------- sampling
+def test_inverse_cdf_definition():
+    w = [0.0, 1.0, 0.0, 2.0, 1.0]   # C = 0,1,1,3,4; total 4
+    assert oracle.inverse_cdf(w, 0.0) == 1
+    assert oracle.inverse_cdf(w, 0.2499) == 1
+    assert oracle.inverse_cdf(w, 0.25) == 3
+    assert oracle.inverse_cdf(w, 0.7499) == 3
+    assert oracle.inverse_cdf(w, 0.75) == 4
+    assert oracle.inverse_cdf(w, 1.0 - 2**-53) == 4
+    assert oracle.inverse_cdf([0.0, 0.0, 5.0, 0.0], 0.999) == 2
+
+
+def test_mc_marginal_draw_frequencies():
+    N = 3
+    psi = inputs.haar_state(N, 77)
+    p = oracle.x_marginal(psi)
+    r = oracle.mc_marginal(psi, 4000, 1, seed=5)
+    counts = np.bincount(r["xs"].astype(np.int64), minlength=1 << N)
+    chi2 = np.sum((counts - 4000 * p) ** 2 / (4000 * p))
+    assert chi2 < 30   # 7 dof; P(chi2 > 30) ~ 1e-4
+
+
+def test_mc_marginal_pairs_are_inverse_cdf_draws():
+    N = 5
+    psi = oracle.circuit_state(N, inputs.random_clifford_tdoped_gates(N, 30, 3, 4))
+    r = oracle.mc_marginal(psi, 6, 4, seed=9, ctr0=17)
+    p = oracle.x_marginal(psi)
+    for i in range(6):
+        x = int(r["xs"][i])
+        assert x == oracle.inverse_cdf(p, oracle.mc_draw(9, 17, i, 0))
+        c = oracle.family_spectrum(psi, x)
+        for k in range(4):
+            z = int(r["zs"][i, k])
+            assert z == oracle.inverse_cdf(c * c, oracle.mc_draw(9, 17, i, 1 + k))
+            assert abs(r["c"][i, k] - oracle.pauli_expectation(psi, x, z)) < 1e-12
+
+
+def test_mc_marginal_stabilizer_is_exactly_zero():
+    N = 6
+    psi = oracle.circuit_state(N, inputs.random_clifford_gates(N, 60, 3))
+    r = oracle.mc_marginal(psi, 20, 8, seed=1)
+    assert np.max(np.abs(r["M"])) < 1e-6 and np.max(np.abs(r["M_rb"])) < 1e-6
+    assert np.allclose(np.abs(r["c"]), 1.0, atol=1e-6)
+
+
+def test_mc_marginal_unbiased():
+    """E over seeds of mean c^2 = E_pi[c^2] = (1/d) sum c^4."""
+    N = 5
+    psi = oracle.circuit_state(N, inputs.random_clifford_tdoped_gates(N, 40, 4, 8))
+    want = oracle.sre_exact(psi)["S"][1] * (1 << N)
+    est = [2.0 ** (-oracle.mc_marginal(psi, 8, 4, seed=s)["M"][1]) for s in range(300)]
+    est_rb = [2.0 ** (-oracle.mc_marginal(psi, 8, 1, seed=s)["M_rb"][1]) for s in range(300)]
+    for e in (np.array(est), np.array(est_rb)):
+        assert abs(e.mean() - want) < 4 * e.std() / np.sqrt(len(e)) + 1e-12
+
+
+def test_mc_uniform_unbiased():
+    """SM Sec. I: S_hat is unbiased for S = sum_x m_{2;x}."""
+    N = 6
+    psi = oracle.circuit_state(N, inputs.random_clifford_tdoped_gates(N, 40, 3, 2))
+    d = 1 << N
+    S = oracle.sre_exact(psi)["S"][1]
+    est = np.array([2.0 ** (-(oracle.mc_uniform(psi, 12, seed=s)["M"][1] + N)) for s in range(300)])
+    assert abs(est.mean() - S) < 4 * est.std() / np.sqrt(len(est))
+    r = oracle.mc_uniform(psi, 12, seed=3)
+    assert r["xs"][0] == 0 and np.all(r["xs"][1:] >= 1) and np.all(r["xs"][1:] < d)
+
+
+def test_mc_all_families_is_exact_at_large_sample():
+    """With x = 0 forced and every other x drawn uniformly many times the
+    uniform estimator converges to the exact S."""
+    N = 4
+    psi = inputs.haar_state(N, 3)
+    ex = oracle.sre_exact(psi)["M"]
+    mc = oracle.mc_uniform(psi, 20000, seed=1)
+    assert np.all(np.abs(mc["M"] - ex) < 5 * mc["err"] + 1e-9)
+
+
+# ------------------------------------------------------------- mutations
+def _pins_pass():
+    """A compact subset of the pins above; False if any fails."""
+    try:
+        for name in ("T", "+i"):
+            psi = np.array(ONE_QUBIT[name], dtype=np.complex64)
+            for (x, z), want in EXPECTED_ONE_QUBIT[name].items():
+                if abs(oracle.pauli_expectation(psi, x, z) - want) > 1e-7:
+                    return False
+                if abs(oracle.family_spectrum(psi, x)[z] - want) > 1e-7:
+                    return False
+        psi = np.zeros(4, dtype=np.complex64)
+        psi[0] = psi[3] = 1 / np.sqrt(2)
+        c = oracle.family_spectrum(psi, 3)
+        if abs(c[3] + 1) > 1e-7 or abs(c[0] - 1) > 1e-7:
+            return False
+        g = np.random.default_rng(5)
+        a = g.standard_normal(4) + 1j * g.standard_normal(4)
+        psi = inputs.product_state([(a[0], a[1]), (a[2], a[3])])
+        bl = [_bloch(a[0], a[1]), _bloch(a[2], a[3])]
+        for x in range(4):
+            cf = oracle.family_spectrum(psi, x)
+            for z in range(4):
+                want = bl[0][(x & 1, z & 1)] * bl[1][(x >> 1, z >> 1)]
+                if abs(cf[z] - want) > 2e-6 or abs(oracle.pauli_expectation(psi, x, z) - want) > 2e-6:
+                    return False
+        r = oracle.sre_exact(inputs.t_product_state(4, 2))
+        if abs(r["M"][1] - 2 * math.log2(4 / 3)) > 1e-6:
+            return False
+        return True
+    finally:
+        pass
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4])
+def test_mutations(m):
+    """1: phase i^{x.z} dropped; 2: conjugation order swapped; 3: wrong
+    output index; 4: "- N" dropped from M_2. Each must fail a pin."""
+    assert _pins_pass()
+    oracle.set_mutation(m)
+    try:
+        assert not _pins_pass()
+    finally:
+        oracle.set_mutation(0)
+    assert _pins_pass()
