@@ -68,6 +68,8 @@ def lib():
                                             ctypes.POINTER(ctypes.c_longlong)]
             L.or_sre_bruteforce.restype = ctypes.c_int
             L.or_x_marginal_direct.argtypes = [_c_fp, ctypes.c_int, _c_dp]
+            L.or_x_marginal_one.argtypes = [_c_fp, ctypes.c_int, ctypes.c_uint64]
+            L.or_x_marginal_one.restype = ctypes.c_double
             L.or_x_marginal_wht.argtypes = [_c_fp, ctypes.c_int, _c_dp]
             L.or_x_marginal_wht.restype = ctypes.c_int
             L.or_inverse_cdf.argtypes = [_c_dp, ctypes.c_uint64, ctypes.c_double]
@@ -215,6 +217,12 @@ def x_marginal(psi, route: str = "wht") -> np.ndarray:
     else:
         lib().or_x_marginal_wht(_fp(a), N, _dp(p))
     return p
+
+
+def x_marginal_one(psi, x: int) -> float:
+    """p(x) for one x by the direct O(d) sum (Parseval on f_x)."""
+    a = _psi(psi)
+    return lib().or_x_marginal_one(_fp(a), _nq(a), int(x))
 
 
 def inverse_cdf(w, u: float) -> int:

@@ -292,6 +292,19 @@ void or_x_marginal_direct(const float *psi, int N, double *p) {
     }
 }
 
+/* One entry of the direct route, O(d): for sampled checks at large N. */
+double or_x_marginal_one(const float *psi, int N, uint64_t x) {
+    uint64_t d = 1ULL << N;
+    double s = 1.0 / or_norm2(psi, N);
+    ksum k = {0, 0};
+    for (uint64_t b = 0; b < d; ++b) {
+        cplx u = amp(psi, b), v = amp(psi, b ^ x);
+        kadd(&k, (creal(u) * creal(u) + cimag(u) * cimag(u)) *
+                     (creal(v) * creal(v) + cimag(v) * cimag(v)));
+    }
+    return s * s * kval(&k);
+}
+
 /* WHT route: q = s|psi|^2, Q = WHT(q) (the x = 0 family, Eq. Z-FWHT), and the
  * XOR autocorrelation q*q = WHT(Q^2)/d. */
 int or_x_marginal_wht(const float *psi, int N, double *p) {

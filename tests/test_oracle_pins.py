@@ -273,6 +273,8 @@ def test_marginal_routes(N):
     p2 = oracle.x_marginal(psi, "wht")
     assert np.max(np.abs(p1 - p2)) < 1e-14
     assert abs(p2.sum() - 1.0) < 1e-12
+    for x in (0, 1, (1 << N) - 1):
+        assert abs(oracle.x_marginal_one(psi, x) - p1[x]) < 1e-15
     if N <= 6:
         for x in range(1 << N):
             c = oracle.family_spectrum(psi, x)
