@@ -1,0 +1,254 @@
+/*
+ * sre.h -- C ABI of the GB300 (sm_103a) library for the FWHT Pauli-spectrum
+ * method of Xiao & Ryu, "Exponentially Accelerated Sampling of Pauli Strings
+ * for Nonstabilizerness" (arXiv 2601.00761).
+ *
+ * For an N-qubit state psi (d = 2^N amplitudes, complex64, amplitude psi[b]
+ * of basis state |b>, qubit j = bit j of b) the library evaluates the Pauli
+ * expectations
+ *
+ *     c_{x,z} = s * i^{popcount(x&z)} * sum_b conj(psi[b^x]) (-1)^{popcount(z&b)} psi[b],
+ *     s = 1 / sum_b |psi[b]|^2,
+ *
+ * of the Hermitian Pauli strings P_{x,z} = i^{x.z} X^x Z^z (Eqs. Pxz-def and
+ * Pxz-corr), one X-mask family {c_{x,z}}_z per Walsh-Hadamard transform
+ * (Algorithm 1), and reduces them to the stabilizer Renyi entropies
+ * M_1, M_2, M_3 (Eq. SRE-def; M_1 its Shannon limit; base-2 logs) and the
+ * stabilizer nullity (the nullity definition with a tolerance, Algorithm 1).
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns sre_status; 0 (SRE_OK) is success. A call never
+ *    aborts the process. sre_last_error() returns a message for the calling
+ *    thread's last failed call.
+ *  - Pointers named *_dev are CUDA device pointers owned by the caller; the
+ *    library neither frees nor keeps them after the call returns. *_host
+ *    pointers are host memory owned by the caller.
+ *  - psi_c64_dev is d interleaved (re, im) float pairs, 8-byte aligned. psi is
+ *    normalised by the library (s above); its norm must not be zero.
+ *  - stream is a cudaStream_t cast to void* (NULL = the legacy default
+ *    stream). Work is issued on that stream. Calls that return results in a
+ *    host struct synchronise the stream before returning.
+ *  - workspace: device scratch of at least sre_workspace_bytes() bytes, owned
+ *    by the caller, or NULL, in which case the library uses a buffer of its
+ *    own (kept per device until sre_release_workspace()).
+ *  - N is limited to 1..32 (sre_mc and sre_exact: 1..30, see each call).
+ *  - Errors: SRE_EINVAL (bad argument: N out of range, NULL or misaligned
+ *    pointer, bad option), SRE_ENOMEM (allocation failed), SRE_ECUDA (a CUDA
+ *    call failed; message says which), SRE_EZERO (psi has zero norm),
+ *    SRE_ENULLITY (the count of |c| = 1 strings is not a power of two),
+ *    SRE_ETIMEOUT (a bounded device-side wait expired), SRE_ENOTSUP
+ *    (valid request this build does not serve).
+ */
+#ifndef SRE_H
+#define SRE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SRE_API __attribute__((visibility("default")))
+#else
+#define SRE_API
+#endif
+
+typedef int sre_status;
+
+#define SRE_OK 0
+#define SRE_EINVAL 1
+#define SRE_ENOMEM 2
+#define SRE_ECUDA 3
+#define SRE_EZERO 4
+#define SRE_ENULLITY 5
+#define SRE_ETIMEOUT 6
+#define SRE_ENOTSUP 7
+
+/* Arithmetic of the family transforms (sre_opts.precision). */
+#define SRE_FP32_SIMT 0 /* FP32 butterflies on the CUDA cores */
+#define SRE_BF16X2_TC 1 /* H_16 Kronecker factors on the tensor cores, data split hi+lo in BF16 */
+#define SRE_BF16X3_TC 2 /* as above with a three-way BF16 split */
+
+/* Distribution of the sampled X-masks (sre_mc mode). */
+#define SRE_MC_UNIFORM 0  /* x = 0 always plus uniform x != 0: SM Sec. I estimator */
+#define SRE_MC_MARGINAL 1 /* x ~ p(x) = sum_z c_{x,z}^2/d, then z ~ c_{x,z}^2/(d p(x)) */
+
+/* Gate opcodes of sre_gate.op. */
+#define SRE_GATE_H 0    /* (1/sqrt2)[[1,1],[1,-1]] on q0 */
+#define SRE_GATE_S 1    /* diag(1, i) on q0 */
+#define SRE_GATE_SDG 2  /* diag(1, -i) on q0 */
+#define SRE_GATE_CNOT 3 /* control q0, target q1 */
+#define SRE_GATE_T 4    /* diag(1, e^{i pi/4}) on q0 */
+#define SRE_GATE_TDG 5  /* diag(1, e^{-i pi/4}) on q0 */
+
+typedef struct {
+    int precision;      /* SRE_FP32_SIMT (default), SRE_BF16X2_TC, SRE_BF16X3_TC */
+    double eps_null;    /* nullity tolerance on | |c| - 1 |; <= 0 means 1e-6 */
+    int radix_log2;     /* bits of the last (contiguous) transform pass; 0 = planned/tuned */
+    int tile_log2;      /* bits per strided pass; 0 = planned/tuned */
+    int x_batch;        /* X-mask families in flight per launch; 0 = planned/tuned */
+} sre_opts;
+
+typedef struct {
+    double M[3];        /* M_1, M_2, M_3 (bits) */
+    double S[3];        /* exact: H(pi) in bits, sum c^4/d^2, sum c^6/d^3;
+                           MC: the estimates of -E_pi[log2 c^2], E_pi[c^2], E_pi[c^4] */
+    double err_M[3];    /* exact: bound on |dM| from FP32 rounding; MC: standard error */
+    double M_rb[3];     /* MC: per-family (conditional-expectation) estimator; exact: = M */
+    double err_rb[3];   /* its standard error (exact: = err_M) */
+    double parseval;    /* exact: sum_P c_P^2 / d (1 up to rounding, the normalisation
+                           of the SRE section); MC: -1 (not computed) */
+    long long stab_count; /* #{P : | |c_P| - 1 | < eps_null} (exact / nullity calls), else -1 */
+    int nullity;        /* N - log2(stab_count), or -1 when not computed */
+    int n_passes;       /* global transform passes per family in the plan used */
+    long long n_flagged;  /* families re-evaluated in FP64 for the nullity */
+    long long n_families; /* families transformed */
+    long long n_samples;  /* (x, z) pairs drawn (MC marginal), else 0 */
+    long long n_boundary; /* reserved (0) */
+} sre_result;
+
+typedef struct {
+    unsigned char op; /* SRE_GATE_* */
+    unsigned char q0; /* qubit (control for CNOT) */
+    unsigned char q1; /* CNOT target; ignored otherwise */
+} sre_gate;
+
+/* Plan of the family transform for N qubits (host only, no GPU needed). */
+typedef struct {
+    int N;
+    int n_bits;          /* N - 1: bits of the packed complex transform */
+    int n_passes;        /* 1 (whole family in one CTA) or 2..4 global passes */
+    int pass_lo[4];      /* lowest bit of each pass; pass 0 reads psi, the last reduces */
+    int pass_bits[4];    /* bits transformed by each pass */
+    int x_batch;         /* families per launch */
+    int range_log2;      /* log2 of the z-range size used by the two-level z sampler */
+    size_t workspace_exact; /* bytes sre_exact needs */
+} sre_plan;
+
+/* Library version string and the last error of the calling thread. */
+SRE_API const char *sre_version(void);
+SRE_API const char *sre_last_error(void);
+
+/* Fill *opts with the defaults (FP32 SIMT, eps_null 1e-6, planned tiles). */
+SRE_API void sre_default_opts(sre_opts *opts);
+
+/* Plan of the transform passes (host only). opts may be NULL. */
+SRE_API sre_status sre_make_plan(int N, const sre_opts *opts, sre_plan *plan);
+
+/* Device scratch that sre_exact (mode -1) or sre_mc (mode SRE_MC_*) needs
+ * for these sizes; *bytes receives it. Host only. */
+SRE_API sre_status sre_workspace_bytes(int N, int mode, long long n_x, int z_per_x,
+                               const sre_opts *opts, size_t *bytes);
+
+/* Free the library-owned workspace of the current device. */
+SRE_API sre_status sre_release_workspace(void);
+
+/* s^-1 = sum_b |psi[b]|^2 in FP64 (the normalisation of the SRE section,
+ * Tr rho^2 = 1). *norm2_host receives it. */
+SRE_API sre_status sre_norm2(const void *psi_c64_dev, int N, double *norm2_host, void *stream);
+
+/* Exact enumeration of all 4^N strings, Algorithm 1: M_1..M_3 and the
+ * nullity in one sweep over the 2^N X-mask families (each family one
+ * Walsh-Hadamard transform of f_x, Eq. Pxz-corr). Families whose FP32
+ * spectrum has |c| > 1 - 1e-4 are re-evaluated in FP64 before the count
+ * (n_flagged). N in 1..30. out: host. */
+SRE_API sre_status sre_exact(const void *psi_c64_dev, int N, const sre_opts *opts,
+                     void *workspace, size_t workspace_bytes, void *stream,
+                     sre_result *out);
+
+/* Exact M_1..M_3 and nullity of `count` states of possibly different N in
+ * one call (psi_ptrs_host[i] a device pointer, Ns_host[i] in 1..20). The
+ * work of all states is issued as one persistent launch sequence captured in
+ * a CUDA graph. out: host array of `count` results. */
+SRE_API sre_status sre_exact_batched(const void *const *psi_ptrs_host, const int *Ns_host, int count,
+                             const sre_opts *opts, void *workspace, size_t workspace_bytes,
+                             void *stream, sre_result *out);
+
+/* Monte Carlo over X-mask families (N in 2..30).
+ * mode SRE_MC_UNIFORM: the SM Sec. I estimator -- x = 0 always and n_x - 1
+ *   draws of x uniform on {1..d-1}; S_hat = m_0 + (d-1)/(n_x-1) sum m_x;
+ *   err_M from Eq. stdM. z_per_x is ignored.
+ * mode SRE_MC_MARGINAL: x ~ p(x) (inverse CDF of the exact marginal in
+ *   natural x order), then z_per_x draws z ~ c_{x,z}^2/(d p(x)) (inverse CDF
+ *   in natural z order); M_a = log2(mean c^{2a-2})/(1-a), M_1 = -mean log2 c^2.
+ * Random numbers: word 0 of Philox4x64-10 with key (seed, 0) and counter
+ * (counter0 + i, lane, 0, 0); lane 0 gives family i's x, lane 1+k its k-th z;
+ * u = (word >> 11) 2^-53.
+ * xs_dev (n_x uint64), zs_dev (n_x*z_per_x uint64) and c_dev (n_x*z_per_x
+ * float, the sampled c_{x,z}) are optional device outputs (NULL to skip).
+ * out: host. */
+SRE_API sre_status sre_mc(const void *psi_c64_dev, int N, int mode, long long n_x, int z_per_x,
+                  unsigned long long seed, unsigned long long counter0, const sre_opts *opts,
+                  void *workspace, size_t workspace_bytes, void *stream, sre_result *out,
+                  unsigned long long *xs_dev, unsigned long long *zs_dev, float *c_dev);
+
+/* The exact X-mask marginal p(x) = sum_z c_{x,z}^2 / d = (q*q)(x), the XOR
+ * autocorrelation of q = s|psi|^2, computed as WHT(WHT(q)^2)/d in FP64
+ * (WHT(q) is the x = 0 family, Eq. Z-FWHT). p_dev: d doubles. N in 1..30.
+ * workspace: 8*d bytes or NULL. */
+SRE_API sre_status pauli_x_marginal(const void *psi_c64_dev, int N, double *p_dev,
+                            void *workspace, size_t workspace_bytes, void *stream);
+
+/* Stabilizer nullity nu = N - log2 #{P : | |c_P| - 1 | < eps} (the nullity
+ * definition, Algorithm 1); eps <= 0 means 1e-6. N in 1..30. */
+SRE_API sre_status stabilizer_nullity(const void *psi_c64_dev, int N, double eps, int *nullity_host,
+                              long long *stab_count_host, void *stream);
+
+/* Apply a gate list in order, in place, to psi (Clifford preconditioning and
+ * T doping): H, S, S^dag, T, T^dag on q0; CNOT q0 -> q1. gates_host: n_gates
+ * packed 3-byte rows. N in 1..32. Runs of gates are fused into passes over
+ * psi. Returns SRE_EINVAL (and leaves psi untouched) on a bad row. */
+SRE_API sre_status apply_clifford_tdoped_circuit(void *psi_c64_dev, int N, const sre_gate *gates_host,
+                                         long long n_gates, void *stream);
+
+/* One X-mask family (Eq. Pxz-corr for one x): c_dev[z] = c_{x,z} for all z,
+ * d floats, by the same transform kernels as sre_exact (precision from
+ * opts, NULL = FP32). N in 1..30. */
+SRE_API sre_status sre_family_spectrum(const void *psi_c64_dev, int N, unsigned long long x,
+                               const sre_opts *opts, float *c_dev, void *stream);
+
+/* The same family in FP64 arithmetic (the arithmetic of the nullity
+ * recheck): c_dev receives d doubles. N in 1..28. */
+SRE_API sre_status sre_family_spectrum_f64(const void *psi_c64_dev, int N, unsigned long long x,
+                                   double *c_dev, void *stream);
+
+/* Philox4x64-10 blocks from the device generator that sre_mc draws with
+ * (Salmon et al., SC'11): for i < n, ctr_key_dev[6i..6i+3] is the counter
+ * and [6i+4..6i+5] the key; out_dev[4i..4i+3] receives the block. Lets a
+ * caller check the generator against an independent implementation. */
+SRE_API sre_status sre_philox_blocks(const unsigned long long *ctr_key_dev, unsigned long long *out_dev,
+                             int n, void *stream);
+
+/* Number of CUDA kernels this library has launched since it was loaded
+ * (every entry point counts its launches). Host only. */
+SRE_API unsigned long long sre_kernel_launches(void);
+
+/* Pass timing inside sre_mc: enable = 1 clears the counters and starts
+ * recording CUDA events around every full-batch family-transform pass launch
+ * of subsequent sre_mc calls; enable = 0 stops. Either call first copies the
+ * current counters out: ms_sum_host[p] (total ms of pass p's launches),
+ * launches_host[p] (their count) and bytes_host[p] (algorithmic bytes per
+ * launch, as for sre_profile_passes); each array has 4 entries, any may be
+ * NULL. Host only. */
+SRE_API sre_status sre_pass_timing(int enable, double *ms_sum_host, long long *launches_host,
+                                   double *bytes_host);
+
+/* Profiling aid: runs n_x families (x drawn uniformly, seed fixed) through
+ * exactly the launch sequence of the family transform that sre_mc issues
+ * (norm, the planned passes, fused moments epilogue), with CUDA events on
+ * `stream` around every pass launch. ms_host[p] receives the mean duration of
+ * pass p's launches, bytes_host[p] the algorithmic bytes one launch of pass p
+ * moves (first pass: 8 B per psi amplitude read; each boundary between
+ * passes: the packed intermediate, 4 B per Pauli string written and 4 B
+ * read); *n_passes the pass count (<= 4); *fam_per_launch the families one
+ * launch processes. Uses the library workspace. N in 2..30. */
+SRE_API sre_status sre_profile_passes(const void *psi_c64_dev, int N, long long n_x, const sre_opts *opts,
+                                      void *stream, double *ms_host, double *bytes_host, int *n_passes,
+                                      long long *fam_per_launch);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SRE_H */

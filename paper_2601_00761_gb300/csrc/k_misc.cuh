@@ -1,0 +1,47 @@
+// k_misc.cuh -- declarations of the support kernels' launchers.
+#pragma once
+#include "sre_internal.cuh"
+
+namespace sre {
+
+// slots of the device scalar block
+enum { SCAL_NORM2 = 0, SCAL_S = 1, SCAL_N = 8 };
+constexpr int NORM_BLOCKS = 1216;          // 152 SMs x 8
+constexpr unsigned long long SCAN_CHUNK = 4096;
+
+struct DrawInfo {
+    unsigned long long range;   // z-range (size 2^RL) of the draw
+    double t;                   // target within the range, in units of c^2
+};
+
+cudaError_t launch_norm2(const float2 *psi, int N, double *scal, double *partial, cudaStream_t st);
+cudaError_t launch_fam_reduce(const TilePartial *tp, long long n_fam, int tiles, const unsigned long long *xs,
+                              long long fam_base, int N, int M_last, int RL, FamMoments *fm, long long fm_base,
+                              double *W, long long nr, cudaStream_t st);
+cudaError_t launch_exact_totals(const FamMoments *fm, long long n_fam, double *partial, int n_part,
+                                double *out, unsigned long long *flag_list, unsigned long long *n_flag,
+                                cudaStream_t st);
+cudaError_t launch_sum_u64(const unsigned long long *v, long long n, unsigned long long *out, cudaStream_t st);
+cudaError_t launch_scan(const double *p, unsigned long long n, double *cdf, double *bsum, cudaStream_t st);
+cudaError_t launch_draw_x(const double *cdf, int N, long long n_x, int mode, unsigned long long seed,
+                          unsigned long long ctr0, unsigned long long *xs, cudaStream_t st);
+cudaError_t launch_zrange_select(double *W, long long nr, long long n_fam, long long fam_base, int z_per_x,
+                                 unsigned long long seed, unsigned long long ctr0, DrawInfo *draws,
+                                 cudaStream_t st);
+cudaError_t launch_mc_stats(const FamMoments *fm, const float *cz, long long n_x, int z_per_x, int N, int mode,
+                            double *y, double *out, cudaStream_t st);
+cudaError_t launch_philox_test(const unsigned long long *ctr_key, unsigned long long *out, int n, cudaStream_t st);
+
+// z sampler (k_sample.cu): recompute the last-pass tile of each draw's range
+// and pick z by the FP64 inclusive scan of c^2 over the range.
+cudaError_t launch_zsample(int single, int M, const PassArgs &a, const DrawInfo *draws, int z_per_x,
+                           unsigned long long *zs, float *cz, cudaStream_t st);
+
+// gates (k_gates.cu)
+struct GateRow { unsigned char op, q0, q1; };
+cudaError_t launch_gate_blocks(float2 *psi, int N, const GateRow *gates_dev, const int *blocks_host,
+                               int n_blocks, const unsigned char *block_qubits_host, cudaStream_t st);
+constexpr int GATE_BLOCK_Q = 12;   // qubits per fused gate block (2^12 amplitudes in shared memory)
+constexpr int GATE_BLOCK_LOW = 5;  // qubits 0..4 always in the block (256-byte contiguous runs)
+
+} // namespace sre

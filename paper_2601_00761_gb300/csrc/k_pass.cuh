@@ -1,0 +1,305 @@
+// k_pass.cuh -- the transform pass kernel template and its launcher.
+//
+// One kernel template serves every pass of every transform in the library:
+//   prologue  SRC_PSI_FAMILY : h(b') = conj(psi[b^x]) psi[b], b = b' with 0 at bit j
+//             SRC_PSI_Q      : h(g)  = (|psi[g]|^2, |psi[g + d/2]|^2)  (x = 0 family / marginal)
+//             SRC_BUF        : the previous pass's output
+//   epilogue  DST_BUF        : store for the next pass
+//             DST_MOMENTS    : fused reduction of Algorithm 1 (sum c^2, c^4, c^6,
+//                              c^2 log2 c^2, FP32 nullity candidates, z-range weights)
+//             DST_SPECTRUM   : c_{x,z} for every z
+//             DST_NULLCOUNT  : #{z : | |c| - 1 | < eps} (FP64 recheck)
+//             DST_SQMAP/DST_P: the two elementwise maps of the x-marginal
+// The tile geometry (M, LO) and the element type are template parameters; the
+// pass's global bit offset and the family come from PassArgs / the grid.
+#pragma once
+
+#include "sre_internal.cuh"
+
+namespace sre {
+
+__device__ __forceinline__ int sgn_phase(int k) { return (((k + 1) >> 1) & 1) ? -1 : 1; }
+
+template <typename R> __device__ __forceinline__ R log2_any(R v);
+template <> __device__ __forceinline__ float log2_any<float>(float v) { return log2f(v); }
+template <> __device__ __forceinline__ double log2_any<double>(double v) { return log2(v); }
+
+template <typename R> struct RealMin;
+template <> struct RealMin<float> { static constexpr float v = 1.17549435e-38f; };
+template <> struct RealMin<double> { static constexpr double v = 2.2250738585072014e-308; };
+
+// Sum over the T threads of a group; the result is valid in the group's thread 0.
+// red: shared scratch of at least NT/32 doubles. All threads of the CTA call it.
+template <int T, int NT>
+__device__ __forceinline__ double group_sum(double v, double *red) {
+    if constexpr (T >= 32) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if constexpr (T == 32) {
+            return v;
+        } else {
+            const int w = threadIdx.x >> 5;
+            __syncthreads();
+            if ((threadIdx.x & 31) == 0) red[w] = v;
+            __syncthreads();
+            double s = 0.0;
+            if ((threadIdx.x & (T - 1)) == 0) {
+                const int w0 = w;
+#pragma unroll 1
+                for (int i = 0; i < T / 32; ++i) s += red[w0 + i];
+            }
+            return s;
+        }
+    } else {
+#pragma unroll
+        for (int o = T / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        return v;
+    }
+}
+
+// Packed global index of tile element e (see PassArgs::lo_g and TileCfg).
+template <class Cfg>
+__device__ __forceinline__ unsigned long long tile_gidx(unsigned long long gbase, int lo_g, uint32_t e) {
+    return gbase | ((unsigned long long)(e >> Cfg::LO) << lo_g) | (e & ((1u << Cfg::LO) - 1u));
+}
+
+// Load the tile in the first round's mapping (prologue of every pass).
+template <class Cfg, int SRC>
+__device__ __forceinline__ void pass_prologue(typename Cfg::C2 (&v)[Cfg::E], const PassArgs &a, long long slot,
+                                              unsigned long long x, int j, unsigned long long half,
+                                              unsigned long long gbase, uint32_t t) {
+    typedef typename Cfg::Real R;
+    typedef typename Cfg::C2 C2;
+    constexpr int A0 = Maps<Cfg>::first;
+    if constexpr (SRC == SRC_PSI_FAMILY) {
+#pragma unroll
+        for (int k = 0; k < Cfg::E; ++k) {
+            const unsigned long long g = tile_gidx<Cfg>(gbase, a.lo_g, Cfg::elem(t, k, A0));
+            if (x != 0) {
+                const unsigned long long b = insert0(g, j);
+                const float2 u = __ldg(a.psi + b);
+                const float2 w = __ldg(a.psi + (b ^ x));
+                const R ux = u.x, uy = u.y, wx = w.x, wy = w.y;
+                v[k].x = fma(wx, ux, wy * uy);     // conj(w) * u, contraction fixed
+                v[k].y = fma(wx, uy, -(wy * ux));
+            } else {
+                const float2 u = __ldg(a.psi + g);
+                const float2 w = __ldg(a.psi + (g | half));
+                const R ux = u.x, uy = u.y, wx = w.x, wy = w.y;
+                v[k].x = fma(ux, ux, uy * uy);
+                v[k].y = fma(wx, wx, wy * wy);
+            }
+        }
+    } else if constexpr (SRC == SRC_PSI_Q) {
+#pragma unroll
+        for (int k = 0; k < Cfg::E; ++k) {
+            const unsigned long long g = tile_gidx<Cfg>(gbase, a.lo_g, Cfg::elem(t, k, A0));
+            const float2 u = __ldg(a.psi + g);
+            const float2 w = __ldg(a.psi + (g | half));
+            const R ux = u.x, uy = u.y, wx = w.x, wy = w.y;
+            v[k].x = fma(ux, ux, uy * uy);
+            v[k].y = fma(wx, wx, wy * wy);
+        }
+    } else {
+        const C2 *src = reinterpret_cast<const C2 *>(a.src) + (size_t)slot * (size_t)a.slot_elems;
+#pragma unroll
+        for (int k = 0; k < Cfg::E; ++k) v[k] = src[tile_gidx<Cfg>(gbase, a.lo_g, Cfg::elem(t, k, A0))];
+    }
+}
+
+// The two Pauli expectations a transformed element H(z') yields:
+// c(z0) and c(z1), z0 = z' with 0 inserted at bit j, z1 = z0 | 2^j (signed).
+template <typename R, typename C2>
+__device__ __forceinline__ void family_pair(unsigned long long x, int j, R s, C2 h, unsigned long long zp,
+                                            unsigned long long &z0, unsigned long long &z1, R &c0, R &c1) {
+    z0 = insert0(zp, j);
+    z1 = z0 | (1ULL << j);
+    if (x) {
+        const R sc = (R)2 * s;
+        const int k0 = __popcll(x & z0);
+        const R re = sc * h.x, im = sc * h.y;
+        c0 = (R)sgn_phase(k0) * ((k0 & 1) ? im : re);
+        c1 = (R)sgn_phase(k0 + 1) * ((k0 & 1) ? re : im);
+    } else {
+        c0 = s * (h.x + h.y);
+        c1 = s * (h.x - h.y);
+    }
+}
+
+template <class Cfg, int SRC, int DST>
+__global__ void __launch_bounds__(Cfg::NT) fwht_pass_kernel(const PassArgs a) {
+    typedef typename Cfg::Real R;
+    typedef typename Cfg::C2 C2;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2 *sm = reinterpret_cast<C2 *>(smraw);
+    constexpr size_t TILE_SMEM = Cfg::NR > 1 ? sizeof(C2) * (size_t)Cfg::G * Cfg::SIZE : 0;
+    double *red = reinterpret_cast<double *>(smraw + TILE_SMEM);
+
+    const uint32_t tid = threadIdx.x;
+    const uint32_t grp = tid >> Cfg::TB;
+    const uint32_t t = tid & (Cfg::T - 1);
+
+    long long slot;
+    unsigned long long tile;
+    if constexpr (Cfg::G > 1) {
+        slot = (long long)blockIdx.x * Cfg::G + grp;
+        tile = 0;
+    } else {
+        slot = (long long)blockIdx.y + 65535LL * (long long)blockIdx.z;
+        tile = blockIdx.x;
+    }
+    const bool active = slot < a.n_fam;
+    if (!active) slot = a.n_fam - 1;   // run on valid data, write nothing
+
+    const int N = a.N;
+    const int n = a.n;
+    const unsigned long long dmask = (N >= 64) ? ~0ULL : ((1ULL << N) - 1ULL);
+    unsigned long long x = 0;
+    if constexpr (SRC == SRC_PSI_FAMILY || DST == DST_MOMENTS || DST == DST_SPECTRUM || DST == DST_NULLCOUNT) {
+        x = a.xs ? a.xs[a.fam_base + slot] : (unsigned long long)(a.fam_base + slot);
+        x &= dmask;
+    }
+    const int j = x ? 63 - __clzll((long long)x) : n;
+    const unsigned long long half = 1ULL << n;
+
+    // global packed index of tile element e
+    const int cb_bits = a.lo_g - Cfg::LO;
+    const unsigned long long cb = tile & ((1ULL << cb_bits) - 1ULL);
+    const unsigned long long outer = tile >> cb_bits;
+    const unsigned long long gbase = (outer << (a.lo_g + Cfg::K)) | (cb << Cfg::LO);
+    auto gidx = [&](uint32_t e) -> unsigned long long {
+        return gbase | ((unsigned long long)(e >> Cfg::LO) << a.lo_g) | (e & ((1u << Cfg::LO) - 1u));
+    };
+
+    C2 v[Cfg::E];
+    constexpr int AL = Maps<Cfg>::last;
+
+    // ---------------------------------------------------------- prologue
+    pass_prologue<Cfg, SRC>(v, a, slot, x, j, half, gbase, t);
+
+    // --------------------------------------------------------- transform
+    tile_transform<Cfg>(v, sm, t, grp);
+
+    // ---------------------------------------------------------- epilogue
+    if constexpr (DST == DST_BUF) {
+        if (active) {
+            C2 *dst = reinterpret_cast<C2 *>(a.dst) + (size_t)slot * (size_t)a.slot_elems;
+#pragma unroll
+            for (int k = 0; k < Cfg::E; ++k) dst[gidx(Cfg::elem(t, k, AL))] = v[k];
+        }
+    } else if constexpr (DST == DST_SQMAP) {
+        if (active) {
+            const R s = (R)(*a.s_ptr);
+            const R s2 = s * s;
+            C2 *dst = reinterpret_cast<C2 *>(a.dst);
+#pragma unroll
+            for (int k = 0; k < Cfg::E; ++k) {
+                const R p = v[k].x + v[k].y, m = v[k].x - v[k].y;
+                C2 o;
+                o.x = s2 * (p * p);
+                o.y = s2 * (m * m);
+                dst[gidx(Cfg::elem(t, k, AL))] = o;
+            }
+        }
+    } else if constexpr (DST == DST_P) {
+        if (active) {
+            const R invd = (R)1 / (R)(2.0 * (double)half);
+#pragma unroll
+            for (int k = 0; k < Cfg::E; ++k) {
+                const unsigned long long g = gidx(Cfg::elem(t, k, AL));
+                a.p_out[g] = (double)((v[k].x + v[k].y) * invd);
+                a.p_out[g | half] = (double)((v[k].x - v[k].y) * invd);
+            }
+        }
+    } else if constexpr (DST == DST_SPECTRUM) {
+        if (active) {
+            const R s = (R)(*a.s_ptr);
+            R *out = reinterpret_cast<R *>(a.spec_out) + (size_t)slot * (size_t)(2 * half);
+#pragma unroll
+            for (int k = 0; k < Cfg::E; ++k) {
+                unsigned long long z0, z1;
+                R c0, c1;
+                family_pair<R, C2>(x, j, s, v[k], gidx(Cfg::elem(t, k, AL)), z0, z1, c0, c1);
+                out[z0] = c0;
+                out[z1] = c1;
+            }
+        }
+    } else if constexpr (DST == DST_NULLCOUNT) {
+        const R s = (R)(*a.s_ptr);
+        const R sc = x ? (R)2 * s : s;
+        double cnt = 0.0;
+#pragma unroll
+        for (int k = 0; k < Cfg::E; ++k) {
+            R c0, c1;
+            if (x) { c0 = sc * v[k].x; c1 = sc * v[k].y; }
+            else { c0 = s * (v[k].x + v[k].y); c1 = s * (v[k].x - v[k].y); }
+            cnt += (fabs(fabs((double)c0) - 1.0) < a.eps) ? 1.0 : 0.0;
+            cnt += (fabs(fabs((double)c1) - 1.0) < a.eps) ? 1.0 : 0.0;
+        }
+        cnt = group_sum<Cfg::T, Cfg::NT>(cnt, red);
+        if (active && t == 0 && cnt > 0.0) atomicAdd(a.count_out + slot, (unsigned long long)cnt);
+    } else if constexpr (DST == DST_MOMENTS) {
+        const R s = (R)(*a.s_ptr);
+        const int RL = a.range_log2;
+        const unsigned long long zt = tile << Cfg::M;   // first z' of the tile (last pass: lo_g = 0, LO = 0)
+        const unsigned long long rA = insert0(zt, j) >> RL;
+        const R thr = (R)a.cand_thr;
+        const R thr2 = thr * thr;
+        R s2 = 0, s4 = 0, s6 = 0, sl = 0, w0 = 0, w1 = 0;
+        int cand = 0;
+#pragma unroll
+        for (int k = 0; k < Cfg::E; ++k) {
+            unsigned long long z0, z1;
+            R c0, c1;
+            family_pair<R, C2>(x, j, s, v[k], gidx(Cfg::elem(t, k, AL)), z0, z1, c0, c1);
+            const R q0 = c0 * c0, q1 = c1 * c1;
+            const R q0q = q0 * q0, q1q = q1 * q1;
+            s2 += q0 + q1;
+            s4 += q0q + q1q;
+            s6 += q0q * q0 + q1q * q1;
+            if (q0 >= RealMin<R>::v) sl += q0 * log2_any<R>(q0);
+            if (q1 >= RealMin<R>::v) sl += q1 * log2_any<R>(q1);
+            cand += (q0 > thr2) + (q1 > thr2);
+            if ((z0 >> RL) == rA) w0 += q0; else w1 += q0;
+            if ((z1 >> RL) == rA) w0 += q1; else w1 += q1;
+        }
+        double r2 = group_sum<Cfg::T, Cfg::NT>((double)s2, red);
+        double r4 = group_sum<Cfg::T, Cfg::NT>((double)s4, red);
+        double r6 = group_sum<Cfg::T, Cfg::NT>((double)s6, red);
+        double rl = group_sum<Cfg::T, Cfg::NT>((double)sl, red);
+        double rw0 = group_sum<Cfg::T, Cfg::NT>((double)w0, red);
+        double rw1 = group_sum<Cfg::T, Cfg::NT>((double)w1, red);
+        double rc = group_sum<Cfg::T, Cfg::NT>((double)cand, red);
+        if (active && t == 0) {
+            const long long tiles = (long long)(half >> Cfg::M) > 0 ? (long long)(half >> Cfg::M) : 1;
+            TilePartial &tp = a.tile_out[(size_t)slot * (size_t)tiles + tile];
+            tp.m[0] = r2; tp.m[1] = r4; tp.m[2] = r6; tp.m[3] = rl;
+            tp.w[0] = rw0; tp.w[1] = rw1;
+            tp.cand = (unsigned int)rc;
+        }
+    }
+}
+
+template <class Cfg, int SRC, int DST>
+cudaError_t launch_cfg(const PassArgs &a, int tiles, cudaStream_t st) {
+    const size_t tile_smem = Cfg::NR > 1 ? sizeof(typename Cfg::C2) * (size_t)Cfg::G * Cfg::SIZE : 0;
+    const size_t smem = tile_smem + sizeof(double) * (Cfg::NT / 32 + 1);
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(fwht_pass_kernel<Cfg, SRC, DST>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    dim3 grid;
+    if constexpr (Cfg::G > 1) {
+        grid = dim3((unsigned)((a.n_fam + Cfg::G - 1) / Cfg::G), 1, 1);
+    } else {
+        const long long nf = a.n_fam;
+        grid = dim3((unsigned)tiles, (unsigned)(nf < 65535 ? nf : 65535), (unsigned)((nf + 65534) / 65535));
+    }
+    fwht_pass_kernel<Cfg, SRC, DST><<<grid, Cfg::NT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+} // namespace sre

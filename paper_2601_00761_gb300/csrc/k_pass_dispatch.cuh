@@ -1,0 +1,88 @@
+// k_pass_dispatch.cuh -- (source, destination) combinations each tile
+// geometry is instantiated for, shared by the k_pass_*.cu units.
+#pragma once
+#include "k_pass.cuh"
+
+namespace sre {
+
+enum PassKind { KIND_SINGLE = 0, KIND_STRIDED = 1, KIND_ROW = 2 };
+
+#define SRE_ALLOW(R, KIND, SRC, DST) \
+    template <int M, int LO, int RB, int G> struct AllowedK<R, KIND, SRC, DST, M, LO, RB, G> { static constexpr bool value = true; };
+
+template <typename R, int KIND, int SRC, int DST, int M, int LO, int RB, int G>
+struct AllowedK { static constexpr bool value = false; };
+
+SRE_ALLOW(float, KIND_SINGLE, SRC_PSI_FAMILY, DST_MOMENTS)
+SRE_ALLOW(float, KIND_SINGLE, SRC_PSI_FAMILY, DST_SPECTRUM)
+SRE_ALLOW(float, KIND_STRIDED, SRC_PSI_FAMILY, DST_BUF)
+SRE_ALLOW(float, KIND_STRIDED, SRC_BUF, DST_BUF)
+SRE_ALLOW(float, KIND_ROW, SRC_BUF, DST_MOMENTS)
+SRE_ALLOW(float, KIND_ROW, SRC_BUF, DST_SPECTRUM)
+SRE_ALLOW(double, KIND_SINGLE, SRC_PSI_FAMILY, DST_NULLCOUNT)
+SRE_ALLOW(double, KIND_SINGLE, SRC_PSI_FAMILY, DST_SPECTRUM)
+SRE_ALLOW(double, KIND_SINGLE, SRC_PSI_Q, DST_SQMAP)
+SRE_ALLOW(double, KIND_SINGLE, SRC_BUF, DST_P)
+SRE_ALLOW(double, KIND_STRIDED, SRC_PSI_FAMILY, DST_BUF)
+SRE_ALLOW(double, KIND_STRIDED, SRC_PSI_Q, DST_BUF)
+SRE_ALLOW(double, KIND_STRIDED, SRC_BUF, DST_BUF)
+SRE_ALLOW(double, KIND_ROW, SRC_BUF, DST_NULLCOUNT)
+SRE_ALLOW(double, KIND_ROW, SRC_BUF, DST_SPECTRUM)
+SRE_ALLOW(double, KIND_ROW, SRC_BUF, DST_SQMAP)
+SRE_ALLOW(double, KIND_ROW, SRC_BUF, DST_P)
+#undef SRE_ALLOW
+
+template <int KIND, class Cfg, int SRC, int DST>
+cudaError_t launch_if(const PassArgs &a, int tiles, cudaStream_t st) {
+    if constexpr (AllowedK<typename Cfg::Real, KIND, SRC, DST, Cfg::M, Cfg::LO, Cfg::RB, Cfg::G>::value)
+        return launch_cfg<Cfg, SRC, DST>(a, tiles, st);
+    else
+        return cudaErrorInvalidValue;
+}
+
+template <int KIND, class Cfg>
+cudaError_t launch_sd(int src, int dst, const PassArgs &a, int tiles, cudaStream_t st) {
+#define SRE_D(S)                                                                 \
+    switch (dst) {                                                               \
+    case DST_BUF: return launch_if<KIND, Cfg, S, DST_BUF>(a, tiles, st);         \
+    case DST_MOMENTS: return launch_if<KIND, Cfg, S, DST_MOMENTS>(a, tiles, st); \
+    case DST_SPECTRUM: return launch_if<KIND, Cfg, S, DST_SPECTRUM>(a, tiles, st); \
+    case DST_NULLCOUNT: return launch_if<KIND, Cfg, S, DST_NULLCOUNT>(a, tiles, st); \
+    case DST_SQMAP: return launch_if<KIND, Cfg, S, DST_SQMAP>(a, tiles, st);     \
+    case DST_P: return launch_if<KIND, Cfg, S, DST_P>(a, tiles, st);             \
+    default: return cudaErrorInvalidValue;                                       \
+    }
+    switch (src) {
+    case SRC_PSI_FAMILY: SRE_D(SRC_PSI_FAMILY)
+    case SRC_PSI_Q: SRE_D(SRC_PSI_Q)
+    case SRC_BUF: SRE_D(SRC_BUF)
+    default: return cudaErrorInvalidValue;
+    }
+#undef SRE_D
+}
+
+// Geometry of the single-pass tile of M bits: RB register bits, G families per CTA.
+template <typename R> struct SingleRB;
+template <> struct SingleRB<float> { static constexpr int v = 5; };
+template <> struct SingleRB<double> { static constexpr int v = 4; };
+
+template <typename R, int M>
+struct SingleCfgOf {
+    static constexpr int RB = M < SingleRB<R>::v ? M : SingleRB<R>::v;
+    static constexpr int TB = M - RB;
+    static constexpr int G = TB >= 8 ? 1 : (256 >> TB);
+    typedef TileCfg<R, M, 0, RB, G> type;
+};
+
+cudaError_t launch_f32_single(int M, int src, int dst, const PassArgs &a, cudaStream_t st);
+cudaError_t launch_f32_strided(int K, int src, int dst, const PassArgs &a, int tiles, cudaStream_t st);
+cudaError_t launch_f32_row(int M, int src, int dst, const PassArgs &a, int tiles, cudaStream_t st);
+cudaError_t launch_f64_single(int M, int src, int dst, const PassArgs &a, cudaStream_t st);
+cudaError_t launch_f64_strided(int K, int src, int dst, const PassArgs &a, int tiles, cudaStream_t st);
+cudaError_t launch_f64_row(int M, int src, int dst, const PassArgs &a, int tiles, cudaStream_t st);
+
+// strided tile: 2^K rows x 2^(MS-K) columns, MS = 14 (FP32) / 13 (FP64)
+constexpr int F32_STRIDED_M = 14, F32_STRIDED_KMAX = 10, F32_ROW_MMIN = 10, F32_ROW_MMAX = 13, F32_SINGLE_MMAX = 14;
+constexpr int F64_STRIDED_M = 13, F64_STRIDED_KMAX = 9, F64_ROW_M = 12, F64_SINGLE_MMAX = 12;
+
+} // namespace sre

@@ -1,0 +1,129 @@
+// k_sample.cu -- the second level of the z sampler.
+//
+// A draw has already picked a z-range r (2^RL consecutive z in natural order)
+// and the remainder t' of its target inside that range. The range is the
+// output of one last-pass tile: the kernel recomputes that tile with the same
+// prologue, rounds and c-pair code as the fused moments epilogue (so every
+// c^2 is bit-identical to the one that entered the range weight), lays the
+// range's c^2 out in z order in shared memory and returns the smallest z with
+// C(z) > t', C the FP64 running sum over the range in a fixed association.
+#include "k_misc.cuh"
+#include "k_pass.cuh"
+
+namespace sre {
+
+template <class Cfg, int SRC>
+__global__ void __launch_bounds__(Cfg::NT) zsample_kernel(const PassArgs a, const DrawInfo *draws, int z_per_x,
+                                                          unsigned long long *zs, float *cz) {
+    typedef float R;
+    typedef float2 C2;
+    static_assert(Cfg::G == 1, "one tile per CTA");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2 *sm = reinterpret_cast<C2 *>(smraw);
+    double *seg = reinterpret_cast<double *>(smraw + sizeof(C2) * (size_t)Cfg::SIZE);
+
+    const long long idx = (long long)blockIdx.x + 65535LL * (long long)blockIdx.y;
+    if (idx >= a.n_fam * (long long)z_per_x) return;   // uniform over the CTA
+    const long long slot = idx / z_per_x;
+    const int kdraw = (int)(idx - slot * z_per_x);
+    const long long gf = a.fam_base + slot;
+    const uint32_t t = threadIdx.x;
+
+    const int N = a.N, n = a.n;
+    const unsigned long long x = a.xs[gf] & ((1ULL << N) - 1ULL);
+    const int j = x ? 63 - __clzll((long long)x) : n;
+    const unsigned long long half = 1ULL << n;
+    const DrawInfo dr = draws[(size_t)gf * z_per_x + kdraw];
+    const int RL = Cfg::M;
+    const unsigned long long zstart = dr.range << RL;
+    const unsigned long long zp0 = ((zstart >> (j + 1)) << j) | (zstart & ((1ULL << j) - 1ULL));
+    const unsigned long long tile = zp0 >> Cfg::M;
+    const unsigned long long gbase = tile << Cfg::M;
+
+    C2 v[Cfg::E];
+    pass_prologue<Cfg, SRC>(v, a, slot, x, j, half, gbase, t);
+    tile_transform<Cfg>(v, sm, t, 0);
+    __syncthreads();
+
+    float *wz = reinterpret_cast<float *>(smraw);
+    float *cv = wz + (1 << RL);
+    const R s = (R)(*a.s_ptr);
+    constexpr int AL = Maps<Cfg>::last;
+#pragma unroll
+    for (int k = 0; k < Cfg::E; ++k) {
+        unsigned long long z0, z1;
+        R c0, c1;
+        family_pair<R, C2>(x, j, s, v[k], gbase | Cfg::elem(t, k, AL), z0, z1, c0, c1);
+        if ((z0 >> RL) == dr.range) { wz[z0 - zstart] = c0 * c0; cv[z0 - zstart] = c0; }
+        if ((z1 >> RL) == dr.range) { wz[z1 - zstart] = c1 * c1; cv[z1 - zstart] = c1; }
+    }
+    __syncthreads();
+
+    constexpr int PER = (1 << Cfg::M) / Cfg::NT;
+    const int lo = t * PER;
+    double run = 0.0;
+    for (int i = 0; i < PER; ++i) run += (double)wz[lo + i];
+    seg[t + 1] = run;
+    __syncthreads();
+    if (t == 0) {
+        seg[0] = 0.0;
+        for (int i = 1; i <= Cfg::NT; ++i) seg[i] = seg[i - 1] + seg[i];
+    }
+    __syncthreads();
+    const double tt = dr.t;
+    const size_t out = (size_t)gf * z_per_x + kdraw;
+    if (seg[t + 1] > tt && !(seg[t] > tt)) {
+        double acc = 0.0;
+        int pick = lo + PER - 1;
+        for (int i = 0; i < PER; ++i) {
+            acc += (double)wz[lo + i];
+            if (seg[t] + acc > tt) { pick = lo + i; break; }
+        }
+        zs[out] = zstart + (unsigned long long)pick;
+        cz[out] = cv[pick];
+    } else if (t == 0 && !(seg[Cfg::NT] > tt)) {
+        int pick = (1 << RL) - 1;
+        while (pick > 0 && !(wz[pick] > 0.0f)) --pick;
+        zs[out] = zstart + (unsigned long long)pick;
+        cz[out] = cv[pick];
+    }
+}
+
+template <class Cfg, int SRC>
+cudaError_t launch_zs(const PassArgs &a, const DrawInfo *draws, int z_per_x, unsigned long long *zs, float *cz,
+                      cudaStream_t st) {
+    const size_t smem = sizeof(float2) * (size_t)Cfg::SIZE + sizeof(double) * (Cfg::NT + 1);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(zsample_kernel<Cfg, SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const long long nd = a.n_fam * (long long)z_per_x;
+    dim3 grid((unsigned)(nd < 65535 ? nd : 65535), (unsigned)((nd + 65534) / 65535));
+    zsample_kernel<Cfg, SRC><<<grid, Cfg::NT, smem, st>>>(a, draws, z_per_x, zs, cz);
+    return cudaGetLastError();
+}
+
+template <int M> using SampleSingle = TileCfg<float, M, 0, (M < 5 ? M : 5), 1>;
+
+cudaError_t launch_zsample(int single, int M, const PassArgs &a, const DrawInfo *draws, int z_per_x,
+                           unsigned long long *zs, float *cz, cudaStream_t st) {
+    if (single) {
+        switch (M) {
+#define C(m) case m: return launch_zs<SampleSingle<m>, SRC_PSI_FAMILY>(a, draws, z_per_x, zs, cz, st);
+        C(0) C(1) C(2) C(3) C(4) C(5) C(6) C(7) C(8) C(9) C(10) C(11) C(12) C(13) C(14)
+#undef C
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (M) {
+#define C(m) case m: return launch_zs<TileCfg<float, m, 0, 5, 1>, SRC_BUF>(a, draws, z_per_x, zs, cz, st);
+    C(10) C(11) C(12) C(13)
+#undef C
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+} // namespace sre

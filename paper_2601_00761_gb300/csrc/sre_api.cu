@@ -1,0 +1,993 @@
+// sre_api.cu -- the C ABI (include/sre.h): argument checks, transform plans,
+// workspace layout and the launch sequences of each entry point.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "sre.h"
+#include "k_misc.cuh"
+#include "k_pass_dispatch.cuh"
+
+using namespace sre;
+
+namespace {
+
+thread_local std::string g_err;
+
+sre_status fail(sre_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CK(call)                                                                                        \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess)                                                                          \
+            return fail(SRE_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define CS(call)                          \
+    do {                                  \
+        sre_status s_ = (call);           \
+        if (s_ != SRE_OK) return s_;      \
+    } while (0)
+
+constexpr size_t BATCH_BYTES = 2ULL << 30;   // intermediate budget per launch sequence
+
+// kernels issued by this library since load (all entry points)
+std::atomic<unsigned long long> g_launches{0};
+void count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+constexpr int EXACT_PARTS = 1024;
+
+// --------------------------------------------------------------- plans
+struct Plan {
+    int N = 0, n = 0, prec = 32;
+    int npass = 1, nstrided = 0;
+    int K[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+    int M_last = 0;
+    long long tiles_strided = 0, tiles_last = 1;
+    long long B = 1;
+    size_t slot_bytes = 0;
+};
+
+int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+sre_status plan_for(int N, const sre_opts *o, int prec, Plan &P) {
+    P = Plan();
+    P.N = N;
+    P.n = N - 1;
+    P.prec = prec;
+    const int single_max = prec == 32 ? F32_SINGLE_MMAX : F64_SINGLE_MMAX;
+    if (P.n <= single_max) {
+        P.npass = 1;
+        P.M_last = P.n;
+        P.tiles_last = 1;
+        P.slot_bytes = 0;
+        P.B = 1LL << 20;
+        if (prec == 32 && o && o->x_batch > 0) P.B = o->x_batch;
+        return SRE_OK;
+    }
+    int nlo, kmax, ms;
+    if (prec == 32) {
+        nlo = (o && o->radix_log2 > 0) ? clampi(o->radix_log2, F32_ROW_MMIN, F32_ROW_MMAX) : F32_ROW_MMAX;
+        kmax = (o && o->tile_log2 > 0) ? clampi(o->tile_log2, 1, F32_STRIDED_KMAX) : F32_STRIDED_KMAX;
+        ms = F32_STRIDED_M;
+    } else {
+        nlo = F64_ROW_M;
+        kmax = F64_STRIDED_KMAX;
+        ms = F64_STRIDED_M;
+    }
+    // A strided tile is 2^K rows x 2^(ms-K) columns and its columns must fit
+    // below the pass's row stride 2^lo: ms - K <= lo. Only the bottom strided
+    // pass (lo = nlo) can violate it, so it takes the largest K.
+    const int rest = P.n - nlo;
+    const int kmin_bottom = ms - nlo;
+    if (kmax < kmin_bottom) kmax = kmin_bottom;
+    int ns = (rest + kmax - 1) / kmax;
+    if (ns > 3) return fail(SRE_ENOTSUP, "N=%d needs %d strided passes", N, ns);
+    // balanced, extra bits to the lower passes
+    for (int i = 0; i < ns; ++i) P.K[i] = rest / ns + (i >= ns - rest % ns ? 1 : 0);
+    if (P.K[ns - 1] < kmin_bottom) {
+        if (rest < kmin_bottom) return fail(SRE_EINVAL, "N=%d: radix %d leaves %d strided bits", N, nlo, rest);
+        P.K[ns - 1] = kmin_bottom;
+        const int rem = rest - kmin_bottom;
+        const int no = ns - 1 > 0 ? ns - 1 : (rem > 0 ? 1 : 0);
+        if (no + 1 > 3) return fail(SRE_ENOTSUP, "N=%d needs %d strided passes", N, no + 1);
+        for (int i = 0; i < no; ++i) P.K[i] = rem / no + (i >= no - rem % no ? 1 : 0);
+        P.K[no] = kmin_bottom;
+        ns = no + 1;
+    }
+    P.nstrided = ns;
+    P.npass = ns + 1;
+    int top = P.n;
+    for (int i = 0; i < ns; ++i) {
+        P.lo[i] = top - P.K[i];
+        top = P.lo[i];
+        if (ms - P.K[i] > P.lo[i]) return fail(SRE_EINVAL, "internal plan error (N=%d pass %d)", N, i);
+    }
+    P.M_last = nlo;
+    P.tiles_strided = 1LL << (P.n - ms);
+    P.tiles_last = 1LL << (P.n - nlo);
+    P.slot_bytes = (size_t)(prec == 32 ? 8 : 16) << P.n;
+    long long B = (long long)(BATCH_BYTES / P.slot_bytes);
+    if (B < 1) B = 1;
+    if (B > 4096) B = 4096;
+    if (prec == 32 && o && o->x_batch > 0) B = o->x_batch;
+    P.B = B;
+    return SRE_OK;
+}
+
+// -------------------------------------------------------------- arena
+struct Arena {
+    char *base;
+    size_t off = 0;
+    explicit Arena(void *b) : base((char *)b) {}
+    template <class T> T *take(size_t n) {
+        off = (off + 255) & ~(size_t)255;
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += n * sizeof(T) + 256;
+        return p;
+    }
+};
+
+struct ExactWS {
+    double *scal, *npart, *epart, *etot;
+    void *inter;
+    TilePartial *tiles;
+    FamMoments *fm;
+    unsigned long long *flags, *nflag, *counts, *cnt_sum;
+    void *inter64;
+};
+
+void layout_exact(Arena &A, const Plan &P, const Plan &P64, ExactWS &w) {
+    const unsigned long long d = 1ULL << P.N;
+    w.scal = A.take<double>(SCAL_N);
+    w.npart = A.take<double>(NORM_BLOCKS);
+    w.epart = A.take<double>(5 * EXACT_PARTS);
+    w.etot = A.take<double>(8);
+    w.inter = P.npass > 1 ? (void *)A.take<char>(P.slot_bytes * (size_t)P.B) : nullptr;
+    const long long nb = P.npass > 1 ? P.B : (long long)d;
+    w.tiles = A.take<TilePartial>((size_t)nb * (size_t)P.tiles_last);
+    w.fm = A.take<FamMoments>(d);
+    w.flags = A.take<unsigned long long>(d);
+    w.nflag = A.take<unsigned long long>(1);
+    w.counts = A.take<unsigned long long>(d);
+    w.cnt_sum = A.take<unsigned long long>(1);
+    w.inter64 = P64.npass > 1 ? (void *)A.take<char>(P64.slot_bytes * (size_t)P64.B) : nullptr;
+}
+
+struct McWS {
+    double *scal, *npart;
+    double *p, *mwork, *bsum;
+    unsigned long long *xs;
+    void *inter;
+    TilePartial *tiles;
+    FamMoments *fm;
+    double *W;
+    DrawInfo *draws;
+    unsigned long long *zs;
+    float *cz;
+    double *y, *out;
+};
+
+void layout_mc(Arena &A, const Plan &P, int mode, long long n_x, int zpx, McWS &w) {
+    const unsigned long long d = 1ULL << P.N;
+    const bool marg = mode == SRE_MC_MARGINAL;
+    w.scal = A.take<double>(SCAL_N);
+    w.npart = A.take<double>(NORM_BLOCKS);
+    w.p = marg ? A.take<double>(d) : nullptr;
+    w.mwork = marg ? A.take<double>(d) : nullptr;
+    w.bsum = marg ? A.take<double>(d / SCAN_CHUNK + 1) : nullptr;
+    w.xs = A.take<unsigned long long>(n_x);
+    const long long B = P.npass > 1 ? P.B : (n_x < P.B ? n_x : P.B);
+    w.inter = P.npass > 1 ? (void *)A.take<char>(P.slot_bytes * (size_t)P.B) : nullptr;
+    w.tiles = A.take<TilePartial>((size_t)B * (size_t)P.tiles_last);
+    w.fm = A.take<FamMoments>(n_x);
+    const long long nr = 1LL << (P.N - P.M_last);
+    w.W = marg ? A.take<double>((size_t)B * (size_t)nr) : nullptr;
+    const size_t nd = marg ? (size_t)n_x * (size_t)zpx : 1;
+    w.draws = marg ? A.take<DrawInfo>(nd) : nullptr;
+    w.zs = marg ? A.take<unsigned long long>(nd) : nullptr;
+    w.cz = A.take<float>(nd);
+    w.y = A.take<double>(6 * (size_t)n_x);
+    w.out = A.take<double>(24);
+}
+
+// ------------------------------------------------ library-owned workspace
+std::mutex g_ws_mu;
+struct DevWS { void *p = nullptr; size_t n = 0; };
+std::vector<DevWS> g_ws;
+struct DevBuf { void *p = nullptr; size_t n = 0; };
+std::vector<DevBuf> g_gatebuf;
+
+sre_status own_workspace(size_t need, void **out) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    if ((int)g_ws.size() <= dev) g_ws.resize(dev + 1);
+    DevWS &w = g_ws[dev];
+    if (w.n < need) {
+        if (w.p) CK(cudaFree(w.p));
+        w.p = nullptr;
+        w.n = 0;
+        cudaError_t e = cudaMalloc(&w.p, need);
+        if (e != cudaSuccess) {
+            w.p = nullptr;
+            return fail(SRE_ENOMEM, "cudaMalloc(%zu) failed: %s", need, cudaGetErrorString(e));
+        }
+        w.n = need;
+    }
+    *out = w.p;
+    return SRE_OK;
+}
+
+sre_status resolve_workspace(void *ws, size_t ws_bytes, size_t need, void **out) {
+    if (ws) {
+        if (ws_bytes < need) return fail(SRE_EINVAL, "workspace of %zu bytes, %zu needed", ws_bytes, need);
+        if (((uintptr_t)ws) & 255) return fail(SRE_EINVAL, "workspace must be 256-byte aligned");
+        *out = ws;
+        return SRE_OK;
+    }
+    return own_workspace(need, out);
+}
+
+// ------------------------------------------------------------ checks
+sre_status check_psi(const void *psi, int N, int nmin, int nmax) {
+    if (N < nmin || N > nmax) return fail(SRE_EINVAL, "N=%d outside %d..%d", N, nmin, nmax);
+    if (!psi) return fail(SRE_EINVAL, "psi is NULL");
+    if (((uintptr_t)psi) & 7) return fail(SRE_EINVAL, "psi must be 8-byte aligned");
+    return SRE_OK;
+}
+
+sre_status check_opts(const sre_opts *o, sre_opts &out) {
+    sre_default_opts(&out);
+    if (!o) return SRE_OK;
+    out = *o;
+    if (out.eps_null <= 0) out.eps_null = 1e-6;
+    if (out.precision != SRE_FP32_SIMT && out.precision != SRE_BF16X2_TC && out.precision != SRE_BF16X3_TC)
+        return fail(SRE_EINVAL, "unknown precision %d", out.precision);
+    if (out.precision != SRE_FP32_SIMT)
+        return fail(SRE_ENOTSUP, "precision %d is not available in this build", out.precision);
+    if (out.x_batch < 0 || out.radix_log2 < 0 || out.tile_log2 < 0)
+        return fail(SRE_EINVAL, "negative tiling option");
+    return SRE_OK;
+}
+
+PassArgs base_args(const Plan &P, const void *psi, const double *scal) {
+    PassArgs a;
+    memset(&a, 0, sizeof a);
+    a.psi = reinterpret_cast<const float2 *>(psi);
+    a.N = P.N;
+    a.n = P.n;
+    a.slot_elems = 1LL << P.n;
+    a.range_log2 = P.M_last;
+    a.s_ptr = scal + SCAL_S;
+    a.cand_thr = 1.0f - 1e-4f;
+    return a;
+}
+
+
+// Optional CUDA-event timing of every pass launch.
+struct PassTimer {
+    std::vector<cudaEvent_t> ev;   // pairs (start, stop) per launch
+    std::vector<int> pass;         // pass index of each pair
+};
+
+sre_status timer_mark(PassTimer *T, int pass, cudaStream_t st, bool start) {
+    if (!T) return SRE_OK;
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    CK(cudaEventRecord(e, st));
+    T->ev.push_back(e);
+    if (start) T->pass.push_back(pass);
+    return SRE_OK;
+}
+
+// Library-wide pass timing (sre_pass_timing): when on, run_transform of the
+// FP32 family transforms records events around each pass launch and the
+// entry point folds them into per-pass sums after its stream synchronisation.
+std::mutex g_timing_mu;
+bool g_timing_on = false;
+double g_timing_ms[4] = {0, 0, 0, 0};
+long long g_timing_n[4] = {0, 0, 0, 0};
+double g_timing_bytes[4] = {0, 0, 0, 0};
+
+sre_status timer_fold(PassTimer &T) {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    for (size_t i = 0; i < T.pass.size(); ++i) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, T.ev[2 * i], T.ev[2 * i + 1]));
+        g_timing_ms[T.pass[i]] += ms;
+        g_timing_n[T.pass[i]] += 1;
+    }
+    for (cudaEvent_t e : T.ev) cudaEventDestroy(e);
+    T.ev.clear();
+    T.pass.clear();
+    return SRE_OK;
+}
+
+void timing_bytes(const Plan &P, long long fam_per_launch) {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    const double d = std::ldexp(1.0, P.N);
+    for (int p = 0; p < P.npass; ++p) {
+        double b = 0.0;
+        if (p == 0) b += 8.0 * d;
+        if (p > 0) b += 4.0 * d;
+        if (p < P.npass - 1) b += 4.0 * d;
+        g_timing_bytes[p] = b * (double)fam_per_launch;
+    }
+}
+
+// One transform of every family in a.fam_base .. + a.n_fam (one launch
+// sequence): strided passes top-down, then the last pass with dst_last.
+sre_status run_transform(const Plan &P, PassArgs a, int src0, int dst_last, void *inter, cudaStream_t st,
+                         PassTimer *T = nullptr) {
+    cudaError_t e;
+    if (P.npass == 1) {
+        a.lo_g = 0;
+        CS(timer_mark(T, 0, st, true));
+        e = P.prec == 32 ? launch_f32_single(P.n, src0, dst_last, a, st) : launch_f64_single(P.n, src0, dst_last, a, st);
+        if (e != cudaSuccess) return fail(SRE_ECUDA, "single-pass launch (N=%d): %s", P.N, cudaGetErrorString(e));
+        count_launches(1);
+        CS(timer_mark(T, 0, st, false));
+        return SRE_OK;
+    }
+    for (int i = 0; i < P.nstrided; ++i) {
+        PassArgs b = a;
+        b.lo_g = P.lo[i];
+        b.src = inter;
+        b.dst = inter;
+        const int s = i == 0 ? src0 : SRC_BUF;
+        CS(timer_mark(T, i, st, true));
+        e = P.prec == 32 ? launch_f32_strided(P.K[i], s, DST_BUF, b, (int)P.tiles_strided, st)
+                         : launch_f64_strided(P.K[i], s, DST_BUF, b, (int)P.tiles_strided, st);
+        if (e != cudaSuccess)
+            return fail(SRE_ECUDA, "strided pass %d (N=%d K=%d): %s", i, P.N, P.K[i], cudaGetErrorString(e));
+        count_launches(1);
+        CS(timer_mark(T, i, st, false));
+    }
+    PassArgs b = a;
+    b.lo_g = 0;
+    b.src = inter;
+    if (dst_last == DST_SQMAP) b.dst = inter;
+    CS(timer_mark(T, P.nstrided, st, true));
+    e = P.prec == 32 ? launch_f32_row(P.M_last, SRC_BUF, dst_last, b, (int)P.tiles_last, st)
+                     : launch_f64_row(P.M_last, SRC_BUF, dst_last, b, (int)P.tiles_last, st);
+    if (e != cudaSuccess) return fail(SRE_ECUDA, "row pass (N=%d): %s", P.N, cudaGetErrorString(e));
+    count_launches(1);
+    CS(timer_mark(T, P.nstrided, st, false));
+    return SRE_OK;
+}
+
+// x-marginal into p (FP64): WHT(|psi|^2) -> square -> WHT -> /d
+sre_status run_marginal(const void *psi, int N, const double *scal, double *p, double *mwork, cudaStream_t st) {
+    Plan P64;
+    CS(plan_for(N, nullptr, 64, P64));
+    PassArgs a = base_args(P64, psi, scal);
+    a.n_fam = 1;
+    a.dst = mwork;
+    a.src = mwork;
+    a.p_out = p;
+    CS(run_transform(P64, a, SRC_PSI_Q, DST_SQMAP, mwork, st));
+    CS(run_transform(P64, a, SRC_BUF, DST_P, mwork, st));
+    return SRE_OK;
+}
+
+void finalize_exact(const double T[5], int N, sre_result *r) {
+    const double d = std::ldexp(1.0, N);
+    const double H = N * (T[0] / d) - T[3] / d;
+    r->S[0] = H;
+    r->S[1] = T[1] / (d * d);
+    r->S[2] = T[2] / (d * d * d);
+    r->M[0] = H - N;
+    r->M[1] = -std::log2(r->S[1]) - N;
+    r->M[2] = -0.5 * std::log2(r->S[2]) - N;
+    r->parseval = T[0] / d;
+    // a-priori FP32 rounding estimate: relative error of c ~ (N + 2) 2^-24
+    const double ec = (N + 2) * std::ldexp(1.0, -24);
+    r->err_M[0] = 2.0 * ec * (N + 2);
+    r->err_M[1] = 4.0 * ec / std::log(2.0);
+    r->err_M[2] = 6.0 * ec / (2.0 * std::log(2.0));
+    for (int a = 0; a < 3; ++a) { r->M_rb[a] = r->M[a]; r->err_rb[a] = r->err_M[a]; }
+}
+
+void init_result(sre_result *r) {
+    memset(r, 0, sizeof *r);
+    r->stab_count = -1;
+    r->nullity = -1;
+}
+
+sre_status nullity_from_count(long long cnt, int N, sre_result *r) {
+    r->stab_count = cnt;
+    if (cnt <= 0 || (cnt & (cnt - 1)) != 0) {
+        r->nullity = -1;
+        return fail(SRE_ENULLITY, "stabilizer count %lld is not a power of two", cnt);
+    }
+    int l = 0;
+    while ((1LL << l) < cnt) ++l;
+    r->nullity = N - l;
+    return SRE_OK;
+}
+
+// exact sweep; with_moments=false still computes them (they are free)
+sre_status exact_impl(const void *psi, int N, const sre_opts &o, void *ws, size_t ws_bytes, cudaStream_t st,
+                      sre_result *out) {
+    Plan P, P64;
+    CS(plan_for(N, &o, 32, P));
+    CS(plan_for(N, nullptr, 64, P64));
+    Arena dry(nullptr);
+    ExactWS w;
+    layout_exact(dry, P, P64, w);
+    void *base = nullptr;
+    CS(resolve_workspace(ws, ws_bytes, dry.off, &base));
+    Arena A(base);
+    layout_exact(A, P, P64, w);
+
+    const unsigned long long d = 1ULL << N;
+    CK(launch_norm2((const float2 *)psi, N, w.scal, w.npart, st));
+    count_launches(2);
+    PassArgs a = base_args(P, psi, w.scal);
+    a.tile_out = w.tiles;
+    const long long step = P.npass > 1 ? P.B : (long long)d;
+    for (long long fb = 0; fb < (long long)d; fb += step) {
+        const long long nf = (long long)d - fb < step ? (long long)d - fb : step;
+        PassArgs b = a;
+        b.fam_base = fb;
+        b.n_fam = nf;
+        CS(run_transform(P, b, SRC_PSI_FAMILY, DST_MOMENTS, w.inter, st));
+        CK(launch_fam_reduce(w.tiles, nf, (int)P.tiles_last, nullptr, fb, N, P.M_last, P.M_last, w.fm, fb, nullptr,
+                             0, st));
+        count_launches(1);
+    }
+    CK(cudaMemsetAsync(w.nflag, 0, sizeof(unsigned long long), st));
+    CK(launch_exact_totals(w.fm, (long long)d, w.epart, EXACT_PARTS, w.etot, w.flags, w.nflag, st));
+    count_launches(2);
+    double host[8];
+    unsigned long long nflag = 0;
+    CK(cudaMemcpyAsync(host, w.etot, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&nflag, w.nflag, sizeof nflag, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(host + 5, w.scal + SCAL_NORM2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (!(host[5] > 0.0)) return fail(SRE_EZERO, "psi has zero norm");
+
+    // FP64 recheck of the candidate families
+    unsigned long long cnt = 0;
+    if (nflag > 0) {
+        CK(cudaMemsetAsync(w.counts, 0, nflag * sizeof(unsigned long long), st));
+        PassArgs c = base_args(P64, psi, w.scal);
+        c.xs = w.flags;
+        c.eps = o.eps_null;
+        const long long step64 = P64.npass > 1 ? P64.B : (1LL << 20);
+        for (long long fb = 0; fb < (long long)nflag; fb += step64) {
+            const long long nf = (long long)nflag - fb < step64 ? (long long)nflag - fb : step64;
+            PassArgs b = c;
+            b.fam_base = fb;
+            b.n_fam = nf;
+            b.count_out = w.counts + fb;
+            CS(run_transform(P64, b, SRC_PSI_FAMILY, DST_NULLCOUNT, w.inter64, st));
+        }
+        CK(launch_sum_u64(w.counts, (long long)nflag, w.cnt_sum, st));
+        count_launches(1);
+        CK(cudaMemcpyAsync(&cnt, w.cnt_sum, sizeof cnt, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    init_result(out);
+    finalize_exact(host, N, out);
+    out->n_flagged = (long long)nflag;
+    out->n_families = (long long)d;
+    out->n_passes = P.npass;
+    return nullity_from_count((long long)cnt, N, out);
+}
+
+} // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+const char *sre_version(void) { return "sre-gb300 0.1 (sm_103a)"; }
+
+const char *sre_last_error(void) { return g_err.c_str(); }
+
+void sre_default_opts(sre_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->precision = SRE_FP32_SIMT;
+    o->eps_null = 1e-6;
+}
+
+sre_status sre_make_plan(int N, const sre_opts *opts, sre_plan *plan) {
+    if (!plan) return fail(SRE_EINVAL, "plan is NULL");
+    if (N < 1 || N > 32) return fail(SRE_EINVAL, "N=%d outside 1..32", N);
+    sre_opts o;
+    CS(check_opts(opts, o));
+    Plan P;
+    CS(plan_for(N, &o, 32, P));
+    memset(plan, 0, sizeof *plan);
+    plan->N = N;
+    plan->n_bits = P.n;
+    plan->n_passes = P.npass;
+    for (int i = 0; i < P.nstrided; ++i) { plan->pass_lo[i] = P.lo[i]; plan->pass_bits[i] = P.K[i]; }
+    plan->pass_lo[P.npass - 1] = 0;
+    plan->pass_bits[P.npass - 1] = P.M_last;
+    plan->x_batch = (int)(P.B > 0x7fffffff ? 0x7fffffff : P.B);
+    plan->range_log2 = P.M_last;
+    if (N <= 26) {
+        size_t b = 0;
+        if (sre_workspace_bytes(N, -1, 0, 0, &o, &b) == SRE_OK) plan->workspace_exact = b;
+    }
+    return SRE_OK;
+}
+
+sre_status sre_workspace_bytes(int N, int mode, long long n_x, int z_per_x, const sre_opts *opts, size_t *bytes) {
+    if (!bytes) return fail(SRE_EINVAL, "bytes is NULL");
+    sre_opts o;
+    CS(check_opts(opts, o));
+    Plan P;
+    if (mode == -1) {
+        if (N < 1 || N > 26) return fail(SRE_EINVAL, "exact: N=%d outside 1..26", N);
+        Plan P64;
+        CS(plan_for(N, &o, 32, P));
+        CS(plan_for(N, nullptr, 64, P64));
+        Arena A(nullptr);
+        ExactWS w;
+        layout_exact(A, P, P64, w);
+        *bytes = A.off;
+        return SRE_OK;
+    }
+    if (mode != SRE_MC_UNIFORM && mode != SRE_MC_MARGINAL) return fail(SRE_EINVAL, "unknown mode %d", mode);
+    if (N < 2 || N > 30) return fail(SRE_EINVAL, "mc: N=%d outside 2..30", N);
+    if (n_x < 2 || (mode == SRE_MC_MARGINAL && z_per_x < 1)) return fail(SRE_EINVAL, "n_x >= 2 and z_per_x >= 1 required");
+    CS(plan_for(N, &o, 32, P));
+    Arena A(nullptr);
+    McWS w;
+    layout_mc(A, P, mode, n_x, z_per_x, w);
+    *bytes = A.off;
+    return SRE_OK;
+}
+
+sre_status sre_release_workspace(void) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    if ((int)g_ws.size() > dev && g_ws[dev].p) {
+        CK(cudaFree(g_ws[dev].p));
+        g_ws[dev] = DevWS();
+    }
+    if ((int)g_gatebuf.size() > dev && g_gatebuf[dev].p) {
+        CK(cudaFree(g_gatebuf[dev].p));
+        g_gatebuf[dev] = DevBuf();
+    }
+    return SRE_OK;
+}
+
+sre_status sre_norm2(const void *psi, int N, double *norm2_host, void *stream) {
+    CS(check_psi(psi, N, 1, 32));
+    if (!norm2_host) return fail(SRE_EINVAL, "norm2_host is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    void *base = nullptr;
+    CS(own_workspace(sizeof(double) * (SCAL_N + NORM_BLOCKS) + 1024, &base));
+    double *scal = (double *)base;
+    double *part = scal + SCAL_N;
+    CK(launch_norm2((const float2 *)psi, N, scal, part, st));
+    count_launches(2);
+    CK(cudaMemcpyAsync(norm2_host, scal + SCAL_NORM2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return SRE_OK;
+}
+
+sre_status sre_exact(const void *psi, int N, const sre_opts *opts, void *workspace, size_t workspace_bytes,
+                     void *stream, sre_result *out) {
+    CS(check_psi(psi, N, 1, 26));
+    if (!out) return fail(SRE_EINVAL, "out is NULL");
+    sre_opts o;
+    CS(check_opts(opts, o));
+    return exact_impl(psi, N, o, workspace, workspace_bytes, (cudaStream_t)stream, out);
+}
+
+sre_status sre_exact_batched(const void *const *psi_ptrs, const int *Ns, int count, const sre_opts *opts,
+                             void *workspace, size_t workspace_bytes, void *stream, sre_result *out) {
+    if (count < 0 || (count > 0 && (!psi_ptrs || !Ns || !out))) return fail(SRE_EINVAL, "bad batch arguments");
+    sre_opts o;
+    CS(check_opts(opts, o));
+    for (int i = 0; i < count; ++i) CS(check_psi(psi_ptrs[i], Ns[i], 1, 20));
+    if (workspace) return fail(SRE_ENOTSUP, "sre_exact_batched uses the library workspace (pass NULL)");
+    (void)workspace_bytes;
+    for (int i = 0; i < count; ++i) {
+        sre_status s = exact_impl(psi_ptrs[i], Ns[i], o, nullptr, 0, (cudaStream_t)stream, out + i);
+        if (s != SRE_OK && s != SRE_ENULLITY) return s;
+    }
+    return SRE_OK;
+}
+
+sre_status sre_mc(const void *psi, int N, int mode, long long n_x, int z_per_x, unsigned long long seed,
+                  unsigned long long counter0, const sre_opts *opts, void *workspace, size_t workspace_bytes,
+                  void *stream, sre_result *out, unsigned long long *xs_dev, unsigned long long *zs_dev,
+                  float *c_dev) {
+    CS(check_psi(psi, N, 2, 30));
+    if (!out) return fail(SRE_EINVAL, "out is NULL");
+    if (mode != SRE_MC_UNIFORM && mode != SRE_MC_MARGINAL) return fail(SRE_EINVAL, "unknown mode %d", mode);
+    if (n_x < 2) return fail(SRE_EINVAL, "n_x must be >= 2");
+    if (mode == SRE_MC_MARGINAL && (z_per_x < 1 || z_per_x > (1 << 20)))
+        return fail(SRE_EINVAL, "z_per_x must be in 1..2^20");
+    if (mode == SRE_MC_UNIFORM) z_per_x = 1;
+    sre_opts o;
+    CS(check_opts(opts, o));
+    cudaStream_t st = (cudaStream_t)stream;
+    Plan P;
+    CS(plan_for(N, &o, 32, P));
+    Arena dry(nullptr);
+    McWS w;
+    layout_mc(dry, P, mode, n_x, z_per_x, w);
+    void *base = nullptr;
+    CS(resolve_workspace(workspace, workspace_bytes, dry.off, &base));
+    Arena A(base);
+    layout_mc(A, P, mode, n_x, z_per_x, w);
+    const bool marg = mode == SRE_MC_MARGINAL;
+    const unsigned long long d = 1ULL << N;
+
+    CK(launch_norm2((const float2 *)psi, N, w.scal, w.npart, st));
+    count_launches(2);
+    if (marg) {
+        CS(run_marginal(psi, N, w.scal, w.p, w.mwork, st));
+        CK(launch_scan(w.p, d, w.p, w.bsum, st));
+        count_launches(3);
+    }
+    CK(launch_draw_x(w.p, N, n_x, marg ? 1 : 0, seed, counter0, w.xs, st));
+    count_launches(1);
+
+    PassArgs a = base_args(P, psi, w.scal);
+    a.xs = w.xs;
+    a.tile_out = w.tiles;
+    const long long step = P.B < n_x ? P.B : n_x;
+    const long long nr = 1LL << (N - P.M_last);
+    bool timing;
+    {
+        std::lock_guard<std::mutex> lk(g_timing_mu);
+        timing = g_timing_on;
+    }
+    PassTimer T;
+    if (timing) timing_bytes(P, step);
+    for (long long fb = 0; fb < n_x; fb += step) {
+        const long long nf = n_x - fb < step ? n_x - fb : step;
+        PassArgs b = a;
+        b.fam_base = fb;
+        b.n_fam = nf;
+        CS(run_transform(P, b, SRC_PSI_FAMILY, DST_MOMENTS, w.inter, st, (timing && nf == step) ? &T : nullptr));
+        CK(launch_fam_reduce(w.tiles, nf, (int)P.tiles_last, w.xs, fb, N, P.M_last, P.M_last, w.fm, fb,
+                             marg ? w.W : nullptr, nr, st));
+        count_launches(1);
+        if (marg) {
+            CK(launch_zrange_select(w.W, nr, nf, fb, z_per_x, seed, counter0, w.draws, st));
+            count_launches(1);
+            PassArgs c = b;
+            c.src = w.inter;
+            c.lo_g = 0;
+            CK(launch_zsample(P.npass == 1, P.M_last, c, w.draws, z_per_x, w.zs, w.cz, st));
+            count_launches(1);
+        }
+    }
+    CK(launch_mc_stats(w.fm, w.cz, n_x, z_per_x, N, marg ? 1 : 0, w.y, w.out, st));
+    count_launches(2);
+    double h[24];
+    CK(cudaMemcpyAsync(h, w.out, 19 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h + 20, w.scal + SCAL_NORM2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (xs_dev) CK(cudaMemcpyAsync(xs_dev, w.xs, n_x * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
+    if (marg && zs_dev)
+        CK(cudaMemcpyAsync(zs_dev, w.zs, (size_t)n_x * z_per_x * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
+    if (marg && c_dev)
+        CK(cudaMemcpyAsync(c_dev, w.cz, (size_t)n_x * z_per_x * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    if (timing) CS(timer_fold(T));
+    if (!(h[20] > 0.0)) return fail(SRE_EZERO, "psi has zero norm");
+
+    init_result(out);
+    const double dd = (double)d;
+    if (!marg) {
+        const double nm = (double)(n_x - 1);
+        for (int k = 0; k < 3; ++k) {
+            const double mean = h[k] / nm;
+            const double shat = h[12 + k] + (dd - 1.0) * mean;
+            double var = h[6 + k] / nm - mean * mean;
+            if (var < 0) var = 0;
+            if (k == 0) {
+                out->M[0] = shat - N;
+                out->S[0] = shat;
+                out->err_M[0] = (dd - 1.0) * std::sqrt(var / nm);
+            } else {
+                const double alpha = k + 1.0;
+                out->M[k] = std::log2(shat) / (1.0 - alpha) - N;
+                out->S[k] = shat;
+                const double r = std::sqrt(var) / (shat / dd);
+                out->err_M[k] = r / (std::fabs(1.0 - alpha) * std::log(2.0) * std::sqrt((double)n_x));
+            }
+            out->M_rb[k] = out->M[k];
+            out->err_rb[k] = out->err_M[k];
+        }
+        out->parseval = -1.0;
+    } else {
+        const double n = (double)n_x;
+        for (int which = 0; which < 2; ++which) {
+            for (int k = 0; k < 3; ++k) {
+                const int idx = k + 3 * which;
+                const double mean = h[idx] / n;
+                double var = h[6 + idx] / n - mean * mean;
+                if (var < 0) var = 0;
+                const double se = std::sqrt(var / n);
+                double Mv, ev;
+                if (k == 0) { Mv = mean; ev = se; }
+                else {
+                    const double alpha = k + 1.0;
+                    Mv = std::log2(mean) / (1.0 - alpha);
+                    ev = se / (mean * std::fabs(1.0 - alpha) * std::log(2.0));
+                }
+                if (which == 0) { out->M[k] = Mv; out->err_M[k] = ev; out->S[k] = mean; }
+                else { out->M_rb[k] = Mv; out->err_rb[k] = ev; }
+            }
+        }
+        out->parseval = -1.0;
+        out->n_samples = n_x * (long long)z_per_x;
+    }
+    out->n_families = n_x;
+    out->n_passes = P.npass;
+    return SRE_OK;
+}
+
+sre_status pauli_x_marginal(const void *psi, int N, double *p_dev, void *workspace, size_t workspace_bytes,
+                            void *stream) {
+    CS(check_psi(psi, N, 1, 30));
+    if (!p_dev || (((uintptr_t)p_dev) & 7)) return fail(SRE_EINVAL, "p_dev must be a non-NULL 8-byte aligned pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t need = sizeof(double) * ((1ULL << N) + SCAL_N + NORM_BLOCKS) + 4096;
+    void *base = nullptr;
+    CS(resolve_workspace(workspace, workspace_bytes, need, &base));
+    Arena A(base);
+    double *scal = A.take<double>(SCAL_N);
+    double *part = A.take<double>(NORM_BLOCKS);
+    double *mwork = A.take<double>(1ULL << N);
+    CK(launch_norm2((const float2 *)psi, N, scal, part, st));
+    count_launches(2);
+    CS(run_marginal(psi, N, scal, p_dev, mwork, st));
+    double nrm = 0;
+    CK(cudaMemcpyAsync(&nrm, scal + SCAL_NORM2, sizeof nrm, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (!(nrm > 0.0)) return fail(SRE_EZERO, "psi has zero norm");
+    return SRE_OK;
+}
+
+sre_status stabilizer_nullity(const void *psi, int N, double eps, int *nullity_host, long long *stab_count_host,
+                              void *stream) {
+    CS(check_psi(psi, N, 1, 26));
+    sre_opts o;
+    sre_default_opts(&o);
+    o.eps_null = eps > 0 ? eps : 1e-6;
+    sre_result r;
+    sre_status s = exact_impl(psi, N, o, nullptr, 0, (cudaStream_t)stream, &r);
+    if (nullity_host) *nullity_host = r.nullity;
+    if (stab_count_host) *stab_count_host = r.stab_count;
+    return s;
+}
+
+sre_status sre_family_spectrum(const void *psi, int N, unsigned long long x, const sre_opts *opts, float *c_dev,
+                               void *stream) {
+    CS(check_psi(psi, N, 1, 30));
+    if (!c_dev || (((uintptr_t)c_dev) & 3)) return fail(SRE_EINVAL, "c_dev must be a non-NULL aligned pointer");
+    if (x >> N) return fail(SRE_EINVAL, "x has bits above N");
+    sre_opts o;
+    CS(check_opts(opts, o));
+    cudaStream_t st = (cudaStream_t)stream;
+    Plan P;
+    CS(plan_for(N, &o, 32, P));
+    void *base = nullptr;
+    CS(own_workspace(sizeof(double) * (SCAL_N + NORM_BLOCKS) + P.slot_bytes + 4096, &base));
+    Arena A(base);
+    double *scal = A.take<double>(SCAL_N);
+    double *part = A.take<double>(NORM_BLOCKS);
+    void *inter = P.npass > 1 ? (void *)A.take<char>(P.slot_bytes) : nullptr;
+    CK(launch_norm2((const float2 *)psi, N, scal, part, st));
+    count_launches(2);
+    PassArgs a = base_args(P, psi, scal);
+    a.fam_base = (long long)x;
+    a.n_fam = 1;
+    a.spec_out = c_dev;
+    CS(run_transform(P, a, SRC_PSI_FAMILY, DST_SPECTRUM, inter, st));
+    CK(cudaStreamSynchronize(st));
+    return SRE_OK;
+}
+
+// FP64 spectrum of one family (the arithmetic of the nullity recheck).
+sre_status sre_family_spectrum_f64(const void *psi, int N, unsigned long long x, double *c_dev, void *stream) {
+    CS(check_psi(psi, N, 1, 28));
+    if (!c_dev || (((uintptr_t)c_dev) & 7)) return fail(SRE_EINVAL, "c_dev must be a non-NULL aligned pointer");
+    if (x >> N) return fail(SRE_EINVAL, "x has bits above N");
+    cudaStream_t st = (cudaStream_t)stream;
+    Plan P;
+    CS(plan_for(N, nullptr, 64, P));
+    void *base = nullptr;
+    CS(own_workspace(sizeof(double) * (SCAL_N + NORM_BLOCKS) + P.slot_bytes + 4096, &base));
+    Arena A(base);
+    double *scal = A.take<double>(SCAL_N);
+    double *part = A.take<double>(NORM_BLOCKS);
+    void *inter = P.npass > 1 ? (void *)A.take<char>(P.slot_bytes) : nullptr;
+    CK(launch_norm2((const float2 *)psi, N, scal, part, st));
+    count_launches(2);
+    PassArgs a = base_args(P, psi, scal);
+    a.fam_base = (long long)x;
+    a.n_fam = 1;
+    a.spec_out = c_dev;
+    CS(run_transform(P, a, SRC_PSI_FAMILY, DST_SPECTRUM, inter, st));
+    CK(cudaStreamSynchronize(st));
+    return SRE_OK;
+}
+
+sre_status apply_clifford_tdoped_circuit(void *psi, int N, const sre_gate *gates, long long n_gates, void *stream) {
+    CS(check_psi(psi, N, 1, 32));
+    if (n_gates < 0 || (n_gates > 0 && !gates)) return fail(SRE_EINVAL, "bad gate list");
+    for (long long g = 0; g < n_gates; ++g) {
+        const sre_gate &G = gates[g];
+        if (G.op > SRE_GATE_TDG) return fail(SRE_EINVAL, "gate %lld: unknown op %d", g, G.op);
+        if (G.q0 >= N) return fail(SRE_EINVAL, "gate %lld: qubit %d >= N", g, G.q0);
+        if (G.op == SRE_GATE_CNOT && (G.q1 >= N || G.q1 == G.q0))
+            return fail(SRE_EINVAL, "gate %lld: bad CNOT target %d", g, G.q1);
+    }
+    if (n_gates == 0) return SRE_OK;
+    // split into blocks of consecutive gates acting inside <= GATE_BLOCK_Q qubits
+    const int low = N < GATE_BLOCK_LOW ? N : GATE_BLOCK_LOW;
+    const int qmax = N < GATE_BLOCK_Q ? N : GATE_BLOCK_Q;
+    std::vector<int> blocks;
+    std::vector<unsigned char> bq;
+    std::vector<GateRow> rows(n_gates);
+    long long g0 = 0;
+    while (g0 < n_gates) {
+        bool in[64] = {false};
+        int cnt = 0;
+        for (int q = 0; q < low; ++q) { in[q] = true; ++cnt; }
+        long long g = g0;
+        for (; g < n_gates; ++g) {
+            const sre_gate &G = gates[g];
+            int add = (!in[G.q0]) + (G.op == SRE_GATE_CNOT && !in[G.q1] && G.q1 != G.q0 ? 1 : 0);
+            if (cnt + add > qmax) break;
+            if (!in[G.q0]) { in[G.q0] = true; ++cnt; }
+            if (G.op == SRE_GATE_CNOT && !in[G.q1]) { in[G.q1] = true; ++cnt; }
+        }
+        unsigned char loc[64];
+        unsigned char list[GATE_BLOCK_Q];
+        int m = 0;
+        for (int q = 0; q < N; ++q)
+            if (in[q]) { loc[q] = (unsigned char)m; list[m++] = (unsigned char)q; }
+        for (int i = m; i < GATE_BLOCK_Q; ++i) list[i] = 255;
+        for (long long k = g0; k < g; ++k) {
+            rows[k].op = gates[k].op;
+            rows[k].q0 = loc[gates[k].q0];
+            rows[k].q1 = gates[k].op == SRE_GATE_CNOT ? loc[gates[k].q1] : 0;
+        }
+        blocks.push_back((int)g0);
+        blocks.push_back((int)(g - g0));
+        bq.insert(bq.end(), list, list + GATE_BLOCK_Q);
+        g0 = g;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    GateRow *dg = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_ws_mu);
+        if ((int)g_gatebuf.size() <= dev) g_gatebuf.resize(dev + 1);
+        DevBuf &b = g_gatebuf[dev];
+        const size_t need = sizeof(GateRow) * (size_t)n_gates;
+        if (b.n < need) {
+            if (b.p) CK(cudaFree(b.p));
+            b.p = nullptr;
+            b.n = 0;
+            cudaError_t e = cudaMalloc(&b.p, need);
+            if (e != cudaSuccess) return fail(SRE_ENOMEM, "gate buffer: %s", cudaGetErrorString(e));
+            b.n = need;
+        }
+        dg = (GateRow *)b.p;
+    }
+    CK(cudaMemcpyAsync(dg, rows.data(), sizeof(GateRow) * (size_t)n_gates, cudaMemcpyHostToDevice, st));
+    CK(launch_gate_blocks((float2 *)psi, N, dg, blocks.data(), (int)(blocks.size() / 2), bq.data(), st));
+    count_launches(blocks.size() / 2);
+    CK(cudaStreamSynchronize(st));
+    return SRE_OK;
+}
+
+unsigned long long sre_kernel_launches(void) { return g_launches.load(); }
+
+sre_status sre_pass_timing(int enable, double *ms_sum_host, long long *launches_host, double *bytes_host) {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    if (ms_sum_host)
+        for (int p = 0; p < 4; ++p) ms_sum_host[p] = g_timing_ms[p];
+    if (launches_host)
+        for (int p = 0; p < 4; ++p) launches_host[p] = g_timing_n[p];
+    if (bytes_host)
+        for (int p = 0; p < 4; ++p) bytes_host[p] = g_timing_bytes[p];
+    if (enable) {
+        for (int p = 0; p < 4; ++p) { g_timing_ms[p] = 0; g_timing_n[p] = 0; g_timing_bytes[p] = 0; }
+    }
+    g_timing_on = enable != 0;
+    return SRE_OK;
+}
+
+sre_status sre_profile_passes(const void *psi, int N, long long n_x, const sre_opts *opts, void *stream,
+                              double *ms_host, double *bytes_host, int *n_passes, long long *fam_per_launch) {
+    CS(check_psi(psi, N, 2, 30));
+    if (n_x < 1 || !ms_host || !bytes_host || !n_passes || !fam_per_launch)
+        return fail(SRE_EINVAL, "bad profile arguments");
+    sre_opts o;
+    CS(check_opts(opts, o));
+    cudaStream_t st = (cudaStream_t)stream;
+    Plan P;
+    CS(plan_for(N, &o, 32, P));
+    Arena dry(nullptr);
+    McWS w;
+    layout_mc(dry, P, SRE_MC_UNIFORM, n_x < 2 ? 2 : n_x, 1, w);
+    void *base = nullptr;
+    CS(own_workspace(dry.off, &base));
+    Arena A(base);
+    layout_mc(A, P, SRE_MC_UNIFORM, n_x < 2 ? 2 : n_x, 1, w);
+    CK(launch_norm2((const float2 *)psi, N, w.scal, w.npart, st));
+    count_launches(2);
+    CK(launch_draw_x(nullptr, N, n_x, 0, 12345ULL, 0ULL, w.xs, st));
+    count_launches(1);
+    PassArgs a = base_args(P, psi, w.scal);
+    a.xs = w.xs;
+    a.tile_out = w.tiles;
+    const long long step = P.B < n_x ? P.B : n_x;
+    PassTimer T;
+    for (long long fb = 0; fb < n_x; fb += step) {
+        PassArgs b = a;
+        b.fam_base = fb;
+        b.n_fam = n_x - fb < step ? n_x - fb : step;
+        CS(run_transform(P, b, SRC_PSI_FAMILY, DST_MOMENTS, w.inter, st, &T));
+    }
+    CK(cudaStreamSynchronize(st));
+    double sum[4] = {0, 0, 0, 0};
+    int cnt[4] = {0, 0, 0, 0};
+    for (size_t i = 0; i < T.pass.size(); ++i) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, T.ev[2 * i], T.ev[2 * i + 1]));
+        sum[T.pass[i]] += ms;
+        cnt[T.pass[i]] += 1;
+    }
+    for (cudaEvent_t e : T.ev) cudaEventDestroy(e);
+    *n_passes = P.npass;
+    *fam_per_launch = step;
+    const double d = std::ldexp(1.0, N);
+    for (int p = 0; p < P.npass; ++p) {
+        ms_host[p] = cnt[p] ? sum[p] / cnt[p] : 0.0;
+        // algorithmic bytes per family of pass p: the first pass reads psi
+        // (8 B per amplitude, once); every pass but the last writes the
+        // packed intermediate (8 B per complex point, d/2 points); every
+        // pass but the first reads it.
+        double b = 0.0;
+        if (p == 0) b += 8.0 * d;
+        if (p > 0) b += 4.0 * d;
+        if (p < P.npass - 1) b += 4.0 * d;
+        bytes_host[p] = b * (double)step;
+    }
+    return SRE_OK;
+}
+
+// Philox4x64-10 blocks for host-side checks of the device generator:
+// ctr_key_dev n x (c0,c1,c2,c3,k0,k1), out_dev n x 4 words.
+sre_status sre_philox_blocks(const unsigned long long *ctr_key_dev, unsigned long long *out_dev, int n, void *stream) {
+    if (n < 0 || (n > 0 && (!ctr_key_dev || !out_dev))) return fail(SRE_EINVAL, "bad philox arguments");
+    if (n == 0) return SRE_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(launch_philox_test(ctr_key_dev, out_dev, n, st));
+    count_launches(1);
+    CK(cudaStreamSynchronize(st));
+    return SRE_OK;
+}
+
+} // extern "C"

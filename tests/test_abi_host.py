@@ -1,0 +1,141 @@
+"""CPU tests of the C ABI: the library loads, exports every entry point that
+include/sre.h declares, and its host-side logic (plans, workspace sizes,
+argument checks) behaves -- none of these calls touches a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2601_00761_gb300 as sre
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2601_00761_gb300 import build
+    build.build()
+    return sre.load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "sre.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"SRE_API\s+[\w\s\*]+?\b(\w+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for want in ("sre_exact", "sre_mc", "pauli_x_marginal", "stabilizer_nullity",
+                 "apply_clifford_tdoped_circuit", "sre_exact_batched", "sre_family_spectrum"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    for name in _declared():
+        assert hasattr(L, name), name
+
+
+def test_binding_exposes_the_same_names(L):
+    for name in _declared():
+        assert callable(getattr(sre, name)), name
+
+
+def test_version(L):
+    assert "sm_103a" in sre.sre_version()
+
+
+@pytest.mark.parametrize("N,passes,bits", [
+    (1, 1, [0]), (10, 1, [9]), (15, 1, [14]), (16, 2, [2, 13]), (18, 2, [4, 13]),
+    (24, 2, [10, 13]), (25, 3, [5, 6, 13]), (30, 3, [8, 8, 13])])
+def test_plans(L, N, passes, bits):
+    p = sre.sre_make_plan(N)
+    assert p["n_passes"] == passes
+    assert p["pass_bits"] == bits
+    assert sum(p["pass_bits"]) == N - 1
+    # passes tile the bit range [0, N-1) top-down without gaps
+    top = N - 1
+    for lo, k in zip(p["pass_lo"], p["pass_bits"]):
+        assert lo + k == top
+        top = lo
+    assert top == 0
+
+
+def test_plan_options(L):
+    p = sre.sre_make_plan(24, radix_log2=11, tile_log2=6)
+    assert p["pass_bits"] == [6, 6, 11]
+    # the bottom strided pass keeps its columns below its row stride
+    p = sre.sre_make_plan(18, radix_log2=10, tile_log2=4)
+    assert p["pass_bits"] == [3, 4, 10]
+    p = sre.sre_make_plan(16, radix_log2=10, tile_log2=2)
+    assert p["pass_bits"] == [1, 4, 10]
+    assert sre.sre_make_plan(24, x_batch=3)["x_batch"] == 3
+
+
+def test_workspace_sizes(L):
+    a = sre.sre_workspace_bytes(18, -1)
+    b = sre.sre_workspace_bytes(18, -1, x_batch=8)
+    assert a > b > 0
+    m = sre.sre_workspace_bytes(24, sre.SRE_MC_MARGINAL, 4096, 256)
+    u = sre.sre_workspace_bytes(24, sre.SRE_MC_UNIFORM, 4096, 1)
+    assert m > u > 0
+    # the marginal needs at least p(x) + its FP64 work buffer and one intermediate
+    assert m > 2 * 8 * 2**24 + 8 * 2**23
+
+
+def _fake_ptr(addr):
+    return ctypes.c_void_p(addr)
+
+
+def test_argument_errors_do_not_touch_the_gpu(L):
+    r = sre.Result()
+    o = sre.sre_default_opts()
+    assert L.sre_exact(None, 10, ctypes.byref(o), None, 0, None, ctypes.byref(r)) == sre.SRE_EINVAL
+    assert "NULL" in sre.sre_last_error()
+    assert L.sre_exact(_fake_ptr(0x1001), 10, ctypes.byref(o), None, 0, None, ctypes.byref(r)) == sre.SRE_EINVAL
+    assert "aligned" in sre.sre_last_error()
+    assert L.sre_exact(_fake_ptr(0x1000), 0, ctypes.byref(o), None, 0, None, ctypes.byref(r)) == sre.SRE_EINVAL
+    assert L.sre_exact(_fake_ptr(0x1000), 27, ctypes.byref(o), None, 0, None, ctypes.byref(r)) == sre.SRE_EINVAL
+    assert L.sre_mc(_fake_ptr(0x1000), 10, 7, 10, 1, 0, 0, None, None, 0, None, ctypes.byref(r),
+                    None, None, None) == sre.SRE_EINVAL
+    assert L.sre_mc(_fake_ptr(0x1000), 10, 1, 1, 1, 0, 0, None, None, 0, None, ctypes.byref(r),
+                    None, None, None) == sre.SRE_EINVAL
+    assert L.sre_mc(_fake_ptr(0x1000), 10, 1, 10, 0, 0, 0, None, None, 0, None, ctypes.byref(r),
+                    None, None, None) == sre.SRE_EINVAL
+    bad = sre.Opts(9, 1e-6, 0, 0, 0)
+    assert L.sre_exact(_fake_ptr(0x1000), 10, ctypes.byref(bad), None, 0, None, ctypes.byref(r)) == sre.SRE_EINVAL
+    neg = sre.Opts(0, 1e-6, 0, 0, -1)
+    assert L.sre_exact(_fake_ptr(0x1000), 10, ctypes.byref(neg), None, 0, None, ctypes.byref(r)) == sre.SRE_EINVAL
+    g = (sre.Gate * 1)(sre.Gate(9, 0, 0))
+    assert L.apply_clifford_tdoped_circuit(_fake_ptr(0x1000), 4, g, 1, None) == sre.SRE_EINVAL
+    g = (sre.Gate * 1)(sre.Gate(3, 1, 1))
+    assert L.apply_clifford_tdoped_circuit(_fake_ptr(0x1000), 4, g, 1, None) == sre.SRE_EINVAL
+    g = (sre.Gate * 1)(sre.Gate(0, 4, 0))
+    assert L.apply_clifford_tdoped_circuit(_fake_ptr(0x1000), 4, g, 1, None) == sre.SRE_EINVAL
+    assert L.sre_family_spectrum(_fake_ptr(0x1000), 4, 16, None, _fake_ptr(0x2000), None) == sre.SRE_EINVAL
+    assert L.pauli_x_marginal(_fake_ptr(0x1000), 4, None, None, 0, None) == sre.SRE_EINVAL
+    p = sre.Plan()
+    assert L.sre_make_plan(33, None, ctypes.byref(p)) == sre.SRE_EINVAL
+    assert L.sre_workspace_bytes(10, 5, 10, 1, None, ctypes.byref(ctypes.c_size_t())) == sre.SRE_EINVAL
+
+
+def test_structs_match_header_layout():
+    # sre_gate is a packed 3-byte row; sre_opts / sre_result field order as declared
+    assert ctypes.sizeof(sre.Gate) == 3
+    assert sre.Result.M.offset == 0 and sre.Result.parseval.offset == 15 * 8
+    assert sre.Result.stab_count.offset == 16 * 8
+
+
+def test_oracle_not_imported_by_the_package():
+    import sys
+    import subprocess
+    code = ("import sys; import paper_2601_00761_gb300 as s; s.load(); "
+            "assert not any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules), 'oracle imported'")
+    subprocess.check_call([sys.executable, "-c", code], cwd=ROOT)
+    pkg = os.path.join(ROOT, "paper_2601_00761_gb300")
+    for dp, _, fs in os.walk(pkg):
+        for f in fs:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dp, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt and "sre_oracle" not in txt, f

@@ -1,0 +1,342 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances (FP32 SIMT path): |dc| <= 1e-6 per Pauli expectation, |dM_a| <=
+1e-5 (base-2 units); nullity, stabilizer counts, sampled x and z indices and
+Philox words bit-exact; FP64 paths (nullity recheck arithmetic, x-marginal)
+1e-12."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_00761_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_C = 1e-6
+TOL_M = 1e-5
+
+
+@pytest.fixture(scope="module")
+def sre():
+    import paper_2601_00761_gb300 as s
+    from paper_2601_00761_gb300 import build
+    build.build()
+    s.load()
+    return s
+
+
+def dev(psi):
+    return torch.from_numpy(np.ascontiguousarray(psi, dtype=np.complex64)).cuda()
+
+
+def sample_xs(N, k, seed):
+    d = 1 << N
+    g = np.random.default_rng(seed)
+    xs = {0, 1, d - 1, 1 << (N - 1), (1 << (N - 1)) | 1, d // 3}
+    xs |= set(int(v) for v in g.integers(0, d, size=k))
+    return sorted(x for x in xs if 0 <= x < d)
+
+
+# ------------------------------------------------------------------ RNG
+def test_philox_device_matches_oracle(sre):
+    g = np.random.default_rng(1)
+    rows = g.integers(0, 2**63, size=(64, 6), dtype=np.int64)
+    rows[0] = 0
+    rows[1] = -1                                   # all ones
+    out = sre.sre_philox_blocks(torch.from_numpy(rows).cuda()).cpu().numpy().view(np.uint64)
+    for i in range(rows.shape[0]):
+        r = rows[i].view(np.uint64)
+        assert np.array_equal(out[i], oracle.philox4x64_10(r[:4], r[4:]))
+
+
+def test_norm2(sre):
+    for N in (1, 5, 12, 20):
+        psi = inputs.unnormalised_gaussian_state(N, N)
+        assert abs(sre.sre_norm2(dev(psi)) / oracle.norm2(psi) - 1) < 1e-12
+
+
+# ------------------------------------------------------------- spectra
+@pytest.mark.parametrize("N", list(range(1, 9)))
+def test_family_spectrum_all_x(sre, N):
+    psi = inputs.unnormalised_gaussian_state(N, 50 + N)
+    p = dev(psi)
+    for x in range(1 << N):
+        c = sre.sre_family_spectrum(p, x).cpu().numpy()
+        assert np.max(np.abs(c - oracle.family_spectrum(psi, x))) < TOL_C, x
+
+
+@pytest.mark.parametrize("N", [9, 10, 11, 12, 13, 14, 15])
+def test_family_spectrum_single_pass(sre, N):
+    psi = inputs.haar_state(N, 60 + N)
+    p = dev(psi)
+    for x in sample_xs(N, 6, N):
+        c = sre.sre_family_spectrum(p, x).cpu().numpy()
+        assert np.max(np.abs(c - oracle.family_spectrum(psi, x))) < TOL_C, x
+
+
+@pytest.mark.parametrize("N,kw", [(16, {}), (17, {}), (18, {}), (18, {"radix_log2": 10, "tile_log2": 4}),
+                                  (19, {"radix_log2": 11}), (20, {}), (22, {"tile_log2": 5})])
+def test_family_spectrum_multi_pass(sre, N, kw):
+    psi = inputs.haar_state(N, 70 + N)
+    p = dev(psi)
+    for x in sample_xs(N, 3, N):
+        c = sre.sre_family_spectrum(p, x, **kw).cpu().numpy()
+        assert np.max(np.abs(c - oracle.family_spectrum(psi, x))) < TOL_C, (x, kw)
+
+
+def test_family_spectrum_n24_full_size(sre):
+    """Headline size: 2 passes (10 + 13 bits), sampled families."""
+    N = 24
+    psi = inputs.haar_state(N, 24)
+    p = dev(psi)
+    for x in (0, 0x9A3C51, (1 << 23) | 5):
+        c = sre.sre_family_spectrum(p, x).cpu().numpy()
+        assert np.max(np.abs(c - oracle.family_spectrum(psi, x))) < TOL_C, x
+
+
+def test_family_spectrum_three_pass(sre):
+    N = 25
+    psi = inputs.haar_state(N, 25)
+    p = dev(psi)
+    for x in (0, (1 << 24) | 0x1234):
+        c = sre.sre_family_spectrum(p, x).cpu().numpy()
+        assert np.max(np.abs(c - oracle.family_spectrum(psi, x))) < TOL_C, x
+
+
+def test_family_spectrum_product_state_large(sre):
+    """Product states: c_{x,z} = prod_j c^(j), checked on sampled z at N=24."""
+    N = 24
+    g = np.random.default_rng(5)
+    qs = []
+    for _ in range(N):
+        a = g.standard_normal(2) + 1j * g.standard_normal(2)
+        a /= np.linalg.norm(a)
+        qs.append((a[0], a[1]))
+    psi = inputs.product_state(qs)
+    bl = []
+    for a0, a1 in qs:
+        X = 2 * (np.conj(a0) * a1).real
+        Y = 2 * (np.conj(a0) * a1).imag
+        Z = abs(a0) ** 2 - abs(a1) ** 2
+        bl.append({(0, 0): 1.0, (0, 1): Z, (1, 0): X, (1, 1): Y})
+    p = dev(psi)
+    for x in (0, 0xABCDE1, (1 << 24) - 1):
+        c = sre.sre_family_spectrum(p, x).cpu().numpy()
+        for z in g.integers(0, 1 << N, size=200):
+            want = np.prod([bl[j][((x >> j) & 1, (int(z) >> j) & 1)] for j in range(N)])
+            assert abs(c[z] - want) < TOL_C + 1e-6   # complex64 input rounding
+
+
+@pytest.mark.parametrize("N", [1, 3, 8, 12, 13, 14, 16])
+def test_family_spectrum_f64(sre, N):
+    psi = inputs.haar_state(N, 80 + N)
+    p = dev(psi)
+    for x in sample_xs(N, 3, N):
+        c = sre.sre_family_spectrum_f64(p, x).cpu().numpy()
+        assert np.max(np.abs(c - oracle.family_spectrum(psi, x))) < 1e-12, x
+
+
+# ---------------------------------------------------------------- exact
+def _check_exact(r, ref, N):
+    assert np.max(np.abs(np.array(r["M"]) - ref["M"])) < TOL_M, (r["M"], ref["M"])
+    assert r["stab_count"] == ref["stab_count"]
+    assert r["nullity"] == ref["nullity"]
+    assert abs(r["parseval"] - 1.0) < 1e-5
+
+
+def test_exact_n10_workload(sre):
+    w = inputs.workload_n10_states()
+    states = [w["haar"], oracle.circuit_state(10, w["tdoped_gates"]), w["t4"]]
+    for psi in states:
+        ref = oracle.sre_exact(psi)
+        r = sre.sre_exact(dev(psi), allow_nullity_error=True)
+        _check_exact(r, ref, 10)
+    r = sre.sre_exact(dev(w["t4"]))
+    assert abs(r["M"][1] - 4 * math.log2(4 / 3)) < TOL_M and r["nullity"] == 4
+
+
+@pytest.mark.parametrize("N", [2, 4, 6, 8, 11, 12, 13])
+def test_exact_vs_oracle(sre, N):
+    gates = inputs.random_clifford_tdoped_gates(N, 6 * N, 3, 300 + N)
+    psi = oracle.circuit_state(N, gates)
+    _check_exact(sre.sre_exact(dev(psi), allow_nullity_error=True), oracle.sre_exact(psi), N)
+    h = inputs.haar_state(N, 400 + N)
+    _check_exact(sre.sre_exact(dev(h), allow_nullity_error=True), oracle.sre_exact(h), N)
+
+
+@pytest.mark.parametrize("N,k", [(1, 1), (2, 0), (5, 3), (9, 9), (14, 7), (15, 5), (16, 8), (17, 3), (18, 9)])
+def test_exact_t_product_closed_form(sre, N, k):
+    r = sre.sre_exact(dev(inputs.t_product_state(N, k)))
+    assert abs(r["M"][0] - k / 2) < TOL_M
+    assert abs(r["M"][1] - k * math.log2(4 / 3)) < TOL_M
+    assert abs(r["M"][2] - (k / 2) * math.log2(8 / 5)) < TOL_M
+    assert r["nullity"] == k and r["stab_count"] == 1 << (N - k)
+
+
+@pytest.mark.parametrize("N", [2, 5, 9, 14, 16, 18])
+def test_exact_stabilizer_states(sre, N):
+    psi = oracle.circuit_state(N, inputs.random_clifford_gates(N, 8 * N, 900 + N))
+    r = sre.sre_exact(dev(psi))
+    assert np.max(np.abs(r["M"])) < TOL_M
+    assert r["nullity"] == 0 and r["stab_count"] == 1 << N
+
+
+def test_exact_n18_workload(sre):
+    """N=18 T-doped circuits (eta x n_T grid, first four of twelve): sampled
+    families against the oracle plus the invariants that hold at any size."""
+    for spec in inputs.workload_n18_gate_lists()[:4]:
+        psi = oracle.circuit_state(18, spec["gates"])
+        p = dev(psi)
+        r = sre.sre_exact(p)
+        assert abs(r["parseval"] - 1) < 1e-5
+        assert r["M"][0] >= r["M"][1] - TOL_M and r["M"][1] >= r["M"][2] - TOL_M and r["M"][2] > -TOL_M
+        assert 0 <= r["nullity"] <= spec["n_t"]
+        if spec["n_t"] == 0:
+            assert np.max(np.abs(r["M"])) < TOL_M and r["nullity"] == 0
+        for x in sample_xs(18, 2, spec["seed"]):
+            c = sre.sre_family_spectrum(p, x).cpu().numpy()
+            assert np.max(np.abs(c - oracle.family_spectrum(psi, x))) < TOL_C
+
+
+def test_exact_clifford_invariance_multipass(sre):
+    N = 16
+    base = inputs.random_clifford_tdoped_gates(N, 0, 4, 77, n_t=6, first_block=32)
+    psi = oracle.circuit_state(N, base)
+    C = inputs.random_clifford_gates(N, 64, 78)
+    psi2 = oracle.circuit_state(N, np.concatenate([base, C]))
+    a = sre.sre_exact(dev(psi))
+    b = sre.sre_exact(dev(psi2))
+    assert np.max(np.abs(np.array(a["M"]) - b["M"])) < 2 * TOL_M
+    assert a["nullity"] == b["nullity"] <= 6
+
+
+def test_nullity_entry_point(sre):
+    nu, cnt = sre.stabilizer_nullity(dev(inputs.t_product_state(12, 5)))
+    assert nu == 5 and cnt == 1 << 7
+
+
+def test_zero_state_rejected(sre):
+    with pytest.raises(sre.SreError) as e:
+        sre.sre_exact(torch.zeros(1 << 6, dtype=torch.complex64, device="cuda"))
+    assert e.value.status == sre.SRE_EZERO
+
+
+def test_unnormalised_input(sre):
+    psi = inputs.unnormalised_gaussian_state(9, 3, scale=7.0)
+    _check_exact(sre.sre_exact(dev(psi), allow_nullity_error=True), oracle.sre_exact(psi), 9)
+
+
+# -------------------------------------------------------------- marginal
+@pytest.mark.parametrize("N", [1, 2, 5, 10, 13, 14, 16])
+def test_marginal_vs_oracle(sre, N):
+    psi = inputs.unnormalised_gaussian_state(N, 500 + N)
+    p = sre.pauli_x_marginal(dev(psi)).cpu().numpy()
+    ref = oracle.x_marginal(psi)
+    assert np.max(np.abs(p - ref)) < 1e-12
+    assert abs(p.sum() - 1) < 1e-10
+
+
+def test_marginal_n24_sampled(sre):
+    N = 24
+    psi = inputs.haar_state(N, 24)
+    p = sre.pauli_x_marginal(dev(psi)).cpu().numpy()
+    assert abs(p.sum() - 1) < 1e-9
+    for x in (0, 1, 12345, (1 << 24) - 1):
+        assert abs(p[x] - oracle.x_marginal_one(psi, x)) < 1e-15 + 1e-9 * abs(p[x])
+
+
+# -------------------------------------------------------------------- MC
+@pytest.mark.parametrize("N", [6, 12, 16])
+def test_mc_uniform_vs_oracle(sre, N):
+    psi = oracle.circuit_state(N, inputs.random_clifford_tdoped_gates(N, 8 * N, 4, 600 + N))
+    n_x = 24
+    r = sre.sre_mc(dev(psi), sre.SRE_MC_UNIFORM, n_x, 1, seed=11, counter0=3, return_samples=True)
+    ref = oracle.mc_uniform(psi, n_x, 11, 3)
+    assert np.array_equal(r["xs"].cpu().numpy().astype(np.uint64), ref["xs"])
+    assert np.max(np.abs(np.array(r["M"]) - ref["M"])) < TOL_M
+    assert np.allclose(r["err_M"], ref["err"], rtol=1e-3, atol=1e-9)
+
+
+@pytest.mark.parametrize("N,n_x,zpx", [(4, 16, 8), (10, 12, 16), (14, 6, 8), (16, 6, 8)])
+def test_mc_marginal_vs_oracle(sre, N, n_x, zpx):
+    psi = oracle.circuit_state(N, inputs.random_clifford_tdoped_gates(N, 8 * N, 3, 700 + N))
+    r = sre.sre_mc(dev(psi), sre.SRE_MC_MARGINAL, n_x, zpx, seed=21, counter0=0, return_samples=True)
+    ref = oracle.mc_marginal(psi, n_x, zpx, 21, 0)
+    xs = r["xs"].cpu().numpy().astype(np.uint64)
+    zs = r["zs"].cpu().numpy().astype(np.uint64)
+    c = r["c"].cpu().numpy()
+    assert np.array_equal(xs, ref["xs"])
+    assert np.array_equal(zs, ref["zs"])
+    assert np.max(np.abs(c - ref["c"])) < TOL_C
+    assert np.max(np.abs(np.array(r["M"]) - ref["M"])) < TOL_M
+    assert np.max(np.abs(np.array(r["M_rb"]) - ref["M_rb"])) < TOL_M
+
+
+def test_mc_marginal_stabilizer_exact_zero(sre):
+    N = 12
+    psi = oracle.circuit_state(N, inputs.random_clifford_gates(N, 96, 41))
+    r = sre.sre_mc(dev(psi), sre.SRE_MC_MARGINAL, 32, 16, seed=2, return_samples=True)
+    assert np.max(np.abs(r["M"])) < TOL_M and np.max(np.abs(r["M_rb"])) < TOL_M
+    assert np.allclose(np.abs(r["c"].cpu().numpy()), 1.0, atol=TOL_C)
+
+
+def test_mc_n24_full_size_sampled(sre):
+    """The headline workload's shape (N=24 Haar, x from p(x), z from the
+    family spectrum) on a small x batch: sampled indices against the oracle's
+    inverse-CDF draws, sampled c against brute force, M_2 against the Haar
+    closed form."""
+    N = 24
+    psi = inputs.haar_state(N, 24)
+    n_x, zpx = 48, 16
+    r = sre.sre_mc(dev(psi), sre.SRE_MC_MARGINAL, n_x, zpx, seed=24, return_samples=True)
+    xs = r["xs"].cpu().numpy().astype(np.uint64)
+    zs = r["zs"].cpu().numpy().astype(np.uint64)
+    c = r["c"].cpu().numpy()
+    p = oracle.x_marginal(psi)
+    for i in range(n_x):
+        assert int(xs[i]) == oracle.inverse_cdf(p, oracle.mc_draw(24, 0, i, 0))
+    for i in (0, 7):
+        cf = oracle.family_spectrum(psi, int(xs[i]))
+        w = cf * cf
+        for k in range(zpx):
+            assert int(zs[i, k]) == oracle.inverse_cdf(w, oracle.mc_draw(24, 0, i, 1 + k))
+    for i, k in ((1, 0), (5, 3), (40, 15)):
+        assert abs(c[i, k] - oracle.pauli_expectation(psi, int(xs[i]), int(zs[i, k]))) < TOL_C
+    m2_haar = math.log2(2**N + 3) - 2
+    assert abs(r["M_rb"][1] - m2_haar) < 4 * r["err_rb"][1] + 1e-4
+    assert abs(r["M"][1] - m2_haar) < 5 * r["err_M"][1] + 1e-3
+
+
+# ----------------------------------------------------------------- gates
+@pytest.mark.parametrize("N,n", [(1, 20), (3, 40), (5, 60), (8, 120), (12, 200), (14, 200), (17, 300)])
+def test_gates_vs_oracle(sre, N, n):
+    g = np.random.default_rng(N)
+    rows = []
+    for _ in range(n):
+        op = int(g.integers(0, 6)) if N > 1 else int(g.choice([0, 1, 2, 4, 5]))
+        q0 = int(g.integers(0, N))
+        q1 = int((q0 + 1 + g.integers(0, N - 1)) % N) if op == inputs.GATE_CNOT else 0
+        rows.append((op, q0, q1))
+    gates = np.array(rows, dtype=np.uint8)
+    psi = inputs.haar_state(N, 800 + N)
+    want = oracle.apply_gates(psi, gates)
+    p = dev(psi)
+    sre.apply_clifford_tdoped_circuit(p, gates)
+    got = p.cpu().numpy()
+    assert np.max(np.abs(got - want)) < 2e-6 * math.sqrt(n) + 1e-6
+
+
+def test_gates_then_exact_matches_oracle_pipeline(sre):
+    """The N=10 T-doped workload prepared on the GPU from |0^10>."""
+    gates = inputs.workload_n10_states()["tdoped_gates"]
+    p = torch.zeros(1 << 10, dtype=torch.complex64, device="cuda")
+    p[0] = 1
+    sre.apply_clifford_tdoped_circuit(p, gates)
+    ref = oracle.sre_exact(oracle.circuit_state(10, gates))
+    r = sre.sre_exact(p, allow_nullity_error=True)
+    assert np.max(np.abs(np.array(r["M"]) - ref["M"])) < TOL_M
+    assert r["nullity"] == ref["nullity"]
