@@ -396,13 +396,25 @@ int or_mc_uniform(const float *psi, int N, long long n_x, uint64_t seed, uint64_
     return 0;
 }
 
-/* Sampling of P ~ pi(P) = c_P^2/d through its x-marginal: x ~ p(x) by the
- * inverse CDF of p in natural x order, then z ~ c_{x,z}^2/(d p(x)) by the
- * inverse CDF of c_{x,.}^2 in natural z order.  The estimators:
- *   z-sample:  S_a = mean of c^{2a-2} over all drawn (x, z); M_a = log2 S_a/(1-a),
- *              M_1 = -mean log2 c^2;  err from the spread of the per-x means.
- *   per-family (Rao-Blackwell): the same, with the mean over z|x replaced by
- *              its exact value sum_z c^{2a}/sum_z c^2.
+/* Sampling of P ~ pi(P) = c_P^2/d through its x-marginal, with x = 0 as
+ * its own stratum. SM Sec. I treats the x = 0 family separately because the
+ * identity makes it atypical (for Haar states its weight is comparable to all
+ * other strings together); under pi the x = 0 family has probability
+ * p(0) ~ 2/d, so a plain draw of x ~ p(x) almost never visits it and the
+ * estimate is off by that family's share. Hence:
+ *   family 0 is x = 0, evaluated exactly (its conditional means over z);
+ *   families 1..n_x-1 draw x ~ p(x | x != 0) by the inverse CDF of p over
+ *   x >= 1 in natural order, then z ~ c_{x,z}^2/(d p(x)) by the inverse CDF
+ *   of c_{x,.}^2 in natural z order (z is drawn for family 0 too, and
+ *   reported, but not used by the estimators).
+ * For g in {-log2 c^2, c^2, c^4}: E_pi[g] = p(0) G_0 + (1 - p(0)) E[g | x != 0],
+ *   z-sample estimator:  E[g | x != 0] ~ mean over families of the mean of g
+ *                        over its z draws;
+ *   per-family (Rao-Blackwell): the same with each family's exact conditional
+ *                        mean sum_z c^2 g / sum_z c^2.
+ * M_1 = E_pi[-log2 c^2]; M_a = log2(E_pi[c^{2a-2}])/(1-a) (a = 2, 3; SM Sec. III
+ * with its "- N" read out, see the header). err: standard error from the
+ * spread of the per-family values (the z draws of one family share x).
  * M, err, M_rb, err_rb: [3]. xs: [n_x]; zs: [n_x * z_per_x]; c_s: the drawn
  * c values [n_x * z_per_x]. Any of xs, zs, c_s may be NULL. */
 int or_mc_marginal(const float *psi, int N, long long n_x, int z_per_x, uint64_t seed,
@@ -417,11 +429,17 @@ int or_mc_marginal(const float *psi, int N, long long n_x, int z_per_x, uint64_t
     cplx *w = (cplx *)malloc(d * sizeof(cplx));
     if (!p || !c || !w || !w2) { free(p); free(c); free(w); free(w2); return -1; }
     or_x_marginal_wht(psi, N, p);
+    const double p0 = p[0];
+    p[0] = 0.0;                      /* weights of x >= 1 */
+    double g0[3] = {0, 0, 0};
     ksum zs_sum[3] = {{0, 0}, {0, 0}, {0, 0}}, zs_sq[3] = {{0, 0}, {0, 0}, {0, 0}};
     ksum rb_sum[3] = {{0, 0}, {0, 0}, {0, 0}}, rb_sq[3] = {{0, 0}, {0, 0}, {0, 0}};
     for (long long i = 0; i < n_x; ++i) {
-        double ux = or_mc_uniform_draw(seed, ctr0, (uint64_t)i, 0);
-        uint64_t x = or_inverse_cdf(p, d, ux);
+        uint64_t x = 0;
+        if (i > 0) {
+            double ux = or_mc_uniform_draw(seed, ctr0, (uint64_t)i, 0);
+            x = or_inverse_cdf(p, d, ux);
+        }
         if (xs) xs[i] = x;
         or_family_spectrum(psi, N, x, s, c, NULL, w);
         for (uint64_t z = 0; z < d; ++z) w2[z] = c[z] * c[z];
@@ -441,12 +459,13 @@ int or_mc_marginal(const float *psi, int N, long long n_x, int z_per_x, uint64_t
         family_moments(c, d, 0.0, m, &cnt);
         double rb[3] = {-m[3] / m[0], m[1] / m[0], m[2] / m[0]};
         for (int a = 0; a < 3; ++a) {
+            if (i == 0) { g0[a] = rb[a]; continue; }
             double y = fam[a] / z_per_x;
             kadd(&zs_sum[a], y); kadd(&zs_sq[a], y * y);
             kadd(&rb_sum[a], rb[a]); kadd(&rb_sq[a], rb[a] * rb[a]);
         }
     }
-    double n = (double)n_x;
+    double n = (double)(n_x - 1);
     for (int a = 0; a < 3; ++a) {
         for (int which = 0; which < 2; ++which) {
             ksum *su = which ? &rb_sum[a] : &zs_sum[a];
@@ -454,13 +473,14 @@ int or_mc_marginal(const float *psi, int N, long long n_x, int z_per_x, uint64_t
             double mean = kval(su) / n;
             double var = kval(sq) / n - mean * mean;
             if (var < 0) var = 0;
-            double se = sqrt(var / n);
+            double S = p0 * g0[a] + (1.0 - p0) * mean;
+            double se = (1.0 - p0) * sqrt(var / n);
             double Mv, ev;
-            if (a == 0) { Mv = mean; ev = se; }
+            if (a == 0) { Mv = S; ev = se; }
             else {
                 double alpha = (double)(a + 1);
-                Mv = log2(mean) / (1.0 - alpha);
-                ev = se / (mean * fabs(1.0 - alpha) * log(2.0));
+                Mv = log2(S) / (1.0 - alpha);
+                ev = se / (S * fabs(1.0 - alpha) * log(2.0));
             }
             if (which) { M_rb[a] = Mv; err_rb[a] = ev; }
             else { M[a] = Mv; err[a] = ev; }

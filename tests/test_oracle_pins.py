@@ -303,13 +303,19 @@ def test_inverse_cdf_definition():
 
 
 def test_mc_marginal_draw_frequencies():
+    """Families 1.. draw x ~ p(x | x != 0)."""
     N = 3
     psi = inputs.haar_state(N, 77)
     p = oracle.x_marginal(psi)
-    r = oracle.mc_marginal(psi, 4000, 1, seed=5)
-    counts = np.bincount(r["xs"].astype(np.int64), minlength=1 << N)
-    chi2 = np.sum((counts - 4000 * p) ** 2 / (4000 * p))
-    assert chi2 < 30   # 7 dof; P(chi2 > 30) ~ 1e-4
+    r = oracle.mc_marginal(psi, 4001, 1, seed=5)
+    assert r["xs"][0] == 0
+    counts = np.bincount(r["xs"][1:].astype(np.int64), minlength=1 << N)
+    q = p.copy()
+    q[0] = 0
+    q /= q.sum()
+    assert counts[0] == 0
+    chi2 = np.sum((counts[1:] - 4000 * q[1:]) ** 2 / (4000 * q[1:]))
+    assert chi2 < 28   # 6 dof; P(chi2 > 28) ~ 1e-4
 
 
 def test_mc_marginal_pairs_are_inverse_cdf_draws():
@@ -317,9 +323,10 @@ def test_mc_marginal_pairs_are_inverse_cdf_draws():
     psi = oracle.circuit_state(N, inputs.random_clifford_tdoped_gates(N, 30, 3, 4))
     r = oracle.mc_marginal(psi, 6, 4, seed=9, ctr0=17)
     p = oracle.x_marginal(psi)
+    p[0] = 0.0
     for i in range(6):
         x = int(r["xs"][i])
-        assert x == oracle.inverse_cdf(p, oracle.mc_draw(9, 17, i, 0))
+        assert x == (0 if i == 0 else oracle.inverse_cdf(p, oracle.mc_draw(9, 17, i, 0)))
         c = oracle.family_spectrum(psi, x)
         for k in range(4):
             z = int(r["zs"][i, k])
@@ -344,6 +351,22 @@ def test_mc_marginal_unbiased():
     est_rb = [2.0 ** (-oracle.mc_marginal(psi, 8, 1, seed=s)["M_rb"][1]) for s in range(300)]
     for e in (np.array(est), np.array(est_rb)):
         assert abs(e.mean() - want) < 4 * e.std() / np.sqrt(len(e)) + 1e-12
+
+
+def test_mc_marginal_haar_needs_the_x0_stratum():
+    """For a Haar state the identity alone holds about a quarter of
+    sum_P c^4 while p(0) ~ 2/d: with x = 0 as its own stratum the estimate of
+    M_2 sits on the closed form log2(d+3) - 2 (SM Sec. I reasoning)."""
+    N = 14
+    psi = inputs.haar_state(N, 14)
+    r = oracle.mc_marginal(psi, 120, 4, seed=7)
+    m2 = math.log2((1 << N) + 3) - 2
+    assert abs(r["M_rb"][1] - m2) < 4 * r["err_rb"][1] + 0.01
+    assert abs(r["M"][1] - m2) < 4 * r["err"][1] + 0.02
+    # what the stratum adds: the x = 0 family's share of sum c^4
+    c0 = oracle.family_spectrum(psi, 0)
+    share = np.sum(c0**4) / (4.0 * (1 << N) / ((1 << N) + 3))   # sum_P c^4 = 4d/(d+3)
+    assert 0.2 < share < 0.3
 
 
 def test_mc_uniform_unbiased():
