@@ -169,9 +169,14 @@ SRE_API sre_status sre_exact_batched(const void *const *psi_ptrs_host, const int
  * mode SRE_MC_UNIFORM: the SM Sec. I estimator -- x = 0 always and n_x - 1
  *   draws of x uniform on {1..d-1}; S_hat = m_0 + (d-1)/(n_x-1) sum m_x;
  *   err_M from Eq. stdM. z_per_x is ignored.
- * mode SRE_MC_MARGINAL: x ~ p(x) (inverse CDF of the exact marginal in
- *   natural x order), then z_per_x draws z ~ c_{x,z}^2/(d p(x)) (inverse CDF
- *   in natural z order); M_a = log2(mean c^{2a-2})/(1-a), M_1 = -mean log2 c^2.
+ * mode SRE_MC_MARGINAL: family 0 is x = 0, evaluated exactly (its own
+ *   stratum, as the SM Sec. I estimator treats it); families 1..n_x-1 draw
+ *   x ~ p(x | x != 0) (inverse CDF of the exact marginal over x >= 1 in
+ *   natural order); every family then draws z_per_x z ~ c_{x,z}^2/(d p(x))
+ *   (inverse CDF in natural z order). For g in {-log2 c^2, c^2, c^4},
+ *   E_pi[g] = p(0) G_0 + (1 - p(0)) mean_i Y_i with Y_i the mean of g over
+ *   family i's z draws (M, err_M) or its exact conditional mean (M_rb,
+ *   err_rb); M_1 = E_pi[-log2 c^2], M_a = log2(E_pi[c^{2a-2}])/(1-a).
  * Random numbers: word 0 of Philox4x64-10 with key (seed, 0) and counter
  * (counter0 + i, lane, 0, 0); lane 0 gives family i's x, lane 1+k its k-th z;
  * u = (word >> 11) 2^-53.

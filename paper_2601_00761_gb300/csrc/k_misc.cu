@@ -300,11 +300,15 @@ __global__ void draw_x_kernel(const double *cdf, int N, long long n_x, int mode,
     const unsigned long long d = 1ULL << N;
     const double u = mc_uniform(seed, ctr0, (unsigned long long)i, 0ULL);
     unsigned long long x;
-    if (mode == 0) {   // uniform: x = 0 first, then 1 + floor(u (d - 1))
-        x = (i == 0) ? 0ULL : 1ULL + (unsigned long long)(u * (double)(d - 1));
+    if (i == 0) {
+        x = 0ULL;          // x = 0 is its own stratum in both modes (SM Sec. I)
+    } else if (mode == 0) {   // uniform on 1..d-1
+        x = 1ULL + (unsigned long long)(u * (double)(d - 1));
         if (x >= d) x = d - 1;
-    } else {
-        x = cdf_search(cdf, d, u * cdf[d - 1]);
+    } else {                  // x ~ p(x | x != 0): inverse CDF over x >= 1
+        const double c0 = cdf[0];
+        x = cdf_search(cdf, d, c0 + u * (cdf[d - 1] - c0));
+        if (x == 0) x = 1;
     }
     xs[i] = x;
 }
@@ -364,7 +368,8 @@ cudaError_t launch_zrange_select(double *W, long long nr, long long n_fam, long 
 // ------------------------------------------------------------ MC statistics
 // Per family i: y[i][0..2] = mean over its z-draws of (-log2 c^2, c^2, c^4);
 // y[i][3..5] = the family's exact conditional means (-sum c^2 log2 c^2,
-// sum c^4, sum c^6) / sum c^2 (marginal mode), or, uniform mode, the SM Sec. I
+// sum c^4, sum c^6) / sum c^2 (marginal mode; family 0, the x = 0 stratum,
+// takes the exact means in both slots), or, uniform mode, the SM Sec. I
 // family values h_x, m_{2;x}, m_{3;x} in y[i][0..2].
 __global__ void mc_family_stats_kernel(const FamMoments *fm, const float *cz, long long n_x, int z_per_x, int N,
                                        int mode, double *y) {
@@ -387,8 +392,9 @@ __global__ void mc_family_stats_kernel(const FamMoments *fm, const float *cz, lo
             a1 += c2;
             a2 += c2 * c2;
         }
-        o[0] = a0 / z_per_x; o[1] = a1 / z_per_x; o[2] = a2 / z_per_x;
         o[3] = -m.m[3] / m.m[0]; o[4] = m.m[1] / m.m[0]; o[5] = m.m[2] / m.m[0];
+        if (i == 0) { o[0] = o[3]; o[1] = o[4]; o[2] = o[5]; }
+        else { o[0] = a0 / z_per_x; o[1] = a1 / z_per_x; o[2] = a2 / z_per_x; }
     }
 }
 
@@ -417,7 +423,7 @@ __global__ void __launch_bounds__(256) mc_totals_kernel(const double *y, long lo
 cudaError_t launch_mc_stats(const FamMoments *fm, const float *cz, long long n_x, int z_per_x, int N, int mode,
                             double *y, double *out, cudaStream_t st) {
     mc_family_stats_kernel<<<(unsigned)((n_x + 127) / 128), 128, 0, st>>>(fm, cz, n_x, z_per_x, N, mode, y);
-    mc_totals_kernel<<<1, 256, 0, st>>>(y, n_x, mode == 0 ? 1 : 0, fm, out);
+    mc_totals_kernel<<<1, 256, 0, st>>>(y, n_x, 1, fm, out);
     return cudaGetLastError();
 }
 

@@ -681,6 +681,8 @@ sre_status sre_mc(const void *psi, int N, int mode, long long n_x, int z_per_x, 
     double h[24];
     CK(cudaMemcpyAsync(h, w.out, 19 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(h + 20, w.scal + SCAL_NORM2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    h[21] = 0.0;
+    if (marg) CK(cudaMemcpyAsync(h + 21, w.p, sizeof(double), cudaMemcpyDeviceToHost, st));   // p(0) = CDF(0)
     if (xs_dev) CK(cudaMemcpyAsync(xs_dev, w.xs, n_x * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
     if (marg && zs_dev)
         CK(cudaMemcpyAsync(zs_dev, w.zs, (size_t)n_x * z_per_x * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
@@ -715,22 +717,25 @@ sre_status sre_mc(const void *psi, int N, int mode, long long n_x, int z_per_x, 
         }
         out->parseval = -1.0;
     } else {
-        const double n = (double)n_x;
+        // x = 0 stratum (exact) + families 1.. drawn from p(x | x != 0)
+        const double n = (double)(n_x - 1);
+        const double p0 = h[21];
         for (int which = 0; which < 2; ++which) {
             for (int k = 0; k < 3; ++k) {
                 const int idx = k + 3 * which;
                 const double mean = h[idx] / n;
                 double var = h[6 + idx] / n - mean * mean;
                 if (var < 0) var = 0;
-                const double se = std::sqrt(var / n);
+                const double S = p0 * h[12 + idx] + (1.0 - p0) * mean;
+                const double se = (1.0 - p0) * std::sqrt(var / n);
                 double Mv, ev;
-                if (k == 0) { Mv = mean; ev = se; }
+                if (k == 0) { Mv = S; ev = se; }
                 else {
                     const double alpha = k + 1.0;
-                    Mv = std::log2(mean) / (1.0 - alpha);
-                    ev = se / (mean * std::fabs(1.0 - alpha) * std::log(2.0));
+                    Mv = std::log2(S) / (1.0 - alpha);
+                    ev = se / (S * std::fabs(1.0 - alpha) * std::log(2.0));
                 }
-                if (which == 0) { out->M[k] = Mv; out->err_M[k] = ev; out->S[k] = mean; }
+                if (which == 0) { out->M[k] = Mv; out->err_M[k] = ev; out->S[k] = S; }
                 else { out->M_rb[k] = Mv; out->err_rb[k] = ev; }
             }
         }
