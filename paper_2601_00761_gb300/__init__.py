@@ -25,7 +25,8 @@ __all__ = ["sre_version", "sre_last_error", "sre_default_opts", "sre_make_plan",
            "lib_path", "load"]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_PKG, "libsre.so")
+# SRE_LIBRARY selects another build of the same library (e.g. a tuning variant)
+_LIB_PATH = os.environ.get("SRE_LIBRARY") or os.path.join(_PKG, "libsre.so")
 
 SRE_OK, SRE_EINVAL, SRE_ENOMEM, SRE_ECUDA, SRE_EZERO, SRE_ENULLITY, SRE_ETIMEOUT, SRE_ENOTSUP = range(8)
 STATUS_NAMES = {0: "SRE_OK", 1: "SRE_EINVAL", 2: "SRE_ENOMEM", 3: "SRE_ECUDA", 4: "SRE_EZERO",

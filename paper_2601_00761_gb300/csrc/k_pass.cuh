@@ -20,14 +20,6 @@ namespace sre {
 
 __device__ __forceinline__ int sgn_phase(int k) { return (((k + 1) >> 1) & 1) ? -1 : 1; }
 
-template <typename R> __device__ __forceinline__ R log2_any(R v);
-template <> __device__ __forceinline__ float log2_any<float>(float v) { return log2f(v); }
-template <> __device__ __forceinline__ double log2_any<double>(double v) { return log2(v); }
-
-template <typename R> struct RealMin;
-template <> struct RealMin<float> { static constexpr float v = 1.17549435e-38f; };
-template <> struct RealMin<double> { static constexpr double v = 2.2250738585072014e-308; };
-
 // Sum over the T threads of a group; the result is valid in the group's thread 0.
 // red: shared scratch of at least NT/32 doubles. All threads of the CTA call it.
 template <int T, int NT>
@@ -44,9 +36,8 @@ __device__ __forceinline__ double group_sum(double v, double *red) {
             __syncthreads();
             double s = 0.0;
             if ((threadIdx.x & (T - 1)) == 0) {
-                const int w0 = w;
 #pragma unroll 1
-                for (int i = 0; i < T / 32; ++i) s += red[w0 + i];
+                for (int i = 0; i < T / 32; ++i) s += red[w + i];
             }
             return s;
         }
@@ -55,6 +46,66 @@ __device__ __forceinline__ double group_sum(double v, double *red) {
         for (int o = T / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         return v;
     }
+}
+
+// NV sums and one maximum over the T threads of a group: FP32 butterfly
+// inside the warp, FP64 across the group's warps (fixed order). Results are
+// valid in the group's thread 0. red: NV * NT/32 doubles + NT/32 floats of
+// shared scratch. Two barriers when a group spans several warps.
+template <int T, int NT, int NV>
+__device__ __forceinline__ void group_reduce(float (&v)[NV], float &mx, double (&out)[NV], float &omx,
+                                             double *red) {
+    constexpr int W = T < 32 ? T : 32;
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if constexpr (T <= 32) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) out[i] = (double)v[i];
+        omx = mx;
+    } else {
+        constexpr int NW = NT / 32;
+        float *redm = reinterpret_cast<float *>(red + NV * NW);
+        const int w = threadIdx.x >> 5;
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) red[i * NW + w] = (double)v[i];
+            redm[w] = mx;
+        }
+        __syncthreads();
+        if ((threadIdx.x & (T - 1)) == 0) {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) {
+                double s = 0.0;
+#pragma unroll 1
+                for (int q = 0; q < T / 32; ++q) s += red[i * NW + w + q];
+                out[i] = s;
+            }
+            float m = 0.f;
+#pragma unroll 1
+            for (int q = 0; q < T / 32; ++q) m = fmaxf(m, redm[w + q]);
+            omx = m;
+        }
+    }
+}
+
+// bit k of the result = parity(a & k), k < 32 (the Walsh function of a)
+__device__ __forceinline__ uint32_t walsh_mask5(uint32_t a) {
+    uint32_t m = 0;
+    if (a & 1u) m ^= 0xAAAAAAAAu;
+    if (a & 2u) m ^= 0xCCCCCCCCu;
+    if (a & 4u) m ^= 0xF0F0F0F0u;
+    if (a & 8u) m ^= 0xFF00FF00u;
+    if (a & 16u) m ^= 0xFFFF0000u;
+    return m;
+}
+
+__device__ __forceinline__ float xlog2x(float q) {
+    return q >= 1.17549435e-38f ? q * __log2f(q) : 0.0f;
 }
 
 // Packed global index of tile element e (see PassArgs::lo_g and TileCfg).
@@ -72,22 +123,43 @@ __device__ __forceinline__ void pass_prologue(typename Cfg::C2 (&v)[Cfg::E], con
     typedef typename Cfg::C2 C2;
     constexpr int A0 = Maps<Cfg>::first;
     if constexpr (SRC == SRC_PSI_FAMILY) {
+        // loads issued in batches of LB slots (2 LB independent 8-byte loads in
+        // flight per thread) before any of them is used
+        constexpr int LB = Cfg::E < 8 ? Cfg::E : 8;
+        if (x != 0) {
 #pragma unroll
-        for (int k = 0; k < Cfg::E; ++k) {
-            const unsigned long long g = tile_gidx<Cfg>(gbase, a.lo_g, Cfg::elem(t, k, A0));
-            if (x != 0) {
-                const unsigned long long b = insert0(g, j);
-                const float2 u = __ldg(a.psi + b);
-                const float2 w = __ldg(a.psi + (b ^ x));
-                const R ux = u.x, uy = u.y, wx = w.x, wy = w.y;
-                v[k].x = fma(wx, ux, wy * uy);     // conj(w) * u, contraction fixed
-                v[k].y = fma(wx, uy, -(wy * ux));
-            } else {
-                const float2 u = __ldg(a.psi + g);
-                const float2 w = __ldg(a.psi + (g | half));
-                const R ux = u.x, uy = u.y, wx = w.x, wy = w.y;
-                v[k].x = fma(ux, ux, uy * uy);
-                v[k].y = fma(wx, wx, wy * wy);
+            for (int k0 = 0; k0 < Cfg::E; k0 += LB) {
+                float2 u[LB], w[LB];
+#pragma unroll
+                for (int q = 0; q < LB; ++q) {
+                    const unsigned long long g = tile_gidx<Cfg>(gbase, a.lo_g, Cfg::elem(t, k0 + q, A0));
+                    const unsigned long long b = insert0(g, j);
+                    u[q] = __ldg(a.psi + b);
+                    w[q] = __ldg(a.psi + (b ^ x));
+                }
+#pragma unroll
+                for (int q = 0; q < LB; ++q) {
+                    const R ux = u[q].x, uy = u[q].y, wx = w[q].x, wy = w[q].y;
+                    v[k0 + q].x = fma(wx, ux, wy * uy);     // conj(w) * u, contraction fixed
+                    v[k0 + q].y = fma(wx, uy, -(wy * ux));
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k0 = 0; k0 < Cfg::E; k0 += LB) {
+                float2 u[LB], w[LB];
+#pragma unroll
+                for (int q = 0; q < LB; ++q) {
+                    const unsigned long long g = tile_gidx<Cfg>(gbase, a.lo_g, Cfg::elem(t, k0 + q, A0));
+                    u[q] = __ldg(a.psi + g);
+                    w[q] = __ldg(a.psi + (g | half));
+                }
+#pragma unroll
+                for (int q = 0; q < LB; ++q) {
+                    const R ux = u[q].x, uy = u[q].y, wx = w[q].x, wy = w[q].y;
+                    v[k0 + q].x = fma(ux, ux, uy * uy);
+                    v[k0 + q].y = fma(wx, wx, wy * wy);
+                }
             }
         }
     } else if constexpr (SRC == SRC_PSI_Q) {
@@ -127,7 +199,7 @@ __device__ __forceinline__ void family_pair(unsigned long long x, int j, R s, C2
 }
 
 template <class Cfg, int SRC, int DST>
-__global__ void __launch_bounds__(Cfg::NT) fwht_pass_kernel(const PassArgs a) {
+__global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const PassArgs a) {
     typedef typename Cfg::Real R;
     typedef typename Cfg::C2 C2;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -239,43 +311,67 @@ __global__ void __launch_bounds__(Cfg::NT) fwht_pass_kernel(const PassArgs a) {
         cnt = group_sum<Cfg::T, Cfg::NT>(cnt, red);
         if (active && t == 0 && cnt > 0.0) atomicAdd(a.count_out + slot, (unsigned long long)cnt);
     } else if constexpr (DST == DST_MOMENTS) {
-        const R s = (R)(*a.s_ptr);
+        static_assert(Cfg::LO == 0 && AL == 0, "moments epilogue runs on last-pass tiles");
+        // z' = zb | k for slot k (last mapping: slot bits are the low RB bits)
+        const float s = (float)(*a.s_ptr);
         const int RL = a.range_log2;
-        const unsigned long long zt = tile << Cfg::M;   // first z' of the tile (last pass: lo_g = 0, LO = 0)
-        const unsigned long long rA = insert0(zt, j) >> RL;
-        const R thr = (R)a.cand_thr;
-        const R thr2 = thr * thr;
-        R s2 = 0, s4 = 0, s6 = 0, sl = 0, w0 = 0, w1 = 0;
-        int cand = 0;
+        const uint32_t zb = (uint32_t)gbase | Cfg::elem(t, 0, 0);
+        float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // c^2, c^4, c^6, c^2 log2 c^2, w_A, w_B
+        float qmax = 0.f;
+        if (x) {
+            const float sc = 2.0f * s;
+            const uint32_t xd = (uint32_t)((x & ((1ULL << j) - 1ULL)) | ((x >> (j + 1)) << j));
+            // bit k: parity of |x & z0| for z' = zb | k (z0 = z' with 0 inserted at bit j)
+            const uint32_t pm = walsh_mask5(xd & (Cfg::E - 1)) ^ ((__popc(xd & zb) & 1) ? 0xFFFFFFFFu : 0u);
+            const bool wr = a.want_ranges;
+            const bool jge = j >= RL;
 #pragma unroll
-        for (int k = 0; k < Cfg::E; ++k) {
-            unsigned long long z0, z1;
-            R c0, c1;
-            family_pair<R, C2>(x, j, s, v[k], gidx(Cfg::elem(t, k, AL)), z0, z1, c0, c1);
-            const R q0 = c0 * c0, q1 = c1 * c1;
-            const R q0q = q0 * q0, q1q = q1 * q1;
-            s2 += q0 + q1;
-            s4 += q0q + q1q;
-            s6 += q0q * q0 + q1q * q1;
-            if (q0 >= RealMin<R>::v) sl += q0 * log2_any<R>(q0);
-            if (q1 >= RealMin<R>::v) sl += q1 * log2_any<R>(q1);
-            cand += (q0 > thr2) + (q1 > thr2);
-            if ((z0 >> RL) == rA) w0 += q0; else w1 += q0;
-            if ((z1 >> RL) == rA) w0 += q1; else w1 += q1;
+            for (int k = 0; k < Cfg::E; ++k) {
+                const float re = sc * v[k].x, im = sc * v[k].y;
+                const float rr = re * re, ii = im * im;
+                const float r2 = rr * rr, i2 = ii * ii;
+                acc[0] += rr + ii;
+                acc[1] += r2 + i2;
+                acc[2] += r2 * rr + i2 * ii;
+                acc[3] += xlog2x(rr) + xlog2x(ii);
+                qmax = fmaxf(qmax, fmaxf(rr, ii));
+                if (wr) {
+                    if (jge) {
+                        const bool odd = (pm >> k) & 1u;   // z0 carries Im when odd
+                        acc[4] += odd ? ii : rr;
+                        acc[5] += odd ? rr : ii;
+                    } else {
+                        const bool hi = ((zb | (uint32_t)k) >> (RL - 1)) & 1u;
+                        const float q = rr + ii;
+                        acc[4] += hi ? 0.f : q;
+                        acc[5] += hi ? q : 0.f;
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < Cfg::E; ++k) {
+                const float c0 = s * (v[k].x + v[k].y), c1 = s * (v[k].x - v[k].y);
+                const float q0 = c0 * c0, q1 = c1 * c1;
+                const float r2 = q0 * q0, i2 = q1 * q1;
+                acc[0] += q0 + q1;
+                acc[1] += r2 + i2;
+                acc[2] += r2 * q0 + i2 * q1;
+                acc[3] += xlog2x(q0) + xlog2x(q1);
+                qmax = fmaxf(qmax, fmaxf(q0, q1));
+                acc[4] += q0;      // z' -> range A, z' + d/2 -> range B
+                acc[5] += q1;
+            }
         }
-        double r2 = group_sum<Cfg::T, Cfg::NT>((double)s2, red);
-        double r4 = group_sum<Cfg::T, Cfg::NT>((double)s4, red);
-        double r6 = group_sum<Cfg::T, Cfg::NT>((double)s6, red);
-        double rl = group_sum<Cfg::T, Cfg::NT>((double)sl, red);
-        double rw0 = group_sum<Cfg::T, Cfg::NT>((double)w0, red);
-        double rw1 = group_sum<Cfg::T, Cfg::NT>((double)w1, red);
-        double rc = group_sum<Cfg::T, Cfg::NT>((double)cand, red);
+        double out[6];
+        float omx;
+        group_reduce<Cfg::T, Cfg::NT, 6>(acc, qmax, out, omx, red);
         if (active && t == 0) {
             const long long tiles = (long long)(half >> Cfg::M) > 0 ? (long long)(half >> Cfg::M) : 1;
             TilePartial &tp = a.tile_out[(size_t)slot * (size_t)tiles + tile];
-            tp.m[0] = r2; tp.m[1] = r4; tp.m[2] = r6; tp.m[3] = rl;
-            tp.w[0] = rw0; tp.w[1] = rw1;
-            tp.cand = (unsigned int)rc;
+            tp.m[0] = out[0]; tp.m[1] = out[1]; tp.m[2] = out[2]; tp.m[3] = out[3];
+            tp.w[0] = out[4]; tp.w[1] = out[5];
+            tp.cand = omx > a.cand_thr * a.cand_thr ? 1u : 0u;
         }
     }
 }
@@ -283,7 +379,7 @@ __global__ void __launch_bounds__(Cfg::NT) fwht_pass_kernel(const PassArgs a) {
 template <class Cfg, int SRC, int DST>
 cudaError_t launch_cfg(const PassArgs &a, int tiles, cudaStream_t st) {
     const size_t tile_smem = Cfg::NR > 1 ? sizeof(typename Cfg::C2) * (size_t)Cfg::G * Cfg::SIZE : 0;
-    const size_t smem = tile_smem + sizeof(double) * (Cfg::NT / 32 + 1);
+    const size_t smem = tile_smem + sizeof(double) * (8 * (Cfg::NT / 32) + 8);
     static bool attr_done = false;
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(fwht_pass_kernel<Cfg, SRC, DST>,

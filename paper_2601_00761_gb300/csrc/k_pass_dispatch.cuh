@@ -75,14 +75,16 @@ struct SingleCfgOf {
 };
 
 cudaError_t launch_f32_single(int M, int src, int dst, const PassArgs &a, cudaStream_t st);
-cudaError_t launch_f32_strided(int K, int src, int dst, const PassArgs &a, int tiles, cudaStream_t st);
+cudaError_t launch_f32_strided(int MS, int K, int src, int dst, const PassArgs &a, int tiles, cudaStream_t st);
 cudaError_t launch_f32_row(int M, int src, int dst, const PassArgs &a, int tiles, cudaStream_t st);
 cudaError_t launch_f64_single(int M, int src, int dst, const PassArgs &a, cudaStream_t st);
 cudaError_t launch_f64_strided(int K, int src, int dst, const PassArgs &a, int tiles, cudaStream_t st);
 cudaError_t launch_f64_row(int M, int src, int dst, const PassArgs &a, int tiles, cudaStream_t st);
 
-// strided tile: 2^K rows x 2^(MS-K) columns, MS = 14 (FP32) / 13 (FP64)
-constexpr int F32_STRIDED_M = 14, F32_STRIDED_KMAX = 10, F32_ROW_MMIN = 10, F32_ROW_MMAX = 13, F32_SINGLE_MMAX = 14;
+// strided tile: 2^K rows x 2^(MS-K) columns; FP32 MS = 13 (K <= 9, 64 KB) or
+// 14 (K = 10, 128 KB); FP64 MS = 13 (128 KB)
+constexpr int F32_STRIDED_KMAX = 10, F32_ROW_MMIN = 10, F32_ROW_MMAX = 14, F32_SINGLE_MMAX = 14;
+__host__ __device__ constexpr int f32_strided_ms(int K) { return K + 4 > 13 ? K + 4 : 13; }
 constexpr int F64_STRIDED_M = 13, F64_STRIDED_KMAX = 9, F64_ROW_M = 12, F64_SINGLE_MMAX = 12;
 
 } // namespace sre

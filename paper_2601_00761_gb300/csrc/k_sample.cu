@@ -120,7 +120,7 @@ cudaError_t launch_zsample(int single, int M, const PassArgs &a, const DrawInfo 
     }
     switch (M) {
 #define C(m) case m: return launch_zs<TileCfg<float, m, 0, 5, 1>, SRC_BUF>(a, draws, z_per_x, zs, cz, st);
-    C(10) C(11) C(12) C(13)
+    C(10) C(11) C(12) C(13) C(14)
 #undef C
     default: return cudaErrorInvalidValue;
     }

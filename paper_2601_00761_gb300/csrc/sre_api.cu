@@ -53,9 +53,9 @@ constexpr int EXACT_PARTS = 1024;
 struct Plan {
     int N = 0, n = 0, prec = 32;
     int npass = 1, nstrided = 0;
-    int K[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+    int K[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0}, ms[4] = {0, 0, 0, 0};
     int M_last = 0;
-    long long tiles_strided = 0, tiles_last = 1;
+    long long tiles_last = 1;
     long long B = 1;
     size_t slot_bytes = 0;
 };
@@ -77,21 +77,20 @@ sre_status plan_for(int N, const sre_opts *o, int prec, Plan &P) {
         if (prec == 32 && o && o->x_batch > 0) P.B = o->x_batch;
         return SRE_OK;
     }
-    int nlo, kmax, ms;
+    int nlo, kmax;
     if (prec == 32) {
-        nlo = (o && o->radix_log2 > 0) ? clampi(o->radix_log2, F32_ROW_MMIN, F32_ROW_MMAX) : F32_ROW_MMAX;
+        nlo = (o && o->radix_log2 > 0) ? clampi(o->radix_log2, F32_ROW_MMIN, F32_ROW_MMAX) : 13;
         kmax = (o && o->tile_log2 > 0) ? clampi(o->tile_log2, 1, F32_STRIDED_KMAX) : F32_STRIDED_KMAX;
-        ms = F32_STRIDED_M;
     } else {
         nlo = F64_ROW_M;
         kmax = F64_STRIDED_KMAX;
-        ms = F64_STRIDED_M;
     }
+    auto ms_of = [&](int K) { return prec == 32 ? f32_strided_ms(K) : F64_STRIDED_M; };
     // A strided tile is 2^K rows x 2^(ms-K) columns and its columns must fit
     // below the pass's row stride 2^lo: ms - K <= lo. Only the bottom strided
-    // pass (lo = nlo) can violate it, so it takes the largest K.
+    // pass (lo = nlo) can violate it: K_bottom >= 13 - nlo.
     const int rest = P.n - nlo;
-    const int kmin_bottom = ms - nlo;
+    const int kmin_bottom = 13 - nlo > 1 ? 13 - nlo : 1;
     if (kmax < kmin_bottom) kmax = kmin_bottom;
     int ns = (rest + kmax - 1) / kmax;
     if (ns > 3) return fail(SRE_ENOTSUP, "N=%d needs %d strided passes", N, ns);
@@ -112,11 +111,11 @@ sre_status plan_for(int N, const sre_opts *o, int prec, Plan &P) {
     int top = P.n;
     for (int i = 0; i < ns; ++i) {
         P.lo[i] = top - P.K[i];
+        P.ms[i] = ms_of(P.K[i]);
         top = P.lo[i];
-        if (ms - P.K[i] > P.lo[i]) return fail(SRE_EINVAL, "internal plan error (N=%d pass %d)", N, i);
+        if (P.ms[i] - P.K[i] > P.lo[i]) return fail(SRE_EINVAL, "internal plan error (N=%d pass %d)", N, i);
     }
     P.M_last = nlo;
-    P.tiles_strided = 1LL << (P.n - ms);
     P.tiles_last = 1LL << (P.n - nlo);
     P.slot_bytes = (size_t)(prec == 32 ? 8 : 16) << P.n;
     long long B = (long long)(BATCH_BYTES / P.slot_bytes);
@@ -349,8 +348,9 @@ sre_status run_transform(const Plan &P, PassArgs a, int src0, int dst_last, void
         b.dst = inter;
         const int s = i == 0 ? src0 : SRC_BUF;
         CS(timer_mark(T, i, st, true));
-        e = P.prec == 32 ? launch_f32_strided(P.K[i], s, DST_BUF, b, (int)P.tiles_strided, st)
-                         : launch_f64_strided(P.K[i], s, DST_BUF, b, (int)P.tiles_strided, st);
+        const int tiles = (int)(1LL << (P.n - P.ms[i]));
+        e = P.prec == 32 ? launch_f32_strided(P.ms[i], P.K[i], s, DST_BUF, b, tiles, st)
+                         : launch_f64_strided(P.K[i], s, DST_BUF, b, tiles, st);
         if (e != cudaSuccess)
             return fail(SRE_ECUDA, "strided pass %d (N=%d K=%d): %s", i, P.N, P.K[i], cudaGetErrorString(e));
         count_launches(1);
@@ -648,6 +648,7 @@ sre_status sre_mc(const void *psi, int N, int mode, long long n_x, int z_per_x, 
     PassArgs a = base_args(P, psi, w.scal);
     a.xs = w.xs;
     a.tile_out = w.tiles;
+    a.want_ranges = marg ? 1 : 0;
     const long long step = P.B < n_x ? P.B : n_x;
     const long long nr = 1LL << (N - P.M_last);
     bool timing;

@@ -26,6 +26,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+// CTAs per SM targeted by the register allocation of 256-thread tiles of at
+// most 64 KB (a build-time tuning constant).
+#ifndef SRE_MINB_SMALL
+#define SRE_MINB_SMALL 2
+#endif
+
 namespace sre {
 
 template <typename R> struct V2;
@@ -48,7 +54,7 @@ __host__ __device__ __forceinline__ unsigned long long insert0(unsigned long lon
 struct TilePartial {
     double m[4];
     double w[2];
-    unsigned int cand;
+    unsigned int cand;     // 1 if the tile holds a |c| > 1 - 1e-4
     unsigned int pad;
     double pad2;
 };
@@ -75,6 +81,9 @@ struct TileCfg {
     static constexpr int K = M - LO;
     static constexpr int NR = RB > 0 ? (K + RB - 1) / RB : 0;
     static constexpr int SIZE = 1 << M;
+    // CTAs per SM the register budget is sized for: tiles of at most 64 KB
+    // (FP32 M <= 13) run several per SM so load and compute phases overlap
+    static constexpr int MINB = (G == 1 && sizeof(C2) * SIZE <= 65536 && NT == 256) ? SRE_MINB_SMALL : 1;
     static_assert(TB >= 0, "tile smaller than a thread's registers");
     static_assert(K >= 0, "bad tile");
 
@@ -84,18 +93,22 @@ struct TileCfg {
     // slot bits of the round for range i: [slot_base(i), slot_base(i) + RB)
     __host__ __device__ static constexpr int slot_base(int i) { return range_hi(i) - RB > 0 ? range_hi(i) - RB : 0; }
 
-    // element index of (thread t, slot k) when the slot bits start at a
+    // element index of (thread t, slot k) when the slot bits start at a;
+    // elem(t, k, a) = elem(t, 0, a) ^ (k << a) (disjoint bits)
     __device__ static __forceinline__ uint32_t elem(uint32_t t, uint32_t k, int a) {
         return (t & ((1u << a) - 1u)) | (k << a) | ((t >> a) << (a + RB));
     }
-    // shared-memory position: nibble-fold XOR swizzle (conflict-free when the
-    // 4 lowest thread bits map to element bits with distinct positions mod 4)
-    __device__ static __forceinline__ uint32_t phys(uint32_t e, uint32_t g) {
-        if (M < 5) return (g << M) + e;
-        uint32_t f = ((e >> 4) ^ (e >> 8) ^ (e >> 12) ^ (e >> 16)) & 15u;
-        uint32_t gs = (TB < 4) ? ((g << TB) & 15u) : 0u;
-        return (g << M) + (e ^ f ^ gs);
+    // Shared-memory swizzle: nibble-fold XOR (conflict-free when the 4 lowest
+    // thread bits map to element bits with distinct positions mod 4). It is
+    // linear over GF(2): swz(e1 ^ e2) = swz(e1) ^ swz(e2), so a round's
+    // addresses are one per-thread base XOR a compile-time constant per slot.
+    __host__ __device__ static constexpr uint32_t swz(uint32_t e) {
+        return M < 5 ? e : (e ^ (((e >> 4) ^ (e >> 8) ^ (e >> 12) ^ (e >> 16)) & 15u));
     }
+    __device__ static __forceinline__ uint32_t grp_base(uint32_t g) {
+        return (g << M) ^ ((M >= 5 && TB < 4) ? ((g << TB) & 15u) : 0u);
+    }
+    __device__ static __forceinline__ uint32_t phys(uint32_t e, uint32_t g) { return grp_base(g) ^ swz(e); }
 };
 
 template <typename C2, int E, int S0, int S1>
@@ -119,15 +132,16 @@ struct Rounds {
     static constexpr int i = Cfg::NR - 1 - r;
     static constexpr int a = Cfg::slot_base(i);
     __device__ static __forceinline__ void run(C2 (&v)[Cfg::E], C2 *sm, uint32_t t, uint32_t g) {
+        const uint32_t pb = Cfg::phys(Cfg::elem(t, 0, a), g);
         if constexpr (r > 0) {
             __syncthreads();
 #pragma unroll
-            for (int k = 0; k < Cfg::E; ++k) v[k] = sm[Cfg::phys(Cfg::elem(t, k, a), g)];
+            for (int k = 0; k < Cfg::E; ++k) v[k] = sm[pb ^ Cfg::swz((uint32_t)k << a)];
         }
         butterflies<C2, Cfg::E, Cfg::range_lo(i) - a, Cfg::range_hi(i) - a>(v);
         if constexpr (r < Cfg::NR - 1) {
 #pragma unroll
-            for (int k = 0; k < Cfg::E; ++k) sm[Cfg::phys(Cfg::elem(t, k, a), g)] = v[k];
+            for (int k = 0; k < Cfg::E; ++k) sm[pb ^ Cfg::swz((uint32_t)k << a)] = v[k];
             Rounds<Cfg, r + 1>::run(v, sm, t, g);
         }
     }
@@ -176,6 +190,7 @@ struct PassArgs {
     double *p_out;                     // marginal output p[d]
     double eps;                        // nullity tolerance
     float cand_thr;                    // FP32 candidate threshold
+    int want_ranges;                   // DST_MOMENTS: also produce the z-range weights
     int *err_flag;                     // device error word (bounds checks)
 };
 

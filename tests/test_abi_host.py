@@ -65,11 +65,12 @@ def test_plans(L, N, passes, bits):
 def test_plan_options(L):
     p = sre.sre_make_plan(24, radix_log2=11, tile_log2=6)
     assert p["pass_bits"] == [6, 6, 11]
+    assert sre.sre_make_plan(24, radix_log2=13, tile_log2=10)["pass_bits"] == [10, 13]
     # the bottom strided pass keeps its columns below its row stride
     p = sre.sre_make_plan(18, radix_log2=10, tile_log2=4)
     assert p["pass_bits"] == [3, 4, 10]
     p = sre.sre_make_plan(16, radix_log2=10, tile_log2=2)
-    assert p["pass_bits"] == [1, 4, 10]
+    assert p["pass_bits"] == [2, 3, 10]
     assert sre.sre_make_plan(24, x_batch=3)["x_batch"] == 3
 
 
