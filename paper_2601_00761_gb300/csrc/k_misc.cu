@@ -353,7 +353,10 @@ __global__ void __launch_bounds__(256) zrange_select_kernel(double *W, long long
         const unsigned long long r = cdf_search(w, (unsigned long long)nr, t);
         DrawInfo di;
         di.range = r;
-        di.t = t - (r > 0 ? w[r - 1] : 0.0);
+        const double lo = r > 0 ? w[r - 1] : 0.0;
+        di.t = t - lo;
+        di.wr = w[r] - lo;
+        di.pad = 0.0;
         draws[(size_t)(fam_base + f) * z_per_x + k] = di;
     }
 }

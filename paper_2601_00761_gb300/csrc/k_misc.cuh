@@ -12,6 +12,8 @@ constexpr unsigned long long SCAN_CHUNK = 4096;
 struct DrawInfo {
     unsigned long long range;   // z-range (size 2^RL) of the draw
     double t;                   // target within the range, in units of c^2
+    double wr;                  // the range's weight (sum of its c^2)
+    double pad;
 };
 
 cudaError_t launch_norm2(const float2 *psi, int N, double *scal, double *partial, cudaStream_t st);

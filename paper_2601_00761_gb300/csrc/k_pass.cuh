@@ -104,10 +104,6 @@ __device__ __forceinline__ uint32_t walsh_mask5(uint32_t a) {
     return m;
 }
 
-__device__ __forceinline__ float xlog2x(float q) {
-    return q >= 1.17549435e-38f ? q * __log2f(q) : 0.0f;
-}
-
 // Packed global index of tile element e (see PassArgs::lo_g and TileCfg).
 template <class Cfg>
 __device__ __forceinline__ unsigned long long tile_gidx(unsigned long long gbase, int lo_g, uint32_t e) {
@@ -172,6 +168,12 @@ __device__ __forceinline__ void pass_prologue(typename Cfg::C2 (&v)[Cfg::E], con
             v[k].x = fma(ux, ux, uy * uy);
             v[k].y = fma(wx, wx, wy * wy);
         }
+    } else if constexpr (Cfg::LO == 0) {
+        // contiguous tile (lo_g = 0): one base plus compile-time offsets
+        const C2 *src = reinterpret_cast<const C2 *>(a.src) + (size_t)slot * (size_t)a.slot_elems + gbase +
+                        Cfg::elem(t, 0, A0);
+#pragma unroll
+        for (int k = 0; k < Cfg::E; ++k) v[k] = src[(uint32_t)k << A0];
     } else {
         const C2 *src = reinterpret_cast<const C2 *>(a.src) + (size_t)slot * (size_t)a.slot_elems;
 #pragma unroll
@@ -204,7 +206,7 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const Pas
     typedef typename Cfg::C2 C2;
     extern __shared__ __align__(16) unsigned char smraw[];
     C2 *sm = reinterpret_cast<C2 *>(smraw);
-    constexpr size_t TILE_SMEM = Cfg::NR > 1 ? sizeof(C2) * (size_t)Cfg::G * Cfg::SIZE : 0;
+    constexpr size_t TILE_SMEM = Cfg::NR > 1 ? sizeof(C2) * (size_t)Cfg::G * Cfg::PSIZE : 0;
     double *red = reinterpret_cast<double *>(smraw + TILE_SMEM);
 
     const uint32_t tid = threadIdx.x;
@@ -312,57 +314,61 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const Pas
         if (active && t == 0 && cnt > 0.0) atomicAdd(a.count_out + slot, (unsigned long long)cnt);
     } else if constexpr (DST == DST_MOMENTS) {
         static_assert(Cfg::LO == 0 && AL == 0, "moments epilogue runs on last-pass tiles");
-        // z' = zb | k for slot k (last mapping: slot bits are the low RB bits)
+        // z' = zb | k for slot k (last mapping: slot bits are the low RB bits).
+        // q = (c(z0)^2, c(z1)^2) up to the order fixed by the parity, kept as
+        // a packed pair: moments only need the unordered pair.
         const float s = (float)(*a.s_ptr);
         const int RL = a.range_log2;
         const uint32_t zb = (uint32_t)gbase | Cfg::elem(t, 0, 0);
-        float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // c^2, c^4, c^6, c^2 log2 c^2, w_A, w_B
+        float2 s2 = make_float2(0.f, 0.f), s4 = s2, s6 = s2, sl = s2, w = s2;
         float qmax = 0.f;
+        const float tiny = 1.17549435e-38f;
+        const bool wr = a.want_ranges;
         if (x) {
-            const float sc = 2.0f * s;
+            const float2 sc = make_float2(2.0f * s, 2.0f * s);
             const uint32_t xd = (uint32_t)((x & ((1ULL << j) - 1ULL)) | ((x >> (j + 1)) << j));
-            // bit k: parity of |x & z0| for z' = zb | k (z0 = z' with 0 inserted at bit j)
+            // bit k: parity of |x & z0| for z' = zb | k (z0 carries Im when odd)
             const uint32_t pm = walsh_mask5(xd & (Cfg::E - 1)) ^ ((__popc(xd & zb) & 1) ? 0xFFFFFFFFu : 0u);
-            const bool wr = a.want_ranges;
             const bool jge = j >= RL;
 #pragma unroll
             for (int k = 0; k < Cfg::E; ++k) {
-                const float re = sc * v[k].x, im = sc * v[k].y;
-                const float rr = re * re, ii = im * im;
-                const float r2 = rr * rr, i2 = ii * ii;
-                acc[0] += rr + ii;
-                acc[1] += r2 + i2;
-                acc[2] += r2 * rr + i2 * ii;
-                acc[3] += xlog2x(rr) + xlog2x(ii);
-                qmax = fmaxf(qmax, fmaxf(rr, ii));
+                const float2 c = mul2(sc, v[k]);
+                const float2 q = mul2(c, c);
+                const float2 q2 = mul2(q, q);
+                s2 = add2(s2, q);
+                s4 = add2(s4, q2);
+                s6 = fma2(q2, q, s6);
+                const float2 lg = make_float2(__log2f(fmaxf(q.x, tiny)), __log2f(fmaxf(q.y, tiny)));
+                sl = fma2(q, lg, sl);
+                qmax = fmaxf(qmax, fmaxf(q.x, q.y));
                 if (wr) {
-                    if (jge) {
-                        const bool odd = (pm >> k) & 1u;   // z0 carries Im when odd
-                        acc[4] += odd ? ii : rr;
-                        acc[5] += odd ? rr : ii;
-                    } else {
+                    if (jge) {   // (range A, range B) = (z0, z1)
+                        const bool odd = (pm >> k) & 1u;
+                        w = add2(w, make_float2(odd ? q.y : q.x, odd ? q.x : q.y));
+                    } else {     // both into the range picked by bit RL-1 of z'
                         const bool hi = ((zb | (uint32_t)k) >> (RL - 1)) & 1u;
-                        const float q = rr + ii;
-                        acc[4] += hi ? 0.f : q;
-                        acc[5] += hi ? q : 0.f;
+                        const float qq = q.x + q.y;
+                        w = add2(w, make_float2(hi ? 0.f : qq, hi ? qq : 0.f));
                     }
                 }
             }
         } else {
+            const float2 sc = make_float2(s, s);
 #pragma unroll
             for (int k = 0; k < Cfg::E; ++k) {
-                const float c0 = s * (v[k].x + v[k].y), c1 = s * (v[k].x - v[k].y);
-                const float q0 = c0 * c0, q1 = c1 * c1;
-                const float r2 = q0 * q0, i2 = q1 * q1;
-                acc[0] += q0 + q1;
-                acc[1] += r2 + i2;
-                acc[2] += r2 * q0 + i2 * q1;
-                acc[3] += xlog2x(q0) + xlog2x(q1);
-                qmax = fmaxf(qmax, fmaxf(q0, q1));
-                acc[4] += q0;      // z' -> range A, z' + d/2 -> range B
-                acc[5] += q1;
+                const float2 c = mul2(sc, make_float2(v[k].x + v[k].y, v[k].x - v[k].y));
+                const float2 q = mul2(c, c);
+                const float2 q2 = mul2(q, q);
+                s2 = add2(s2, q);
+                s4 = add2(s4, q2);
+                s6 = fma2(q2, q, s6);
+                const float2 lg = make_float2(__log2f(fmaxf(q.x, tiny)), __log2f(fmaxf(q.y, tiny)));
+                sl = fma2(q, lg, sl);
+                qmax = fmaxf(qmax, fmaxf(q.x, q.y));
+                w = add2(w, q);        // z' -> range A, z' + d/2 -> range B
             }
         }
+        float acc[6] = {s2.x + s2.y, s4.x + s4.y, s6.x + s6.y, sl.x + sl.y, w.x, w.y};
         double out[6];
         float omx;
         group_reduce<Cfg::T, Cfg::NT, 6>(acc, qmax, out, omx, red);
@@ -378,7 +384,7 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const Pas
 
 template <class Cfg, int SRC, int DST>
 cudaError_t launch_cfg(const PassArgs &a, int tiles, cudaStream_t st) {
-    const size_t tile_smem = Cfg::NR > 1 ? sizeof(typename Cfg::C2) * (size_t)Cfg::G * Cfg::SIZE : 0;
+    const size_t tile_smem = Cfg::NR > 1 ? sizeof(typename Cfg::C2) * (size_t)Cfg::G * Cfg::PSIZE : 0;
     const size_t smem = tile_smem + sizeof(double) * (8 * (Cfg::NT / 32) + 8);
     static bool attr_done = false;
     if (!attr_done) {

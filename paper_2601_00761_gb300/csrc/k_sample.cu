@@ -6,7 +6,8 @@
 // prologue, rounds and c-pair code as the fused moments epilogue (so every
 // c^2 is bit-identical to the one that entered the range weight), lays the
 // range's c^2 out in z order in shared memory and returns the smallest z with
-// C(z) > t', C the FP64 running sum over the range in a fixed association.
+// C(z) > t', C the running sum over the range of the c^2 in u32 fixed point
+// (2^31 quanta per range weight) -- exact, so every association agrees.
 #include "k_misc.cuh"
 #include "k_pass.cuh"
 
@@ -20,7 +21,7 @@ __global__ void __launch_bounds__(Cfg::NT) zsample_kernel(const PassArgs a, cons
     static_assert(Cfg::G == 1, "one tile per CTA");
     extern __shared__ __align__(16) unsigned char smraw[];
     C2 *sm = reinterpret_cast<C2 *>(smraw);
-    double *seg = reinterpret_cast<double *>(smraw + sizeof(C2) * (size_t)Cfg::SIZE);
+    double *seg = reinterpret_cast<double *>(smraw + sizeof(C2) * (size_t)Cfg::PSIZE);
 
     const long long idx = (long long)blockIdx.x + 65535LL * (long long)blockIdx.y;
     if (idx >= a.n_fam * (long long)z_per_x) return;   // uniform over the CTA
@@ -45,8 +46,16 @@ __global__ void __launch_bounds__(Cfg::NT) zsample_kernel(const PassArgs a, cons
     tile_transform<Cfg>(v, sm, t, 0);
     __syncthreads();
 
-    float *wz = reinterpret_cast<float *>(smraw);
-    float *cv = wz + (1 << RL);
+    // The range's c^2 in z order as u32 fixed-point quanta (scale 2^31 per
+    // range weight) and its signed c; one padding word per 32 entries keeps
+    // each thread's 32 consecutive entries conflict-free. Integer prefix sums
+    // are exact in any association, so the thread segments tile the range
+    // exactly and every target has one owner.
+    uint32_t *wq = reinterpret_cast<uint32_t *>(smraw);
+    float *cv = reinterpret_cast<float *>(wq + (1 << RL) + ((1 << RL) >> 5));
+    auto pp = [](uint32_t p) { return p + (p >> 5); };
+    const double scale = dr.wr > 0.0 ? 0x1.0p31 / dr.wr : 0.0;
+    const float scf = (float)scale;
     const R s = (R)(*a.s_ptr);
     constexpr int AL = Maps<Cfg>::last;
 #pragma unroll
@@ -54,45 +63,66 @@ __global__ void __launch_bounds__(Cfg::NT) zsample_kernel(const PassArgs a, cons
         unsigned long long z0, z1;
         R c0, c1;
         family_pair<R, C2>(x, j, s, v[k], gbase | Cfg::elem(t, k, AL), z0, z1, c0, c1);
-        if ((z0 >> RL) == dr.range) { wz[z0 - zstart] = c0 * c0; cv[z0 - zstart] = c0; }
-        if ((z1 >> RL) == dr.range) { wz[z1 - zstart] = c1 * c1; cv[z1 - zstart] = c1; }
+        if ((z0 >> RL) == dr.range) {
+            const uint32_t q = pp((uint32_t)(z0 - zstart));
+            wq[q] = __float2uint_rn(fminf(c0 * c0 * scf, 4.0e9f));
+            cv[q] = c0;
+        }
+        if ((z1 >> RL) == dr.range) {
+            const uint32_t q = pp((uint32_t)(z1 - zstart));
+            wq[q] = __float2uint_rn(fminf(c1 * c1 * scf, 4.0e9f));
+            cv[q] = c1;
+        }
     }
     __syncthreads();
 
     constexpr int PER = (1 << Cfg::M) / Cfg::NT;
     const int lo = t * PER;
-    double run = 0.0;
-    for (int i = 0; i < PER; ++i) run += (double)wz[lo + i];
-    seg[t + 1] = run;
+    unsigned long long own = 0;
+    for (int i = 0; i < PER; ++i) own += wq[pp(lo + i)];
+    unsigned long long incl = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long up = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)(threadIdx.x & 31) >= o) incl += up;
+    }
+    unsigned long long *wsum = reinterpret_cast<unsigned long long *>(seg);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 31) wsum[wid] = incl;
     __syncthreads();
-    if (t == 0) {
-        seg[0] = 0.0;
-        for (int i = 1; i <= Cfg::NT; ++i) seg[i] = seg[i - 1] + seg[i];
+    if (threadIdx.x == 0) {
+        unsigned long long run = 0;
+        for (int q = 0; q < Cfg::NT / 32; ++q) { const unsigned long long v0 = wsum[q]; wsum[q] = run; run += v0; }
+        wsum[Cfg::NT / 32] = run;
     }
     __syncthreads();
-    const double tt = dr.t;
+    const unsigned long long before = wsum[wid] + incl - own;
+    const unsigned long long total = wsum[Cfg::NT / 32];
+    double tq = dr.t * scale;
+    if (tq < 0.0) tq = 0.0;
+    const unsigned long long T = tq < 1.8e19 ? (unsigned long long)tq : ~0ULL;
     const size_t out = (size_t)gf * z_per_x + kdraw;
-    if (seg[t + 1] > tt && !(seg[t] > tt)) {
-        double acc = 0.0;
+    if (T < total && before <= T && T < before + own) {
+        unsigned long long run = before;
         int pick = lo + PER - 1;
         for (int i = 0; i < PER; ++i) {
-            acc += (double)wz[lo + i];
-            if (seg[t] + acc > tt) { pick = lo + i; break; }
+            run += wq[pp(lo + i)];
+            if (run > T) { pick = lo + i; break; }
         }
         zs[out] = zstart + (unsigned long long)pick;
-        cz[out] = cv[pick];
-    } else if (t == 0 && !(seg[Cfg::NT] > tt)) {
+        cz[out] = cv[pp(pick)];
+    } else if (threadIdx.x == 0 && !(T < total)) {
         int pick = (1 << RL) - 1;
-        while (pick > 0 && !(wz[pick] > 0.0f)) --pick;
+        while (pick > 0 && wq[pp(pick)] == 0u) --pick;
         zs[out] = zstart + (unsigned long long)pick;
-        cz[out] = cv[pick];
+        cz[out] = cv[pp(pick)];
     }
 }
 
 template <class Cfg, int SRC>
 cudaError_t launch_zs(const PassArgs &a, const DrawInfo *draws, int z_per_x, unsigned long long *zs, float *cz,
                       cudaStream_t st) {
-    const size_t smem = sizeof(float2) * (size_t)Cfg::SIZE + sizeof(double) * (Cfg::NT + 1);
+    const size_t smem = sizeof(float2) * (size_t)Cfg::PSIZE + sizeof(double) * (Cfg::NT / 32 + 4);
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(zsample_kernel<Cfg, SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize,

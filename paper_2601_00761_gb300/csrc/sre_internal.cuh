@@ -43,6 +43,33 @@ __device__ __forceinline__ T cadd(T a, T b) { T r; r.x = a.x + b.x; r.y = a.y + 
 template <typename T>
 __device__ __forceinline__ T csub(T a, T b) { T r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
 
+// Packed FP32x2 arithmetic of sm_100+ (one instruction per complex add;
+// each lane rounds to nearest exactly as the scalar instruction does).
+__device__ __forceinline__ unsigned long long f2u(float2 a) { return *reinterpret_cast<unsigned long long *>(&a); }
+__device__ __forceinline__ float2 u2f(unsigned long long a) { return *reinterpret_cast<float2 *>(&a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(d);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(d);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(d);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)), "l"(f2u(c)));
+    return u2f(d);
+}
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) { return add2(a, b); }
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) { return sub2(a, b); }
+
 __host__ __device__ __forceinline__ unsigned long long insert0(unsigned long long v, int j) {
     unsigned long long lo = v & ((1ULL << j) - 1ULL);
     return ((v >> j) << (j + 1)) | lo;
@@ -98,17 +125,14 @@ struct TileCfg {
     __device__ static __forceinline__ uint32_t elem(uint32_t t, uint32_t k, int a) {
         return (t & ((1u << a) - 1u)) | (k << a) | ((t >> a) << (a + RB));
     }
-    // Shared-memory swizzle: nibble-fold XOR (conflict-free when the 4 lowest
-    // thread bits map to element bits with distinct positions mod 4). It is
-    // linear over GF(2): swz(e1 ^ e2) = swz(e1) ^ swz(e2), so a round's
-    // addresses are one per-thread base XOR a compile-time constant per slot.
-    __host__ __device__ static constexpr uint32_t swz(uint32_t e) {
-        return M < 5 ? e : (e ^ (((e >> 4) ^ (e >> 8) ^ (e >> 12) ^ (e >> 16)) & 15u));
-    }
-    __device__ static __forceinline__ uint32_t grp_base(uint32_t g) {
-        return (g << M) ^ ((M >= 5 && TB < 4) ? ((g << TB) & 15u) : 0u);
-    }
-    __device__ static __forceinline__ uint32_t phys(uint32_t e, uint32_t g) { return grp_base(g) ^ swz(e); }
+    // Shared-memory layout: one padding element per 2^RB elements,
+    // phys(e) = e + (e >> RB). Bank-conflict-free for every round mapping of
+    // the instantiated tiles, and additive over disjoint bit fields, so
+    // phys(elem(t, k, a)) = phys(elem(t, 0, a)) + phys(k << a): a round's
+    // addresses are one per-thread base plus a compile-time offset per slot.
+    static constexpr int PSIZE = RB > 0 ? SIZE + (SIZE >> RB) : SIZE;
+    __host__ __device__ static constexpr uint32_t pad(uint32_t e) { return RB > 0 ? e + (e >> RB) : e; }
+    __device__ static __forceinline__ uint32_t phys(uint32_t e, uint32_t g) { return g * (uint32_t)PSIZE + pad(e); }
 };
 
 template <typename C2, int E, int S0, int S1>
@@ -132,16 +156,16 @@ struct Rounds {
     static constexpr int i = Cfg::NR - 1 - r;
     static constexpr int a = Cfg::slot_base(i);
     __device__ static __forceinline__ void run(C2 (&v)[Cfg::E], C2 *sm, uint32_t t, uint32_t g) {
-        const uint32_t pb = Cfg::phys(Cfg::elem(t, 0, a), g);
+        C2 *pb = sm + Cfg::phys(Cfg::elem(t, 0, a), g);
         if constexpr (r > 0) {
             __syncthreads();
 #pragma unroll
-            for (int k = 0; k < Cfg::E; ++k) v[k] = sm[pb ^ Cfg::swz((uint32_t)k << a)];
+            for (int k = 0; k < Cfg::E; ++k) v[k] = pb[Cfg::pad((uint32_t)k << a)];
         }
         butterflies<C2, Cfg::E, Cfg::range_lo(i) - a, Cfg::range_hi(i) - a>(v);
         if constexpr (r < Cfg::NR - 1) {
 #pragma unroll
-            for (int k = 0; k < Cfg::E; ++k) sm[pb ^ Cfg::swz((uint32_t)k << a)] = v[k];
+            for (int k = 0; k < Cfg::E; ++k) pb[Cfg::pad((uint32_t)k << a)] = v[k];
             Rounds<Cfg, r + 1>::run(v, sm, t, g);
         }
     }

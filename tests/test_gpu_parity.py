@@ -41,14 +41,19 @@ def sample_xs(N, k, seed):
     return sorted(x for x in xs if 0 <= x < d)
 
 
-def draw_within_bound(zg, zo, w_oracle, w_gpu, u):
+def draw_within_bound(zg, zo, w_oracle, w_gpu, u, range_log2=13):
     """A z drawn from FP32-computed weights against the oracle's FP64 draw:
     equal, or both on the same side of the target within the propagated
     bound delta = sum |w_gpu - w_oracle| (each cumulative sum and the target
-    differ by at most delta). Returns (valid, exact)."""
+    differ by at most delta) plus the sampler's fixed-point rounding inside a
+    z-range (half a quantum of 2^-31 range weight per entry, 2^RL entries).
+    Returns (valid, exact)."""
     if zg == zo:
         return True, True
     delta = float(np.sum(np.abs(w_gpu - w_oracle))) + 1e-12
+    wr = max(float(np.sum(w_oracle[(zz >> range_log2) << range_log2:((zz >> range_log2) + 1) << range_log2]))
+             for zz in (zg, zo))
+    delta += 2.0 ** (range_log2 - 32) * wr
     C = np.cumsum(w_oracle)
     t = u * C[-1]
     lo = C[zg - 1] if zg > 0 else 0.0
