@@ -80,24 +80,28 @@ __global__ void __launch_bounds__(Cfg::NT) zsample_kernel(const PassArgs a, cons
     const int lo = t * PER;
     unsigned long long own = 0;
     for (int i = 0; i < PER; ++i) own += wq[pp(lo + i)];
+    // warps of the CTA (the smallest tiles have fewer than 32 threads)
+    constexpr int NW = (Cfg::NT + 31) / 32;
+    constexpr int WL = Cfg::NT < 32 ? Cfg::NT : 32;
+    constexpr unsigned MASK = Cfg::NT < 32 ? ((1u << Cfg::NT) - 1u) : 0xffffffffu;
     unsigned long long incl = own;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long up = __shfl_up_sync(0xffffffffu, incl, o);
+    for (int o = 1; o < WL; o <<= 1) {
+        const unsigned long long up = __shfl_up_sync(MASK, incl, o);
         if ((int)(threadIdx.x & 31) >= o) incl += up;
     }
     unsigned long long *wsum = reinterpret_cast<unsigned long long *>(seg);
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 31) wsum[wid] = incl;
+    if (lane == WL - 1) wsum[wid] = incl;
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long run = 0;
-        for (int q = 0; q < Cfg::NT / 32; ++q) { const unsigned long long v0 = wsum[q]; wsum[q] = run; run += v0; }
-        wsum[Cfg::NT / 32] = run;
+        for (int q = 0; q < NW; ++q) { const unsigned long long v0 = wsum[q]; wsum[q] = run; run += v0; }
+        wsum[NW] = run;
     }
     __syncthreads();
     const unsigned long long before = wsum[wid] + incl - own;
-    const unsigned long long total = wsum[Cfg::NT / 32];
+    const unsigned long long total = wsum[NW];
     double tq = dr.t * scale;
     if (tq < 0.0) tq = 0.0;
     const unsigned long long T = tq < 1.8e19 ? (unsigned long long)tq : ~0ULL;
@@ -122,7 +126,7 @@ __global__ void __launch_bounds__(Cfg::NT) zsample_kernel(const PassArgs a, cons
 template <class Cfg, int SRC>
 cudaError_t launch_zs(const PassArgs &a, const DrawInfo *draws, int z_per_x, unsigned long long *zs, float *cz,
                       cudaStream_t st) {
-    const size_t smem = sizeof(float2) * (size_t)Cfg::PSIZE + sizeof(double) * (Cfg::NT / 32 + 4);
+    const size_t smem = sizeof(float2) * (size_t)Cfg::PSIZE + sizeof(double) * ((Cfg::NT + 31) / 32 + 4);
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(zsample_kernel<Cfg, SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
