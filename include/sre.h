@@ -252,6 +252,30 @@ SRE_API sre_status sre_profile_passes(const void *psi_c64_dev, int N, long long 
                                       void *stream, double *ms_host, double *bytes_host, int *n_passes,
                                       long long *fam_per_launch);
 
+/* sre_exact without any device allocation. The paper has no counterpart:
+ * this is a deployment variant for callers that cannot allocate device memory
+ * at call time -- a process whose device memory is held entirely by another
+ * allocator (a framework's caching pool) or that runs under a fixed memory
+ * budget, where a cudaMalloc could fail, and latency-sensitive callers that
+ * cannot afford the device-wide synchronisation cudaMalloc/cudaFree can imply.
+ * It runs the same launch sequence as sre_exact on a scratch array that the
+ * library reserves statically (SRE_NOALLOC_SCRATCH_BYTES on every GPU that
+ * loads the library, held until the process exits); psi, the stream and the
+ * host result are the caller's as for sre_exact.
+ *  - N is limited to 1..SRE_NOALLOC_MAX_N; larger N returns SRE_EINVAL with a
+ *    message naming the limit, before any device work.
+ *  - The first call on a device looks up the scratch's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call uses the same scratch and leaves its contents behind; the
+ *    call clears what must start at zero. Calls whose device work overlaps
+ *    (different streams, threads or processes sharing the context) race on
+ *    the scratch: serialise them. */
+#define SRE_NOALLOC_SCRATCH_BYTES (2u << 20)
+#define SRE_NOALLOC_MAX_N 13
+SRE_API sre_status sre_exact_noalloc(const void *psi_c64_dev, int N, const sre_opts *opts, void *stream,
+                                     sre_result *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,7 +20,7 @@ __all__ = ["sre_version", "sre_last_error", "sre_default_opts", "sre_make_plan",
            "sre_release_workspace", "sre_norm2", "sre_exact", "sre_exact_batched", "sre_mc",
            "pauli_x_marginal", "stabilizer_nullity", "apply_clifford_tdoped_circuit",
            "sre_family_spectrum", "sre_family_spectrum_f64", "sre_philox_blocks", "sre_kernel_launches",
-           "sre_profile_passes", "sre_pass_timing", "SreError",
+           "sre_profile_passes", "sre_pass_timing", "sre_exact_noalloc", "SreError",
            "SRE_FP32_SIMT", "SRE_BF16X2_TC", "SRE_BF16X3_TC", "SRE_MC_UNIFORM", "SRE_MC_MARGINAL",
            "lib_path", "load"]
 
@@ -112,6 +112,7 @@ def load():
         "sre_family_spectrum_f64": ([_vp, ctypes.c_int, ctypes.c_ulonglong, _vp, _vp], st),
         "sre_philox_blocks": ([_vp, _vp, ctypes.c_int, _vp], st),
         "sre_kernel_launches": ([], ctypes.c_ulonglong),
+        "sre_exact_noalloc": ([_vp, ctypes.c_int, ctypes.POINTER(Opts), _vp, ctypes.POINTER(Result)], st),
         "sre_pass_timing": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                              ctypes.POINTER(ctypes.c_double)], st),
         "sre_profile_passes": ([_vp, ctypes.c_int, ctypes.c_longlong, ctypes.POINTER(Opts), _vp,
@@ -349,3 +350,15 @@ def sre_pass_timing(enable: bool) -> dict:
     by = (ctypes.c_double * 4)()
     _check(load().sre_pass_timing(1 if enable else 0, ms, n, by))
     return {"ms_sum": list(ms), "launches": list(n), "bytes_per_launch": list(by)}
+
+
+def sre_exact_noalloc(psi, allow_nullity_error=False, **kw) -> dict:
+    """sre_exact on the library's fixed scratch: allocates no device memory
+    (N <= 13). For callers that cannot allocate at call time."""
+    p, N = _psi_ptr(psi)
+    r = Result()
+    st = load().sre_exact_noalloc(p, N, ctypes.byref(_opts(**kw)), _stream(), ctypes.byref(r))
+    _check(st, allow=(SRE_ENULLITY,) if allow_nullity_error else ())
+    d = r.as_dict()
+    d["status"] = st
+    return d

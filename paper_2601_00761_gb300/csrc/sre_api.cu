@@ -491,6 +491,11 @@ sre_status exact_impl(const void *psi, int N, const sre_opts &o, void *ws, size_
 
 } // namespace
 
+namespace sre {
+// error message of the calling thread for entry points in other units
+void set_error_message(const char *msg) { g_err = msg; }
+}
+
 // =================================================================== C ABI
 extern "C" {
 
