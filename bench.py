@@ -49,6 +49,26 @@ def parse():
     return ap.parse_args()
 
 
+def profiled_traffic(N, dom_pass):
+    """DRAM bytes per family of the dominant kernel from the committed ncu
+    summary (profiles/strided_pass_n24.md), or None when that summary is for
+    another kernel or the kernel's sources changed since it was captured."""
+    import hashlib
+    if N != 24 or dom_pass != 0:
+        return None
+    try:
+        txt = open(os.path.join(ROOT, "profiles", "strided_pass_n24.md")).read()
+        vals = dict(l.split(": ", 1) for l in txt.splitlines() if l.startswith(("traffic_bytes", "source_sha")))
+        h = hashlib.sha256()
+        for f in ("k_pass.cuh", "sre_internal.cuh", "k_pass_f32_multi.cu"):
+            h.update(open(os.path.join(ROOT, "paper_2601_00761_gb300", "csrc", f), "rb").read())
+        if h.hexdigest()[:16] != vals["source_sha256_16"].strip():
+            return None
+        return float(vals["traffic_bytes_per_family"])
+    except Exception:
+        return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -245,8 +265,13 @@ def run_cuda(a):
     avg_ms = timing["ms_sum"][dom] / max(1, timing["launches"][dom])
     achieved = timing["bytes_per_launch"][dom] / (avg_ms / 1e3) / 1e9
     step_bytes = sum(timing["bytes_per_launch"][p] * timing["launches"][p] for p in range(npass)) / a.steps
+    fam_per_launch = timing["bytes_per_launch"][dom] / (12.0 * 2 ** N) if dom == 0 else None
+    tpf = profiled_traffic(N, dom) if not (a.radix or a.tile or a.x_batch) else None
+    traffic = tpf * fam_per_launch if (tpf is not None and fam_per_launch) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": ["strided pass 0 (reads psi, writes the packed intermediate)",
+                "traffic": traffic,
+                "traffic_note": "ncu dram read+write of a 4-family capture scaled to the launch's families "
+                                "(profiles/strided_pass_n24.md)" if traffic else None, "kernel": ["strided pass 0 (reads psi, writes the packed intermediate)",
                                             "row pass (reads the intermediate, fused moments)"][min(dom, 1)]
                 if npass == 2 else f"pass {dom}",
                 "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
