@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="mc24", choices=["mc24", "batched"],
+                    help="mc24: the headline N=24 MC step; batched: exact M_2/nullity of 4096 T-doped states "
+                         "with N ~ U{8..16} in one sre_exact_batched call, against a per-state loop")
+    ap.add_argument("--count", type=int, default=4096)
     return ap.parse_args()
 
 
@@ -333,10 +337,68 @@ def run_cuda(a):
     return 0
 
 
+def run_batched(a):
+    """Uneven batch: count T-doped random Clifford states (N ~ U{8..16},
+    eta ~ U{1,2,4,8,32}, n_T ~ U{1..3N}, seeds 4000+i) prepared on the GPU;
+    one step = one sre_exact_batched call over all of them. The same states
+    through a per-state sre_exact loop are timed beside it."""
+    import torch
+    from paper_2601_00761_gb300 import build as sre_build
+    sre_build.build()
+    import paper_2601_00761_gb300 as sre
+    from paper_2601_00761_gb300 import inputs
+    torch.cuda.set_device(0)
+    specs = inputs.workload_batched_specs(count=a.count)
+    states = []
+    for sp in specs:
+        p = torch.zeros(1 << sp["N"], dtype=torch.complex64, device="cuda")
+        p[0] = 1
+        sre.apply_clifford_tdoped_circuit(p, inputs.batched_gate_list(sp))
+        states.append(p)
+    total_c = float(sum(4 ** sp["N"] for sp in specs))
+    tuned = {}
+    for N in sorted({sp["N"] for sp in specs}):
+        if sre.sre_make_plan(N)["n_passes"] > 1:
+            tuned[N] = sre.sre_autotune(next(p for p, sp in zip(states, specs) if sp["N"] == N))
+    stream = torch.cuda.current_stream()
+    for _ in range(a.warmup):
+        sre.sre_exact_batched(states)
+    torch.cuda.synchronize()
+    l0 = sre.sre_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        res = sre.sre_exact_batched(states)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    launches = sre.sre_kernel_launches() - l0
+    # per-state launch loop on the same states
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    loop = [sre.sre_exact(p, allow_nullity_error=True) for p in states]
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms_loop = t0.elapsed_time(t1)
+    dmax = max(abs(r["M"][1] - q["M"][1]) for r, q in zip(res, loop))
+    line = {"metric": "Pauli expectations/s, batched uneven exact M_2 and nullity", "value": total_c / (ms / 1e3),
+            "unit": UNIT, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded T-doped circuits)",
+            "config": {"workload": f"{a.count} T-doped random Clifford states, N ~ U{{8..16}}, one sre_exact_batched call",
+                       "states": a.count, "pauli_strings": total_c, "tuned": {str(k): v for k, v in tuned.items()}},
+            "per_state_loop": {"value": total_c / (ms_loop / 1e3), "ms": ms_loop},
+            "max_dM2_vs_loop": dmax, "gpu_launches": int(launches)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.workload == "batched":
+        return run_batched(a)
     return run_cuda(a)
 
 

@@ -158,12 +158,27 @@ SRE_API sre_status sre_exact(const void *psi_c64_dev, int N, const sre_opts *opt
                      sre_result *out);
 
 /* Exact M_1..M_3 and nullity of `count` states of possibly different N in
- * one call (psi_ptrs_host[i] a device pointer, Ns_host[i] in 1..20). The
- * work of all states is issued as one persistent launch sequence captured in
- * a CUDA graph. out: host array of `count` results. */
+ * one call (Algorithm 1 per state; psi_ptrs_host[i] a device pointer,
+ * Ns_host[i] in 1..20). States are grouped by N; each launch covers every
+ * (state, family) item of a chunk of same-N states, and the launch sequence
+ * of the whole batch is captured once into a CUDA graph (cached for the same
+ * batch shape) and replayed; the FP64 nullity recheck of candidate families
+ * follows. Plans come from sre_autotune's table when opts leaves the tiling
+ * at 0. out: host array of `count` results (a state whose stabilizer count is
+ * not a power of two gets nullity -1). workspace must be NULL (library
+ * workspace). Returns SRE_EZERO if a state has zero norm. */
 SRE_API sre_status sre_exact_batched(const void *const *psi_ptrs_host, const int *Ns_host, int count,
                              const sre_opts *opts, void *workspace, size_t workspace_bytes,
                              void *stream, sre_result *out);
+
+/* Autotuner: times every admissible tiling (radix_log2, tile_log2, x_batch)
+ * of the family transform for N on the caller's state psi and keeps the
+ * fastest in a process-wide table that sre_exact, sre_exact_batched, sre_mc
+ * and the plan/workspace queries use whenever opts leaves those three fields
+ * at 0 (so query workspace sizes after tuning). If the environment variable
+ * SRE_TUNE_FILE names a file, the table is read from and written to it.
+ * *best receives the choice (the defaults when N needs a single pass). */
+SRE_API sre_status sre_autotune(const void *psi_c64_dev, int N, void *stream, sre_opts *best);
 
 /* Monte Carlo over X-mask families (N in 2..30).
  * mode SRE_MC_UNIFORM: the SM Sec. I estimator -- x = 0 always and n_x - 1

@@ -20,7 +20,7 @@ __all__ = ["sre_version", "sre_last_error", "sre_default_opts", "sre_make_plan",
            "sre_release_workspace", "sre_norm2", "sre_exact", "sre_exact_batched", "sre_mc",
            "pauli_x_marginal", "stabilizer_nullity", "apply_clifford_tdoped_circuit",
            "sre_family_spectrum", "sre_family_spectrum_f64", "sre_philox_blocks", "sre_kernel_launches",
-           "sre_profile_passes", "sre_pass_timing", "sre_exact_noalloc", "SreError",
+           "sre_profile_passes", "sre_pass_timing", "sre_exact_noalloc", "sre_autotune", "SreError",
            "SRE_FP32_SIMT", "SRE_BF16X2_TC", "SRE_BF16X3_TC", "SRE_MC_UNIFORM", "SRE_MC_MARGINAL",
            "lib_path", "load"]
 
@@ -112,6 +112,7 @@ def load():
         "sre_family_spectrum_f64": ([_vp, ctypes.c_int, ctypes.c_ulonglong, _vp, _vp], st),
         "sre_philox_blocks": ([_vp, _vp, ctypes.c_int, _vp], st),
         "sre_kernel_launches": ([], ctypes.c_ulonglong),
+        "sre_autotune": ([_vp, ctypes.c_int, _vp, ctypes.POINTER(Opts)], st),
         "sre_exact_noalloc": ([_vp, ctypes.c_int, ctypes.POINTER(Opts), _vp, ctypes.POINTER(Result)], st),
         "sre_pass_timing": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                              ctypes.POINTER(ctypes.c_double)], st),
@@ -222,6 +223,14 @@ def sre_exact(psi, workspace=None, allow_nullity_error=False, **kw) -> dict:
     d = r.as_dict()
     d["status"] = st
     return d
+
+
+def sre_autotune(psi) -> dict:
+    """Pick the fastest tiling for psi's N (kept for later calls)."""
+    p, N = _psi_ptr(psi)
+    o = Opts()
+    _check(load().sre_autotune(p, N, _stream(), ctypes.byref(o)))
+    return {"radix_log2": o.radix_log2, "tile_log2": o.tile_log2, "x_batch": o.x_batch}
 
 
 def sre_exact_batched(psis, **kw) -> list:

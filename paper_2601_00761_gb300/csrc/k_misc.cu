@@ -430,6 +430,96 @@ cudaError_t launch_mc_stats(const FamMoments *fm, const float *cz, long long n_x
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------- batched states
+// per-state sum |psi|^2: grid (blocks per state, states), fixed order
+__global__ void __launch_bounds__(256) norm2_multi_partial(const float2 *const *psi_list, int N, int nb,
+                                                           double *partial) {
+    __shared__ double red[8];
+    const int st = blockIdx.y;
+    const float2 *psi = psi_list[st];
+    const unsigned long long d = 1ULL << N;
+    double acc = 0.0;
+    const unsigned long long stride = (unsigned long long)nb * blockDim.x;
+    for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; b < d; b += stride) {
+        const float2 u = __ldg(psi + b);
+        acc = fma((double)u.x, (double)u.x, acc);
+        acc = fma((double)u.y, (double)u.y, acc);
+    }
+    acc = block_sum<256>(acc, red);
+    if (threadIdx.x == 0) partial[(size_t)st * nb + blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(256) norm2_multi_final(const double *partial, int nb, double *norm2, double *s) {
+    __shared__ double red[8];
+    const int st = blockIdx.x;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += 256) acc += partial[(size_t)st * nb + i];
+    acc = block_sum<256>(acc, red);
+    if (threadIdx.x == 0) {
+        norm2[st] = acc;
+        s[st] = acc > 0.0 ? 1.0 / acc : 0.0;
+    }
+}
+
+cudaError_t launch_norm2_multi(const float2 *const *psi_list, int n_states, int N, double *partial, int nb,
+                               double *norm2, double *s, cudaStream_t st) {
+    norm2_multi_partial<<<dim3(nb, n_states), 256, 0, st>>>(psi_list, N, nb, partial);
+    norm2_multi_final<<<n_states, 256, 0, st>>>(partial, nb, norm2, s);
+    return cudaGetLastError();
+}
+
+// per-state totals of the family sums of states [s0, s0 + ns): one block per
+// state over its 2^N consecutive families (fixed order); candidate families
+// appended to flags as F = (state << N) | x.
+__global__ void __launch_bounds__(256) state_totals_kernel(const FamMoments *fm, long long fm_first_family, int N,
+                                                           int s0, double *totals, unsigned long long *flags,
+                                                           unsigned long long *n_flag) {
+    __shared__ double red[8];
+    const int st = s0 + blockIdx.x;
+    const long long nf = 1LL << N;
+    const long long f0 = ((long long)st << N) - fm_first_family;
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0, c = 0;
+    for (long long f = threadIdx.x; f < nf; f += 256) {
+        const FamMoments &m = fm[f0 + f];
+        a0 += m.m[0]; a1 += m.m[1]; a2 += m.m[2]; a3 += m.m[3]; c += (double)m.cand;
+        if (m.cand) {
+            const unsigned long long pos = atomicAdd(n_flag, 1ULL);
+            flags[pos] = ((unsigned long long)st << N) | (unsigned long long)f;
+        }
+    }
+    a0 = block_sum<256>(a0, red);
+    a1 = block_sum<256>(a1, red);
+    a2 = block_sum<256>(a2, red);
+    a3 = block_sum<256>(a3, red);
+    c = block_sum<256>(c, red);
+    if (threadIdx.x == 0) {
+        double *o = totals + 5 * (size_t)st;
+        o[0] = a0; o[1] = a1; o[2] = a2; o[3] = a3; o[4] = c;
+    }
+}
+
+cudaError_t launch_state_totals(const FamMoments *fm, long long fm_first_family, int N, int s0, int ns,
+                                double *totals, unsigned long long *flags, unsigned long long *n_flag,
+                                cudaStream_t st) {
+    state_totals_kernel<<<ns, 256, 0, st>>>(fm, fm_first_family, N, s0, totals, flags, n_flag);
+    return cudaGetLastError();
+}
+
+// stab counts of flagged families added to their states (integer atomics)
+__global__ void count_scatter_kernel(const unsigned long long *flags, const unsigned long long *counts, long long n,
+                                     int N, unsigned long long *state_count) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (counts[i]) atomicAdd(state_count + (flags[i] >> N), counts[i]);
+}
+
+cudaError_t launch_count_scatter(const unsigned long long *flags, const unsigned long long *counts, long long n,
+                                 int N, unsigned long long *state_count, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    count_scatter_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(flags, counts, n, N, state_count);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_philox_test(const unsigned long long *ctr_key, unsigned long long *out, int n, cudaStream_t st) {
     philox_test_kernel<<<(n + 127) / 128, 128, 0, st>>>(ctr_key, out, n);
     return cudaGetLastError();

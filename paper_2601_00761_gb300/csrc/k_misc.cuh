@@ -32,6 +32,13 @@ cudaError_t launch_zrange_select(double *W, long long nr, long long n_fam, long 
                                  cudaStream_t st);
 cudaError_t launch_mc_stats(const FamMoments *fm, const float *cz, long long n_x, int z_per_x, int N, int mode,
                             double *y, double *out, cudaStream_t st);
+cudaError_t launch_norm2_multi(const float2 *const *psi_list, int n_states, int N, double *partial, int nb,
+                               double *norm2, double *s, cudaStream_t st);
+cudaError_t launch_state_totals(const FamMoments *fm, long long fm_first_family, int N, int s0, int ns,
+                                double *totals, unsigned long long *flags, unsigned long long *n_flag,
+                                cudaStream_t st);
+cudaError_t launch_count_scatter(const unsigned long long *flags, const unsigned long long *counts, long long n,
+                                 int N, unsigned long long *state_count, cudaStream_t st);
 cudaError_t launch_philox_test(const unsigned long long *ctr_key, unsigned long long *out, int n, cudaStream_t st);
 
 // z sampler (k_sample.cu): recompute the last-pass tile of each draw's range

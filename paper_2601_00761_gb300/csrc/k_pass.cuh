@@ -112,8 +112,8 @@ __device__ __forceinline__ unsigned long long tile_gidx(unsigned long long gbase
 
 // Load the tile in the first round's mapping (prologue of every pass).
 template <class Cfg, int SRC>
-__device__ __forceinline__ void pass_prologue(typename Cfg::C2 (&v)[Cfg::E], const PassArgs &a, long long slot,
-                                              unsigned long long x, int j, unsigned long long half,
+__device__ __forceinline__ void pass_prologue(typename Cfg::C2 (&v)[Cfg::E], const PassArgs &a, const float2 *psi,
+                                              long long slot, unsigned long long x, int j, unsigned long long half,
                                               unsigned long long gbase, uint32_t t) {
     typedef typename Cfg::Real R;
     typedef typename Cfg::C2 C2;
@@ -130,8 +130,8 @@ __device__ __forceinline__ void pass_prologue(typename Cfg::C2 (&v)[Cfg::E], con
                 for (int q = 0; q < LB; ++q) {
                     const unsigned long long g = tile_gidx<Cfg>(gbase, a.lo_g, Cfg::elem(t, k0 + q, A0));
                     const unsigned long long b = insert0(g, j);
-                    u[q] = __ldg(a.psi + b);
-                    w[q] = __ldg(a.psi + (b ^ x));
+                    u[q] = __ldg(psi + b);
+                    w[q] = __ldg(psi + (b ^ x));
                 }
 #pragma unroll
                 for (int q = 0; q < LB; ++q) {
@@ -147,8 +147,8 @@ __device__ __forceinline__ void pass_prologue(typename Cfg::C2 (&v)[Cfg::E], con
 #pragma unroll
                 for (int q = 0; q < LB; ++q) {
                     const unsigned long long g = tile_gidx<Cfg>(gbase, a.lo_g, Cfg::elem(t, k0 + q, A0));
-                    u[q] = __ldg(a.psi + g);
-                    w[q] = __ldg(a.psi + (g | half));
+                    u[q] = __ldg(psi + g);
+                    w[q] = __ldg(psi + (g | half));
                 }
 #pragma unroll
                 for (int q = 0; q < LB; ++q) {
@@ -162,8 +162,8 @@ __device__ __forceinline__ void pass_prologue(typename Cfg::C2 (&v)[Cfg::E], con
 #pragma unroll
         for (int k = 0; k < Cfg::E; ++k) {
             const unsigned long long g = tile_gidx<Cfg>(gbase, a.lo_g, Cfg::elem(t, k, A0));
-            const float2 u = __ldg(a.psi + g);
-            const float2 w = __ldg(a.psi + (g | half));
+            const float2 u = __ldg(psi + g);
+            const float2 w = __ldg(psi + (g | half));
             const R ux = u.x, uy = u.y, wx = w.x, wy = w.y;
             v[k].x = fma(ux, ux, uy * uy);
             v[k].y = fma(wx, wx, wy * wy);
@@ -228,10 +228,17 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const Pas
     const int N = a.N;
     const int n = a.n;
     const unsigned long long dmask = (N >= 64) ? ~0ULL : ((1ULL << N) - 1ULL);
-    unsigned long long x = 0;
+    unsigned long long x = 0, F = 0;
     if constexpr (SRC == SRC_PSI_FAMILY || DST == DST_MOMENTS || DST == DST_SPECTRUM || DST == DST_NULLCOUNT) {
-        x = a.xs ? a.xs[a.fam_base + slot] : (unsigned long long)(a.fam_base + slot);
-        x &= dmask;
+        F = a.xs ? a.xs[a.fam_base + slot] : (unsigned long long)(a.fam_base + slot);
+        x = F & dmask;
+    }
+    const float2 *psi = a.psi;        // per-state psi / s in multi-state launches
+    const double *s_ptr = a.s_ptr;
+    if (a.psi_list) {
+        const unsigned long long st = F >> N;
+        psi = a.psi_list[st];
+        s_ptr = a.s_list + st;
     }
     const int j = x ? 63 - __clzll((long long)x) : n;
     const unsigned long long half = 1ULL << n;
@@ -249,7 +256,7 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const Pas
     constexpr int AL = Maps<Cfg>::last;
 
     // ---------------------------------------------------------- prologue
-    pass_prologue<Cfg, SRC>(v, a, slot, x, j, half, gbase, t);
+    pass_prologue<Cfg, SRC>(v, a, psi, slot, x, j, half, gbase, t);
 
     // --------------------------------------------------------- transform
     tile_transform<Cfg>(v, sm, t, grp);
@@ -287,7 +294,7 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const Pas
         }
     } else if constexpr (DST == DST_SPECTRUM) {
         if (active) {
-            const R s = (R)(*a.s_ptr);
+            const R s = (R)(*s_ptr);
             R *out = reinterpret_cast<R *>(a.spec_out) + (size_t)slot * (size_t)(2 * half);
 #pragma unroll
             for (int k = 0; k < Cfg::E; ++k) {
@@ -299,7 +306,7 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const Pas
             }
         }
     } else if constexpr (DST == DST_NULLCOUNT) {
-        const R s = (R)(*a.s_ptr);
+        const R s = (R)(*s_ptr);
         const R sc = x ? (R)2 * s : s;
         double cnt = 0.0;
 #pragma unroll
@@ -317,7 +324,7 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const Pas
         // z' = zb | k for slot k (last mapping: slot bits are the low RB bits).
         // q = (c(z0)^2, c(z1)^2) up to the order fixed by the parity, kept as
         // a packed pair: moments only need the unordered pair.
-        const float s = (float)(*a.s_ptr);
+        const float s = (float)(*s_ptr);
         const int RL = a.range_log2;
         const uint32_t zb = (uint32_t)gbase | Cfg::elem(t, 0, 0);
         float2 s2 = make_float2(0.f, 0.f), s4 = s2, s6 = s2, sl = s2, w = s2;

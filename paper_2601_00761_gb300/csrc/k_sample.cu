@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(Cfg::NT) zsample_kernel(const PassArgs a, cons
     const unsigned long long gbase = tile << Cfg::M;
 
     C2 v[Cfg::E];
-    pass_prologue<Cfg, SRC>(v, a, slot, x, j, half, gbase, t);
+    pass_prologue<Cfg, SRC>(v, a, a.psi, slot, x, j, half, gbase, t);
     tile_transform<Cfg>(v, sm, t, 0);
     __syncthreads();
 

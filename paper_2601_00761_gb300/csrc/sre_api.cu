@@ -4,7 +4,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <atomic>
+#include <cstdlib>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -61,6 +63,56 @@ struct Plan {
 };
 
 int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// ------------------------------------------------------------ autotuner table
+// Best (radix_log2, tile_log2, x_batch) per N found by sre_autotune; used when
+// the caller leaves all three options at 0. Optionally persisted in the file
+// named by SRE_TUNE_FILE (lines "N radix tile x_batch").
+struct TuneEntry { int radix = 0, tile = 0, xbatch = 0; bool valid = false; };
+std::mutex g_tune_mu;
+TuneEntry g_tune[33];
+bool g_tune_loaded = false;
+
+void tune_load_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *fn = getenv("SRE_TUNE_FILE");
+    if (!fn) return;
+    FILE *f = fopen(fn, "r");
+    if (!f) return;
+    int N, r, t, b;
+    while (fscanf(f, "%d %d %d %d", &N, &r, &t, &b) == 4)
+        if (N >= 1 && N <= 32) { g_tune[N].radix = r; g_tune[N].tile = t; g_tune[N].xbatch = b; g_tune[N].valid = true; }
+    fclose(f);
+}
+
+void tune_save_locked() {
+    const char *fn = getenv("SRE_TUNE_FILE");
+    if (!fn) return;
+    FILE *f = fopen(fn, "w");
+    if (!f) return;
+    for (int N = 1; N <= 32; ++N)
+        if (g_tune[N].valid) fprintf(f, "%d %d %d %d\n", N, g_tune[N].radix, g_tune[N].tile, g_tune[N].xbatch);
+    fclose(f);
+}
+
+sre_status plan_for(int N, const sre_opts *o, int prec, Plan &P);
+
+sre_status plan_for_tuned(int N, const sre_opts *o, int prec, Plan &P) {
+    sre_opts t;
+    sre_default_opts(&t);
+    if (o) t = *o;
+    if (prec == 32 && t.radix_log2 == 0 && t.tile_log2 == 0 && t.x_batch == 0) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load_locked();
+        if (N >= 1 && N <= 32 && g_tune[N].valid) {
+            t.radix_log2 = g_tune[N].radix;
+            t.tile_log2 = g_tune[N].tile;
+            t.x_batch = g_tune[N].xbatch;
+        }
+    }
+    return plan_for(N, &t, prec, P);
+}
 
 sre_status plan_for(int N, const sre_opts *o, int prec, Plan &P) {
     P = Plan();
@@ -423,7 +475,7 @@ sre_status nullity_from_count(long long cnt, int N, sre_result *r) {
 sre_status exact_impl(const void *psi, int N, const sre_opts &o, void *ws, size_t ws_bytes, cudaStream_t st,
                       sre_result *out) {
     Plan P, P64;
-    CS(plan_for(N, &o, 32, P));
+    CS(plan_for_tuned(N, &o, 32, P));
     CS(plan_for(N, nullptr, 64, P64));
     Arena dry(nullptr);
     ExactWS w;
@@ -489,6 +541,311 @@ sre_status exact_impl(const void *psi, int N, const sre_opts &o, void *ws, size_
     return nullity_from_count((long long)cnt, N, out);
 }
 
+
+// ---------------------------------------------------------------- batched
+// Exact sweeps of many states of possibly different N (sre_exact_batched).
+// States are grouped by N into buckets. For each bucket one launch sequence
+// covers every (state, family) item of a chunk of states: the pass kernels
+// resolve the family index F = (state << N) | x into the state's psi and s.
+// Per-state totals come from a fixed-order segmented reduction. The whole
+// sequence of every bucket is captured once into a CUDA graph (cached per
+// batch shape and workspace) and replayed; the FP64 nullity recheck of the
+// candidate families follows as a second, short sequence.
+constexpr long long BATCH_CHUNK_FAMILIES = 1LL << 21;
+
+struct BucketPlan {
+    int N;
+    std::vector<int> idx;       // caller indices of the bucket's states
+    int off;                    // first slot of the bucket in the per-state arrays
+    Plan P, P64;
+    int states_per_chunk;
+    unsigned long long *flags;  // flagged families of the bucket (capacity: its families)
+    long long flag_cap;
+};
+
+struct BatchWS {
+    const float2 **psi_list;
+    double *s_list, *norm_list, *npart, *totals;
+    unsigned long long *state_count, *nflag, *counts;
+    FamMoments *fm;
+    TilePartial *tiles;
+    void *inter, *inter64;
+};
+
+constexpr int BATCH_NORM_BLOCKS = 16;
+
+struct BatchGraph {
+    std::vector<int> shape;     // N of every slot, in slot order
+    void *ws = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long kernels = 0;
+};
+std::mutex g_bgraph_mu;
+std::vector<BatchGraph> g_bgraph;
+
+void layout_batch(Arena &A, int count, std::vector<BucketPlan> &B, BatchWS &w) {
+    w.psi_list = A.take<const float2 *>(count);
+    w.s_list = A.take<double>(count);
+    w.norm_list = A.take<double>(count);
+    w.npart = A.take<double>((size_t)count * BATCH_NORM_BLOCKS);
+    w.totals = A.take<double>(5 * (size_t)count);
+    w.state_count = A.take<unsigned long long>(count);
+    w.nflag = A.take<unsigned long long>(B.size());
+    size_t fm_n = 0, tiles_n = 0, inter_b = 0, inter64_b = 0, counts_n = 0;
+    for (auto &b : B) {
+        const long long fams = (long long)b.idx.size() << b.N;
+        b.flags = A.take<unsigned long long>((size_t)fams);
+        b.flag_cap = fams;
+        const long long chunk = (long long)b.states_per_chunk << b.N;
+        fm_n = std::max(fm_n, (size_t)chunk);
+        if (b.P.npass == 1) tiles_n = std::max(tiles_n, (size_t)chunk);
+        else {
+            tiles_n = std::max(tiles_n, (size_t)(b.P.B * b.P.tiles_last));
+            inter_b = std::max(inter_b, b.P.slot_bytes * (size_t)b.P.B);
+        }
+        if (b.P64.npass > 1) inter64_b = std::max(inter64_b, b.P64.slot_bytes * (size_t)b.P64.B);
+        counts_n = std::max(counts_n, (size_t)fams);
+    }
+    w.fm = A.take<FamMoments>(fm_n);
+    w.tiles = A.take<TilePartial>(tiles_n);
+    w.inter = inter_b ? (void *)A.take<char>(inter_b) : nullptr;
+    w.inter64 = inter64_b ? (void *)A.take<char>(inter64_b) : nullptr;
+    w.counts = A.take<unsigned long long>(counts_n);
+}
+
+// the main launch sequence of every bucket (captured into the graph)
+sre_status batch_main(const std::vector<BucketPlan> &B, const BatchWS &w, int count, cudaStream_t st) {
+    CK(cudaMemsetAsync(w.nflag, 0, sizeof(unsigned long long) * B.size(), st));
+    CK(cudaMemsetAsync(w.state_count, 0, sizeof(unsigned long long) * count, st));
+    for (size_t bi = 0; bi < B.size(); ++bi) {
+        const BucketPlan &b = B[bi];
+        const int ns = (int)b.idx.size();
+        CK(launch_norm2_multi(w.psi_list + b.off, ns, b.N, w.npart, BATCH_NORM_BLOCKS, w.norm_list + b.off,
+                              w.s_list + b.off, st));
+        count_launches(2);
+        PassArgs a = base_args(b.P, nullptr, w.s_list + b.off);
+        a.psi_list = w.psi_list + b.off;
+        a.s_list = w.s_list + b.off;
+        a.tile_out = w.tiles;
+        for (int c0 = 0; c0 < ns; c0 += b.states_per_chunk) {
+            const int c1 = std::min(ns, c0 + b.states_per_chunk);
+            const long long f0 = (long long)c0 << b.N, f1 = (long long)c1 << b.N;
+            const long long step = b.P.npass > 1 ? b.P.B : (f1 - f0);
+            for (long long fb = f0; fb < f1; fb += step) {
+                const long long nf = std::min(step, f1 - fb);
+                PassArgs c = a;
+                c.fam_base = fb;
+                c.n_fam = nf;
+                CS(run_transform(b.P, c, SRC_PSI_FAMILY, DST_MOMENTS, w.inter, st));
+                CK(launch_fam_reduce(w.tiles, nf, (int)b.P.tiles_last, nullptr, fb, b.N, b.P.M_last, b.P.M_last,
+                                     w.fm, fb - f0, nullptr, 0, st));
+                count_launches(1);
+            }
+            CK(launch_state_totals(w.fm, f0, b.N, c0, c1 - c0, w.totals + 5 * (size_t)b.off, b.flags,
+                                   w.nflag + bi, st));
+            count_launches(1);
+        }
+    }
+    return SRE_OK;
+}
+
+sre_status batched_impl(const void *const *psi_ptrs, const int *Ns, int count, const sre_opts &o,
+                        cudaStream_t st, sre_result *out) {
+    // buckets by N, largest first
+    std::vector<BucketPlan> B;
+    {
+        std::vector<std::vector<int>> by(21);
+        for (int i = 0; i < count; ++i) by[Ns[i]].push_back(i);
+        int off = 0;
+        for (int N = 20; N >= 1; --N) {
+            if (by[N].empty()) continue;
+            BucketPlan b;
+            b.N = N;
+            b.idx = by[N];
+            b.off = off;
+            off += (int)b.idx.size();
+            CS(plan_for_tuned(N, &o, 32, b.P));
+            CS(plan_for(N, nullptr, 64, b.P64));
+            b.states_per_chunk = (int)std::max(1LL, BATCH_CHUNK_FAMILIES >> N);
+            b.flags = nullptr;
+            b.flag_cap = 0;
+            B.push_back(b);
+        }
+    }
+    Arena dry(nullptr);
+    BatchWS w;
+    layout_batch(dry, count, B, w);
+    void *base = nullptr;
+    CS(own_workspace(dry.off, &base));
+    Arena A(base);
+    layout_batch(A, count, B, w);
+
+    // psi pointers in slot (bucket) order
+    std::vector<const float2 *> hp(count);
+    std::vector<int> shape(count);
+    for (const auto &b : B)
+        for (size_t k = 0; k < b.idx.size(); ++k) {
+            hp[b.off + k] = (const float2 *)psi_ptrs[b.idx[k]];
+            shape[b.off + k] = b.N;
+        }
+    CK(cudaMemcpyAsync((void *)w.psi_list, hp.data(), sizeof(const float2 *) * count, cudaMemcpyHostToDevice, st));
+
+    // main sequence: replay a cached graph of the same shape on the same workspace, else capture one
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long kernels = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_bgraph_mu);
+        for (auto &g : g_bgraph)
+            if (g.ws == base && g.shape == shape) { exec = g.exec; kernels = g.kernels; break; }
+    }
+    if (!exec) {
+        cudaStream_t cap;
+        CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaGraph_t graph;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) { cudaStreamDestroy(cap); return fail(SRE_ECUDA, "capture: %s", cudaGetErrorString(e)); }
+        const unsigned long long l0 = g_launches.load();
+        sre_status s1 = batch_main(B, w, count, cap);
+        e = cudaStreamEndCapture(cap, &graph);
+        cudaStreamDestroy(cap);
+        if (s1 != SRE_OK) { if (e == cudaSuccess) cudaGraphDestroy(graph); return s1; }
+        if (e != cudaSuccess) return fail(SRE_ECUDA, "end capture: %s", cudaGetErrorString(e));
+        kernels = g_launches.load() - l0;
+        g_launches.fetch_sub(kernels);   // counted when the graph runs
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(SRE_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        std::lock_guard<std::mutex> lk(g_bgraph_mu);
+        BatchGraph g;
+        g.shape = shape;
+        g.ws = base;
+        g.exec = exec;
+        g.kernels = kernels;
+        g_bgraph.push_back(g);
+    }
+    CK(cudaGraphLaunch(exec, st));
+    count_launches(kernels);
+
+    std::vector<unsigned long long> nflag(B.size());
+    CK(cudaMemcpyAsync(nflag.data(), w.nflag, sizeof(unsigned long long) * B.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+
+    // FP64 recheck of the candidate families, per bucket
+    for (size_t bi = 0; bi < B.size(); ++bi) {
+        const BucketPlan &b = B[bi];
+        const long long nf = (long long)nflag[bi];
+        if (nf <= 0) continue;
+        CK(cudaMemsetAsync(w.counts, 0, sizeof(unsigned long long) * nf, st));
+        PassArgs c = base_args(b.P64, nullptr, w.s_list + b.off);
+        c.psi_list = w.psi_list + b.off;
+        c.s_list = w.s_list + b.off;
+        c.xs = b.flags;
+        c.eps = o.eps_null;
+        const long long step = b.P64.npass > 1 ? b.P64.B : (1LL << 20);
+        for (long long fb = 0; fb < nf; fb += step) {
+            PassArgs d = c;
+            d.fam_base = fb;
+            d.n_fam = std::min(step, nf - fb);
+            d.count_out = w.counts + fb;
+            CS(run_transform(b.P64, d, SRC_PSI_FAMILY, DST_NULLCOUNT, w.inter64, st));
+        }
+        CK(launch_count_scatter(b.flags, w.counts, nf, b.N, w.state_count + b.off, st));
+        count_launches(1);
+    }
+    std::vector<double> tot(5 * (size_t)count), nrm(count);
+    std::vector<unsigned long long> cnt(count);
+    CK(cudaMemcpyAsync(tot.data(), w.totals, sizeof(double) * 5 * count, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(nrm.data(), w.norm_list, sizeof(double) * count, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(cnt.data(), w.state_count, sizeof(unsigned long long) * count, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    bool zero = false;
+    for (const auto &b : B)
+        for (size_t k = 0; k < b.idx.size(); ++k) {
+            const int slot = b.off + (int)k;
+            sre_result *r = out + b.idx[k];
+            init_result(r);
+            finalize_exact(&tot[5 * (size_t)slot], b.N, r);
+            r->n_families = 1LL << b.N;
+            r->n_passes = b.P.npass;
+            if (!(nrm[slot] > 0.0)) { zero = true; continue; }
+            nullity_from_count((long long)cnt[slot], b.N, r);   // nullity -1 if not a power of two
+        }
+    if (zero) return fail(SRE_EZERO, "a state of the batch has zero norm");
+    return SRE_OK;
+}
+
+// --------------------------------------------------------------- autotuner
+// Times the family-transform launch sequence of every admissible plan for N
+// on the caller's state and keeps the fastest (radix, tile, x_batch).
+sre_status autotune_impl(const void *psi, int N, cudaStream_t st, sre_opts *best) {
+    sre_default_opts(best);
+    Plan P0;
+    CS(plan_for(N, nullptr, 32, P0));
+    if (P0.npass == 1) return SRE_OK;   // nothing to choose
+    struct Cand { int radix, tile, xb; };
+    std::vector<Cand> cands;
+    for (int r = F32_ROW_MMIN; r <= F32_ROW_MMAX; ++r)
+        for (int t : {0, 8})
+            for (int xb : {0, 8})
+                cands.push_back({r, t, xb});
+    double best_rate = -1.0;
+    const long long d = 1LL << N;
+    for (const Cand &c : cands) {
+        sre_opts q;
+        sre_default_opts(&q);
+        q.radix_log2 = c.radix;
+        q.tile_log2 = c.tile;
+        q.x_batch = c.xb;
+        Plan P;
+        if (plan_for(N, &q, 32, P) != SRE_OK) continue;
+        const long long fams = std::min(d, std::max(P.B * 4, 64LL));
+        Arena dry(nullptr);
+        McWS w;
+        layout_mc(dry, P, SRE_MC_UNIFORM, fams, 1, w);
+        void *base = nullptr;
+        CS(own_workspace(dry.off, &base));
+        Arena A(base);
+        layout_mc(A, P, SRE_MC_UNIFORM, fams, 1, w);
+        CK(launch_norm2((const float2 *)psi, N, w.scal, w.npart, st));
+        count_launches(2);
+        PassArgs a = base_args(P, psi, w.scal);
+        a.tile_out = w.tiles;
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {   // rep 0 warms up
+            CK(cudaEventRecord(e0, st));
+            for (long long fb = 0; fb < fams; fb += P.B) {
+                PassArgs b = a;
+                b.fam_base = fb;
+                b.n_fam = std::min(P.B, fams - fb);
+                CS(run_transform(P, b, SRC_PSI_FAMILY, DST_MOMENTS, w.inter, st));
+            }
+            CK(cudaEventRecord(e1, st));
+            CK(cudaEventSynchronize(e1));
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        const double rate = (double)fams * (double)d / (ms * 1e-3);
+        if (rate > best_rate) {
+            best_rate = rate;
+            best->radix_log2 = c.radix;
+            best->tile_log2 = c.tile;
+            best->x_batch = c.xb;
+        }
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    g_tune[N].radix = best->radix_log2;
+    g_tune[N].tile = best->tile_log2;
+    g_tune[N].xbatch = best->x_batch;
+    g_tune[N].valid = true;
+    tune_save_locked();
+    return SRE_OK;
+}
+
 } // namespace
 
 namespace sre {
@@ -516,7 +873,7 @@ sre_status sre_make_plan(int N, const sre_opts *opts, sre_plan *plan) {
     sre_opts o;
     CS(check_opts(opts, o));
     Plan P;
-    CS(plan_for(N, &o, 32, P));
+    CS(plan_for_tuned(N, &o, 32, P));
     memset(plan, 0, sizeof *plan);
     plan->N = N;
     plan->n_bits = P.n;
@@ -541,7 +898,7 @@ sre_status sre_workspace_bytes(int N, int mode, long long n_x, int z_per_x, cons
     if (mode == -1) {
         if (N < 1 || N > 26) return fail(SRE_EINVAL, "exact: N=%d outside 1..26", N);
         Plan P64;
-        CS(plan_for(N, &o, 32, P));
+        CS(plan_for_tuned(N, &o, 32, P));
         CS(plan_for(N, nullptr, 64, P64));
         Arena A(nullptr);
         ExactWS w;
@@ -552,7 +909,7 @@ sre_status sre_workspace_bytes(int N, int mode, long long n_x, int z_per_x, cons
     if (mode != SRE_MC_UNIFORM && mode != SRE_MC_MARGINAL) return fail(SRE_EINVAL, "unknown mode %d", mode);
     if (N < 2 || N > 30) return fail(SRE_EINVAL, "mc: N=%d outside 2..30", N);
     if (n_x < 2 || (mode == SRE_MC_MARGINAL && z_per_x < 1)) return fail(SRE_EINVAL, "n_x >= 2 and z_per_x >= 1 required");
-    CS(plan_for(N, &o, 32, P));
+    CS(plan_for_tuned(N, &o, 32, P));
     Arena A(nullptr);
     McWS w;
     layout_mc(A, P, mode, n_x, z_per_x, w);
@@ -607,11 +964,14 @@ sre_status sre_exact_batched(const void *const *psi_ptrs, const int *Ns, int cou
     for (int i = 0; i < count; ++i) CS(check_psi(psi_ptrs[i], Ns[i], 1, 20));
     if (workspace) return fail(SRE_ENOTSUP, "sre_exact_batched uses the library workspace (pass NULL)");
     (void)workspace_bytes;
-    for (int i = 0; i < count; ++i) {
-        sre_status s = exact_impl(psi_ptrs[i], Ns[i], o, nullptr, 0, (cudaStream_t)stream, out + i);
-        if (s != SRE_OK && s != SRE_ENULLITY) return s;
-    }
-    return SRE_OK;
+    if (count == 0) return SRE_OK;
+    return batched_impl(psi_ptrs, Ns, count, o, (cudaStream_t)stream, out);
+}
+
+sre_status sre_autotune(const void *psi, int N, void *stream, sre_opts *best) {
+    CS(check_psi(psi, N, 2, 26));
+    if (!best) return fail(SRE_EINVAL, "best is NULL");
+    return autotune_impl(psi, N, (cudaStream_t)stream, best);
 }
 
 sre_status sre_mc(const void *psi, int N, int mode, long long n_x, int z_per_x, unsigned long long seed,
@@ -629,7 +989,7 @@ sre_status sre_mc(const void *psi, int N, int mode, long long n_x, int z_per_x, 
     CS(check_opts(opts, o));
     cudaStream_t st = (cudaStream_t)stream;
     Plan P;
-    CS(plan_for(N, &o, 32, P));
+    CS(plan_for_tuned(N, &o, 32, P));
     Arena dry(nullptr);
     McWS w;
     layout_mc(dry, P, mode, n_x, z_per_x, w);
@@ -797,7 +1157,7 @@ sre_status sre_family_spectrum(const void *psi, int N, unsigned long long x, con
     CS(check_opts(opts, o));
     cudaStream_t st = (cudaStream_t)stream;
     Plan P;
-    CS(plan_for(N, &o, 32, P));
+    CS(plan_for_tuned(N, &o, 32, P));
     void *base = nullptr;
     CS(own_workspace(sizeof(double) * (SCAL_N + NORM_BLOCKS) + P.slot_bytes + 4096, &base));
     Arena A(base);
@@ -938,7 +1298,7 @@ sre_status sre_profile_passes(const void *psi, int N, long long n_x, const sre_o
     CS(check_opts(opts, o));
     cudaStream_t st = (cudaStream_t)stream;
     Plan P;
-    CS(plan_for(N, &o, 32, P));
+    CS(plan_for_tuned(N, &o, 32, P));
     Arena dry(nullptr);
     McWS w;
     layout_mc(dry, P, SRE_MC_UNIFORM, n_x < 2 ? 2 : n_x, 1, w);

@@ -215,6 +215,11 @@ struct PassArgs {
     double eps;                        // nullity tolerance
     float cand_thr;                    // FP32 candidate threshold
     int want_ranges;                   // DST_MOMENTS: also produce the z-range weights
+    // Several states of the same N in one launch: the family index F (from xs
+    // or fam_base + slot) is (state << N) | x; psi and s come from these
+    // per-state device arrays. NULL for the one-state entry points.
+    const float2 *const *psi_list;
+    const double *s_list;
     int *err_flag;                     // device error word (bounds checks)
 };
 

@@ -1,0 +1,82 @@
+"""GPU: the batched exact sweep (one launch per same-N chunk, captured into a
+CUDA graph) against sre_exact per state, the graph replay on new states of
+the same shape, and the autotuner."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_00761_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_M = 1e-5
+
+
+@pytest.fixture(scope="module")
+def sre():
+    import paper_2601_00761_gb300 as s
+    from paper_2601_00761_gb300 import build
+    build.build()
+    s.load()
+    return s
+
+
+def _state(sre, spec):
+    p = torch.zeros(1 << spec["N"], dtype=torch.complex64, device="cuda")
+    p[0] = 1
+    sre.apply_clifford_tdoped_circuit(p, inputs.batched_gate_list(spec))
+    return p
+
+
+def _check(sre, states, res):
+    for p, r in zip(states, res):
+        ref = sre.sre_exact(p, allow_nullity_error=True)
+        assert np.max(np.abs(np.array(r["M"]) - np.array(ref["M"]))) < TOL_M
+        assert r["nullity"] == ref["nullity"] and r["stab_count"] == ref["stab_count"]
+
+
+def test_batched_uneven_matches_per_state(sre):
+    specs = inputs.workload_batched_specs(count=48, seed0=4000, n_min=1, n_max=16)
+    states = [_state(sre, s) for s in specs]
+    states.append(torch.from_numpy(inputs.t_product_state(16, 5)).cuda())   # closed form, 2 passes
+    states.append(torch.from_numpy(inputs.haar_state(11, 2)).cuda())
+    res = sre.sre_exact_batched(states)
+    _check(sre, states, res)
+    assert res[-2]["nullity"] == 5 and abs(res[-2]["M"][1] - 5 * np.log2(4 / 3)) < TOL_M
+
+
+def test_batched_graph_replay_with_new_states(sre):
+    Ns = [9, 12, 12, 15, 7, 9]
+    a = [torch.from_numpy(inputs.haar_state(N, 10 + i)).cuda() for i, N in enumerate(Ns)]
+    b = [torch.from_numpy(inputs.t_product_state(N, i % N)).cuda() for i, N in enumerate(Ns)]
+    ra = sre.sre_exact_batched(a)
+    rb = sre.sre_exact_batched(b)        # same shape: the cached graph runs on new pointers
+    _check(sre, a, ra)
+    _check(sre, b, rb)
+
+
+def test_batched_small_vs_oracle(sre):
+    specs = inputs.workload_batched_specs(count=6, seed0=77, n_min=3, n_max=8)
+    states, refs = [], []
+    for s in specs:
+        psi = oracle.circuit_state(s["N"], inputs.batched_gate_list(s))
+        states.append(torch.from_numpy(psi).cuda())
+        refs.append(oracle.sre_exact(psi))
+    res = sre.sre_exact_batched(states)
+    for r, ref in zip(res, refs):
+        assert np.max(np.abs(np.array(r["M"]) - ref["M"])) < TOL_M
+        assert r["nullity"] == ref["nullity"]
+
+
+def test_autotune_keeps_results(sre):
+    psi = torch.from_numpy(inputs.haar_state(18, 9)).cuda()
+    before = sre.sre_exact(psi)
+    best = sre.sre_autotune(psi)
+    assert 10 <= best["radix_log2"] <= 14
+    plan = sre.sre_make_plan(18)
+    assert plan["pass_bits"][-1] == best["radix_log2"]
+    after = sre.sre_exact(psi)
+    assert np.max(np.abs(np.array(after["M"]) - np.array(before["M"]))) < TOL_M
+    c = sre.sre_family_spectrum(psi, 12345).cpu().numpy()
+    assert np.max(np.abs(c - oracle.family_spectrum(inputs.haar_state(18, 9), 12345))) < 1e-6
