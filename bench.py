@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tc", action="store_true")
     ap.add_argument("--workload", default="mc24", choices=["mc24", "batched"],
                     help="mc24: the headline N=24 MC step; batched: exact M_2/nullity of 4096 T-doped states "
                          "with N ~ U{8..16} in one sre_exact_batched call, against a per-state loop")
@@ -283,6 +284,38 @@ def run_cuda(a):
                 "pass_ms_share": [s / sum(shares) for s in shares],
                 "step_algorithmic_GBps": step_bytes / (ms / a.steps / 1e3) / 1e9 / world * world}
 
+    # the split-BF16 tensor-core form on the same workload (BF16X3: FP32-level accuracy)
+    tc = None
+    if not a.no_tc:
+        kw_tc = dict(kw, precision=2)
+        def step_tc(i):
+            return sre.sre_mc(psi, sre.SRE_MC_MARGINAL, n_x, zpx, seed=24, counter0=base_ctr + (1 << 31) + i * n_x,
+                              workspace=ws, outputs=(xs, zs, cs), **kw_tc)
+        step_tc(0)
+        torch.cuda.synchronize()
+        sre.sre_pass_timing(True)
+        t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0e.record(stream)
+        tc_steps = max(1, min(a.steps, 3))
+        for i in range(tc_steps):
+            rtc = step_tc(1 + i)
+        t1e.record(stream)
+        torch.cuda.synchronize()
+        tt = sre.sre_pass_timing(False)
+        tms = t0e.elapsed_time(t1e)
+        if world > 1:
+            t = torch.tensor([tms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tms = float(t.item())
+        tdom = int(np.argmax([tt["ms_sum"][p] for p in range(npass)]))
+        tavg = tt["ms_sum"][tdom] / max(1, tt["launches"][tdom])
+        tach = tt["bytes_per_launch"][tdom] / (tavg / 1e3) / 1e9
+        tc = {"precision": "split-BF16 x3 (mma.sync m16n8k16, FP32 accumulate)",
+              "value": world * tc_steps * n_x * float(2 ** N) / (tms / 1e3), "unit": UNIT,
+              "ms_per_step": tms / tc_steps, "dominant_pass": tdom, "achieved_GBps": tach, "frac": tach / hbm,
+              "pass_ms_share": [tt["ms_sum"][p] / sum(tt["ms_sum"][:npass]) for p in range(npass)],
+              "M_rb": rtc["M_rb"], "err_rb": rtc["err_rb"]}
+
     # end to end through the public API with host buffers
     e2e = None
     if not a.no_e2e:
@@ -327,7 +360,7 @@ def run_cuda(a):
                            "N": N, "n_x_per_step": n_x, "z_per_x": zpx, "seed": 24, "precision": "FP32 SIMT",
                            "passes": npass, "l2": "inputs larger than L2: psi is 128 MiB and every step "
                                                   "streams GiBs of intermediate", "parallelism": f"replica x{world}"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "roofline": roofline, "tensor_core_form": tc, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": int(launches),
                 "estimates": {"M": res["M"], "err_M": res["err_M"], "M_rb": res["M_rb"], "err_rb": res["err_rb"],
                               "M2_haar_closed_form": math.log2(2 ** N + 3) - 2}}

@@ -15,6 +15,7 @@
 #pragma once
 
 #include "sre_internal.cuh"
+#include "k_tc.cuh"
 
 namespace sre {
 
@@ -200,13 +201,13 @@ __device__ __forceinline__ void family_pair(unsigned long long x, int j, R s, C2
     }
 }
 
-template <class Cfg, int SRC, int DST>
+template <class Cfg, int SRC, int DST, int PREC = 0>
 __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const PassArgs a) {
     typedef typename Cfg::Real R;
     typedef typename Cfg::C2 C2;
     extern __shared__ __align__(16) unsigned char smraw[];
     C2 *sm = reinterpret_cast<C2 *>(smraw);
-    constexpr size_t TILE_SMEM = Cfg::NR > 1 ? sizeof(C2) * (size_t)Cfg::G * Cfg::PSIZE : 0;
+    constexpr size_t TILE_SMEM = (Cfg::NR > 1 || PREC != 0) ? sizeof(C2) * (size_t)Cfg::G * Cfg::PSIZE : 0;
     double *red = reinterpret_cast<double *>(smraw + TILE_SMEM);
 
     const uint32_t tid = threadIdx.x;
@@ -259,7 +260,8 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const Pas
     pass_prologue<Cfg, SRC>(v, a, psi, slot, x, j, half, gbase, t);
 
     // --------------------------------------------------------- transform
-    tile_transform<Cfg>(v, sm, t, grp);
+    if constexpr (PREC == 0) tile_transform<Cfg>(v, sm, t, grp);
+    else tc_tile_transform<Cfg, PREC>(v, sm, t, grp);
 
     // ---------------------------------------------------------- epilogue
     if constexpr (DST == DST_BUF) {
@@ -389,13 +391,13 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const Pas
     }
 }
 
-template <class Cfg, int SRC, int DST>
+template <class Cfg, int SRC, int DST, int PREC = 0>
 cudaError_t launch_cfg(const PassArgs &a, int tiles, cudaStream_t st) {
-    const size_t tile_smem = Cfg::NR > 1 ? sizeof(typename Cfg::C2) * (size_t)Cfg::G * Cfg::PSIZE : 0;
+    const size_t tile_smem = (Cfg::NR > 1 || PREC != 0) ? sizeof(typename Cfg::C2) * (size_t)Cfg::G * Cfg::PSIZE : 0;
     const size_t smem = tile_smem + sizeof(double) * (8 * (Cfg::NT / 32) + 8);
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(fwht_pass_kernel<Cfg, SRC, DST>,
+        cudaError_t e = cudaFuncSetAttribute(fwht_pass_kernel<Cfg, SRC, DST, PREC>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_done = true;
@@ -407,7 +409,7 @@ cudaError_t launch_cfg(const PassArgs &a, int tiles, cudaStream_t st) {
         const long long nf = a.n_fam;
         grid = dim3((unsigned)tiles, (unsigned)(nf < 65535 ? nf : 65535), (unsigned)((nf + 65534) / 65535));
     }
-    fwht_pass_kernel<Cfg, SRC, DST><<<grid, Cfg::NT, smem, st>>>(a);
+    fwht_pass_kernel<Cfg, SRC, DST, PREC><<<grid, Cfg::NT, smem, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -1,6 +1,7 @@
 // k_pass_dispatch.cuh -- (source, destination) combinations each tile
 // geometry is instantiated for, shared by the k_pass_*.cu units.
 #pragma once
+#include <type_traits>
 #include "k_pass.cuh"
 
 namespace sre {
@@ -32,12 +33,25 @@ SRE_ALLOW(double, KIND_ROW, SRC_BUF, DST_SQMAP)
 SRE_ALLOW(double, KIND_ROW, SRC_BUF, DST_P)
 #undef SRE_ALLOW
 
+// Tensor-core variants exist for FP32 tiles whose groups are whole warps.
+template <class Cfg> struct TcOK {
+    static constexpr bool value = std::is_same<typename Cfg::Real, float>::value && Cfg::T >= 32;
+};
+
 template <int KIND, class Cfg, int SRC, int DST>
 cudaError_t launch_if(const PassArgs &a, int tiles, cudaStream_t st) {
-    if constexpr (AllowedK<typename Cfg::Real, KIND, SRC, DST, Cfg::M, Cfg::LO, Cfg::RB, Cfg::G>::value)
-        return launch_cfg<Cfg, SRC, DST>(a, tiles, st);
-    else
+    if constexpr (AllowedK<typename Cfg::Real, KIND, SRC, DST, Cfg::M, Cfg::LO, Cfg::RB, Cfg::G>::value) {
+        if (a.precision == 0) return launch_cfg<Cfg, SRC, DST, 0>(a, tiles, st);
+        if constexpr (TcOK<Cfg>::value) {
+            if (a.precision == 2) return launch_cfg<Cfg, SRC, DST, 2>(a, tiles, st);
+            if (a.precision == 3) return launch_cfg<Cfg, SRC, DST, 3>(a, tiles, st);
+        } else {
+            return launch_cfg<Cfg, SRC, DST, 0>(a, tiles, st);   // tiles below one warp: FP32 butterflies
+        }
         return cudaErrorInvalidValue;
+    } else {
+        return cudaErrorInvalidValue;
+    }
 }
 
 template <int KIND, class Cfg>

@@ -13,7 +13,7 @@
 
 namespace sre {
 
-template <class Cfg, int SRC>
+template <class Cfg, int SRC, int PREC>
 __global__ void __launch_bounds__(Cfg::NT) zsample_kernel(const PassArgs a, const DrawInfo *draws, int z_per_x,
                                                           unsigned long long *zs, float *cz) {
     typedef float R;
@@ -43,7 +43,8 @@ __global__ void __launch_bounds__(Cfg::NT) zsample_kernel(const PassArgs a, cons
 
     C2 v[Cfg::E];
     pass_prologue<Cfg, SRC>(v, a, a.psi, slot, x, j, half, gbase, t);
-    tile_transform<Cfg>(v, sm, t, 0);
+    if constexpr (PREC == 0) tile_transform<Cfg>(v, sm, t, 0);
+    else tc_tile_transform<Cfg, PREC>(v, sm, t, 0);
     __syncthreads();
 
     // The range's c^2 in z order as u32 fixed-point quanta (scale 2^31 per
@@ -123,21 +124,32 @@ __global__ void __launch_bounds__(Cfg::NT) zsample_kernel(const PassArgs a, cons
     }
 }
 
-template <class Cfg, int SRC>
-cudaError_t launch_zs(const PassArgs &a, const DrawInfo *draws, int z_per_x, unsigned long long *zs, float *cz,
-                      cudaStream_t st) {
+template <class Cfg, int SRC, int PREC>
+cudaError_t launch_zs1(const PassArgs &a, const DrawInfo *draws, int z_per_x, unsigned long long *zs, float *cz,
+                       cudaStream_t st) {
     const size_t smem = sizeof(float2) * (size_t)Cfg::PSIZE + sizeof(double) * ((Cfg::NT + 31) / 32 + 4);
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(zsample_kernel<Cfg, SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(zsample_kernel<Cfg, SRC, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const long long nd = a.n_fam * (long long)z_per_x;
     dim3 grid((unsigned)(nd < 65535 ? nd : 65535), (unsigned)((nd + 65534) / 65535));
-    zsample_kernel<Cfg, SRC><<<grid, Cfg::NT, smem, st>>>(a, draws, z_per_x, zs, cz);
+    zsample_kernel<Cfg, SRC, PREC><<<grid, Cfg::NT, smem, st>>>(a, draws, z_per_x, zs, cz);
     return cudaGetLastError();
+}
+
+template <class Cfg, int SRC>
+cudaError_t launch_zs(const PassArgs &a, const DrawInfo *draws, int z_per_x, unsigned long long *zs, float *cz,
+                      cudaStream_t st) {
+    if (a.precision == 0 || Cfg::T < 32) return launch_zs1<Cfg, SRC, 0>(a, draws, z_per_x, zs, cz, st);
+    if constexpr (Cfg::T >= 32) {
+        if (a.precision == 2) return launch_zs1<Cfg, SRC, 2>(a, draws, z_per_x, zs, cz, st);
+        if (a.precision == 3) return launch_zs1<Cfg, SRC, 3>(a, draws, z_per_x, zs, cz, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <int M> using SampleSingle = TileCfg<float, M, 0, (M < 5 ? M : 5), 1>;

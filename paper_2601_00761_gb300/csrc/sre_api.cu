@@ -307,8 +307,6 @@ sre_status check_opts(const sre_opts *o, sre_opts &out) {
     if (out.eps_null <= 0) out.eps_null = 1e-6;
     if (out.precision != SRE_FP32_SIMT && out.precision != SRE_BF16X2_TC && out.precision != SRE_BF16X3_TC)
         return fail(SRE_EINVAL, "unknown precision %d", out.precision);
-    if (out.precision != SRE_FP32_SIMT)
-        return fail(SRE_ENOTSUP, "precision %d is not available in this build", out.precision);
     if (out.x_batch < 0 || out.radix_log2 < 0 || out.tile_log2 < 0)
         return fail(SRE_EINVAL, "negative tiling option");
     return SRE_OK;
@@ -324,7 +322,13 @@ PassArgs base_args(const Plan &P, const void *psi, const double *scal) {
     a.range_log2 = P.M_last;
     a.s_ptr = scal + SCAL_S;
     a.cand_thr = 1.0f - 1e-4f;
+    a.precision = 0;
     return a;
+}
+
+// precision code of the FP32 family transforms for the kernels
+int prec_code(const sre_opts &o) {
+    return o.precision == SRE_BF16X3_TC ? 3 : (o.precision == SRE_BF16X2_TC ? 2 : 0);
 }
 
 
@@ -489,6 +493,7 @@ sre_status exact_impl(const void *psi, int N, const sre_opts &o, void *ws, size_
     CK(launch_norm2((const float2 *)psi, N, w.scal, w.npart, st));
     count_launches(2);
     PassArgs a = base_args(P, psi, w.scal);
+    a.precision = prec_code(o);
     a.tile_out = w.tiles;
     const long long step = P.npass > 1 ? P.B : (long long)d;
     for (long long fb = 0; fb < (long long)d; fb += step) {
@@ -579,6 +584,7 @@ struct BatchGraph {
     void *ws = nullptr;
     cudaGraphExec_t exec = nullptr;
     unsigned long long kernels = 0;
+    int prec = 0;
 };
 std::mutex g_bgraph_mu;
 std::vector<BatchGraph> g_bgraph;
@@ -614,7 +620,7 @@ void layout_batch(Arena &A, int count, std::vector<BucketPlan> &B, BatchWS &w) {
 }
 
 // the main launch sequence of every bucket (captured into the graph)
-sre_status batch_main(const std::vector<BucketPlan> &B, const BatchWS &w, int count, cudaStream_t st) {
+sre_status batch_main(const std::vector<BucketPlan> &B, const BatchWS &w, int count, int prec, cudaStream_t st) {
     CK(cudaMemsetAsync(w.nflag, 0, sizeof(unsigned long long) * B.size(), st));
     CK(cudaMemsetAsync(w.state_count, 0, sizeof(unsigned long long) * count, st));
     for (size_t bi = 0; bi < B.size(); ++bi) {
@@ -624,6 +630,7 @@ sre_status batch_main(const std::vector<BucketPlan> &B, const BatchWS &w, int co
                               w.s_list + b.off, st));
         count_launches(2);
         PassArgs a = base_args(b.P, nullptr, w.s_list + b.off);
+        a.precision = prec;
         a.psi_list = w.psi_list + b.off;
         a.s_list = w.s_list + b.off;
         a.tile_out = w.tiles;
@@ -696,7 +703,7 @@ sre_status batched_impl(const void *const *psi_ptrs, const int *Ns, int count, c
     {
         std::lock_guard<std::mutex> lk(g_bgraph_mu);
         for (auto &g : g_bgraph)
-            if (g.ws == base && g.shape == shape) { exec = g.exec; kernels = g.kernels; break; }
+            if (g.ws == base && g.shape == shape && g.prec == prec_code(o)) { exec = g.exec; kernels = g.kernels; break; }
     }
     if (!exec) {
         cudaStream_t cap;
@@ -705,7 +712,7 @@ sre_status batched_impl(const void *const *psi_ptrs, const int *Ns, int count, c
         cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) { cudaStreamDestroy(cap); return fail(SRE_ECUDA, "capture: %s", cudaGetErrorString(e)); }
         const unsigned long long l0 = g_launches.load();
-        sre_status s1 = batch_main(B, w, count, cap);
+        sre_status s1 = batch_main(B, w, count, prec_code(o), cap);
         e = cudaStreamEndCapture(cap, &graph);
         cudaStreamDestroy(cap);
         if (s1 != SRE_OK) { if (e == cudaSuccess) cudaGraphDestroy(graph); return s1; }
@@ -721,6 +728,7 @@ sre_status batched_impl(const void *const *psi_ptrs, const int *Ns, int count, c
         g.ws = base;
         g.exec = exec;
         g.kernels = kernels;
+        g.prec = prec_code(o);
         g_bgraph.push_back(g);
     }
     CK(cudaGraphLaunch(exec, st));
@@ -1011,6 +1019,7 @@ sre_status sre_mc(const void *psi, int N, int mode, long long n_x, int z_per_x, 
     count_launches(1);
 
     PassArgs a = base_args(P, psi, w.scal);
+    a.precision = prec_code(o);
     a.xs = w.xs;
     a.tile_out = w.tiles;
     a.want_ranges = marg ? 1 : 0;
@@ -1167,6 +1176,7 @@ sre_status sre_family_spectrum(const void *psi, int N, unsigned long long x, con
     CK(launch_norm2((const float2 *)psi, N, scal, part, st));
     count_launches(2);
     PassArgs a = base_args(P, psi, scal);
+    a.precision = prec_code(o);
     a.fam_base = (long long)x;
     a.n_fam = 1;
     a.spec_out = c_dev;
@@ -1311,6 +1321,7 @@ sre_status sre_profile_passes(const void *psi, int N, long long n_x, const sre_o
     CK(launch_draw_x(nullptr, N, n_x, 0, 12345ULL, 0ULL, w.xs, st));
     count_launches(1);
     PassArgs a = base_args(P, psi, w.scal);
+    a.precision = prec_code(o);
     a.xs = w.xs;
     a.tile_out = w.tiles;
     const long long step = P.B < n_x ? P.B : n_x;

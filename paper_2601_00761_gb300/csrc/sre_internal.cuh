@@ -220,6 +220,7 @@ struct PassArgs {
     // per-state device arrays. NULL for the one-state entry points.
     const float2 *const *psi_list;
     const double *s_list;
+    int precision;                     // 0: FP32 butterflies; 2, 3: split-BF16 tensor cores (FP32 tiles)
     int *err_flag;                     // device error word (bounds checks)
 };
 
