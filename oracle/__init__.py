@@ -84,6 +84,9 @@ def lib():
             L.or_apply_gates.argtypes = [_c_dp, ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong]
             L.or_apply_gates.restype = ctypes.c_int
             L.or_set_mutation.argtypes = [ctypes.c_int]
+            L.or_clifford_conjugate.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_uint64,
+                                                ctypes.c_uint64, _c_u64p, _c_u64p, ctypes.POINTER(ctypes.c_int)]
+            L.or_clifford_conjugate.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -269,6 +272,20 @@ def apply_gates(psi, gates, N: int | None = None) -> np.ndarray:
     if rc != 0:
         raise ValueError("bad gate row")
     return a
+
+
+def clifford_conjugate(N: int, gates, x: int, z: int):
+    """(x', z', sign) with C^dag P_{x,z} C = sign * P_{x',z'} for the Clifford
+    gate list C (applied in list order); raises on a T gate."""
+    g = np.ascontiguousarray(np.asarray(gates, dtype=np.uint8).reshape(-1, 3))
+    xo = ctypes.c_uint64(0)
+    zo = ctypes.c_uint64(0)
+    sg = ctypes.c_int(0)
+    rc = lib().or_clifford_conjugate(N, g.ctypes.data, g.shape[0], int(x), int(z), ctypes.byref(xo),
+                                     ctypes.byref(zo), ctypes.byref(sg))
+    if rc != 0:
+        raise ValueError("not a Clifford gate list")
+    return xo.value, zo.value, sg.value
 
 
 def circuit_state(N: int, gates) -> np.ndarray:

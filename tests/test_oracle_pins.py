@@ -265,6 +265,32 @@ def test_bad_gate_rejected():
         oracle.apply_gates(np.ones(4, np.complex64), np.array([[9, 0, 0]]))
 
 
+@pytest.mark.parametrize("N,seed", [(2, 1), (3, 2), (4, 3)])
+def test_clifford_conjugation_matches_bruteforce(N, seed):
+    """c_P(C psi) = sign * c_{P'}(psi) with C^dag P C = sign P' (Clifford
+    invariance, main text); every gate type including S^dag."""
+    g = np.random.default_rng(seed)
+    rows = []
+    for _ in range(30):
+        op = int(g.choice([inputs.GATE_H, inputs.GATE_S, inputs.GATE_SDG, inputs.GATE_CNOT])) if N > 1 \
+            else int(g.choice([inputs.GATE_H, inputs.GATE_S, inputs.GATE_SDG]))
+        q0 = int(g.integers(0, N))
+        q1 = int((q0 + 1 + g.integers(0, N - 1)) % N) if op == inputs.GATE_CNOT else 0
+        rows.append((op, q0, q1))
+    C = np.array(rows, dtype=np.uint8)
+    psi = inputs.haar_state(N, seed)
+    Cpsi = oracle.apply_gates(psi, C).astype(np.complex64)
+    for x in range(1 << N):
+        for z in range(1 << N):
+            x2, z2, sg = oracle.clifford_conjugate(N, C, x, z)
+            assert abs(oracle.pauli_expectation(Cpsi, x, z) - sg * oracle.pauli_expectation(psi, x2, z2)) < 1e-5
+
+
+def test_clifford_conjugation_rejects_t():
+    with pytest.raises(ValueError):
+        oracle.clifford_conjugate(2, np.array([[inputs.GATE_T, 0, 0]], dtype=np.uint8), 1, 0)
+
+
 # -------------------------------------------------------------- marginal
 @pytest.mark.parametrize("N", [1, 3, 6, 9])
 def test_marginal_routes(N):
