@@ -50,9 +50,15 @@ __device__ __forceinline__ double group_sum(double v, double *red) {
 }
 
 // NV sums and one maximum over the T threads of a group: FP32 butterfly
-// inside the warp, FP64 across the group's warps (fixed order). Results are
-// valid in the group's thread 0. red: NV * NT/32 doubles + NT/32 floats of
-// shared scratch. Two barriers when a group spans several warps.
+// inside the warp, FP64 butterfly across the group's warps. Results are valid
+// in the group's thread 0. red: (NV + 1) * NT/32 floats of shared scratch.
+// Two barriers when a group spans several warps.
+//
+// The cross-warp step runs in the group's first warp with one lane per
+// (value, warp) pair, so the whole tile costs a handful of FP64 warp
+// instructions: the FP64 pipe issues one warp instruction per 16 cycles on
+// this part, and a serial per-value loop in one thread would sit on the
+// critical path of every tile.
 template <int T, int NT, int NV>
 __device__ __forceinline__ void group_reduce(float (&v)[NV], float &mx, double (&out)[NV], float &omx,
                                              double *red) {
@@ -68,28 +74,40 @@ __device__ __forceinline__ void group_reduce(float (&v)[NV], float &mx, double (
         for (int i = 0; i < NV; ++i) out[i] = (double)v[i];
         omx = mx;
     } else {
-        constexpr int NW = NT / 32;
-        float *redm = reinterpret_cast<float *>(red + NV * NW);
-        const int w = threadIdx.x >> 5;
+        constexpr int NW = NT / 32;          // warps in the CTA
+        constexpr int WPG = T / 32;          // warps per group (power of two, <= 32)
+        constexpr int VPP = 32 / WPG;        // values reduced per round by one warp
+        constexpr int NVM = NV + 1;          // the sums and the maximum
+        constexpr int ROUNDS = (NVM + VPP - 1) / VPP;
+        float *rf = reinterpret_cast<float *>(red);
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
         __syncthreads();
-        if ((threadIdx.x & 31) == 0) {
+        if (lane == 0) {
 #pragma unroll
-            for (int i = 0; i < NV; ++i) red[i * NW + w] = (double)v[i];
-            redm[w] = mx;
+            for (int i = 0; i < NV; ++i) rf[i * NW + w] = v[i];
+            rf[NV * NW + w] = mx;
         }
         __syncthreads();
-        if ((threadIdx.x & (T - 1)) == 0) {
+        if ((w & (WPG - 1)) == 0) {
+            const int q = lane & (WPG - 1), vi = lane / WPG;
 #pragma unroll
-            for (int i = 0; i < NV; ++i) {
-                double s = 0.0;
-#pragma unroll 1
-                for (int q = 0; q < T / 32; ++q) s += red[i * NW + w + q];
-                out[i] = s;
+            for (int r = 0; r < ROUNDS; ++r) {
+                const int vv = r * VPP + vi;
+                const float f = vv < NVM ? rf[vv * NW + w + q] : 0.f;
+                double sd = (double)f;
+                float sm = f;
+#pragma unroll
+                for (int o = WPG / 2; o > 0; o >>= 1) {
+                    sd += __shfl_xor_sync(0xffffffffu, sd, o);
+                    sm = fmaxf(sm, __shfl_xor_sync(0xffffffffu, sm, o));
+                }
+#pragma unroll
+                for (int u = 0; u < VPP; ++u) {
+                    const int idx = r * VPP + u;
+                    if (idx < NV) out[idx] = __shfl_sync(0xffffffffu, sd, u * WPG);
+                    else if (idx == NV) omx = __shfl_sync(0xffffffffu, sm, u * WPG);
+                }
             }
-            float m = 0.f;
-#pragma unroll 1
-            for (int q = 0; q < T / 32; ++q) m = fmaxf(m, redm[w + q]);
-            omx = m;
         }
     }
 }
@@ -256,6 +274,15 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const Pas
     C2 v[Cfg::E];
     constexpr int AL = Maps<Cfg>::last;
 
+    // The moments epilogue wants s in FP32 in every thread; one conversion per
+    // group, passed through shared memory (the transform's barriers order it).
+    constexpr bool S_SHARED = DST == DST_MOMENTS && Cfg::T >= 32;
+    float *s_sh = reinterpret_cast<float *>(red) + 8 * (Cfg::NT / 32);
+    if constexpr (S_SHARED) {
+        if (t == 0) s_sh[grp] = (float)(*s_ptr);
+        if constexpr (Cfg::NR <= 1 && PREC == 0) __syncthreads();
+    }
+
     // ---------------------------------------------------------- prologue
     pass_prologue<Cfg, SRC>(v, a, psi, slot, x, j, half, gbase, t);
 
@@ -326,7 +353,9 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const Pas
         // z' = zb | k for slot k (last mapping: slot bits are the low RB bits).
         // q = (c(z0)^2, c(z1)^2) up to the order fixed by the parity, kept as
         // a packed pair: moments only need the unordered pair.
-        const float s = (float)(*s_ptr);
+        float s;
+        if constexpr (S_SHARED) s = s_sh[grp];
+        else s = (float)(*s_ptr);
         const int RL = a.range_log2;
         const uint32_t zb = (uint32_t)gbase | Cfg::elem(t, 0, 0);
         float2 s2 = make_float2(0.f, 0.f), s4 = s2, s6 = s2, sl = s2, w = s2;

@@ -41,6 +41,22 @@ __global__ void __launch_bounds__(Cfg::NT) zsample_kernel(const PassArgs a, cons
     const unsigned long long tile = zp0 >> Cfg::M;
     const unsigned long long gbase = tile << Cfg::M;
 
+    // The per-draw FP64 scalars (fixed-point scale, target in quanta, s) are
+    // formed once by thread 0 and passed through shared memory: the FP64
+    // pipe is narrow on this part and a divide in every thread would
+    // dominate the kernel. The barrier after the transform orders the write.
+    constexpr int NW = (Cfg::NT + 31) / 32;
+    unsigned long long *bc = reinterpret_cast<unsigned long long *>(seg) + NW + 1;
+    if (t == 0) {
+        const double scale = dr.wr > 0.0 ? 0x1.0p31 / dr.wr : 0.0;
+        double tq = dr.t * scale;
+        if (tq < 0.0) tq = 0.0;
+        bc[0] = tq < 1.8e19 ? (unsigned long long)tq : ~0ULL;
+        float *bf = reinterpret_cast<float *>(bc + 1);
+        bf[0] = (float)scale;
+        bf[1] = (float)(*a.s_ptr);
+    }
+
     C2 v[Cfg::E];
     pass_prologue<Cfg, SRC>(v, a, a.psi, slot, x, j, half, gbase, t);
     if constexpr (PREC == 0) tile_transform<Cfg>(v, sm, t, 0);
@@ -55,9 +71,9 @@ __global__ void __launch_bounds__(Cfg::NT) zsample_kernel(const PassArgs a, cons
     uint32_t *wq = reinterpret_cast<uint32_t *>(smraw);
     float *cv = reinterpret_cast<float *>(wq + (1 << RL) + ((1 << RL) >> 5));
     auto pp = [](uint32_t p) { return p + (p >> 5); };
-    const double scale = dr.wr > 0.0 ? 0x1.0p31 / dr.wr : 0.0;
-    const float scf = (float)scale;
-    const R s = (R)(*a.s_ptr);
+    const float scf = reinterpret_cast<const float *>(bc + 1)[0];
+    const R s = reinterpret_cast<const float *>(bc + 1)[1];
+    const unsigned long long T = bc[0];
     constexpr int AL = Maps<Cfg>::last;
 #pragma unroll
     for (int k = 0; k < Cfg::E; ++k) {
@@ -82,7 +98,6 @@ __global__ void __launch_bounds__(Cfg::NT) zsample_kernel(const PassArgs a, cons
     unsigned long long own = 0;
     for (int i = 0; i < PER; ++i) own += wq[pp(lo + i)];
     // warps of the CTA (the smallest tiles have fewer than 32 threads)
-    constexpr int NW = (Cfg::NT + 31) / 32;
     constexpr int WL = Cfg::NT < 32 ? Cfg::NT : 32;
     constexpr unsigned MASK = Cfg::NT < 32 ? ((1u << Cfg::NT) - 1u) : 0xffffffffu;
     unsigned long long incl = own;
@@ -103,9 +118,6 @@ __global__ void __launch_bounds__(Cfg::NT) zsample_kernel(const PassArgs a, cons
     __syncthreads();
     const unsigned long long before = wsum[wid] + incl - own;
     const unsigned long long total = wsum[NW];
-    double tq = dr.t * scale;
-    if (tq < 0.0) tq = 0.0;
-    const unsigned long long T = tq < 1.8e19 ? (unsigned long long)tq : ~0ULL;
     const size_t out = (size_t)gf * z_per_x + kdraw;
     if (T < total && before <= T && T < before + own) {
         unsigned long long run = before;
