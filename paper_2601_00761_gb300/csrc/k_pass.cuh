@@ -219,6 +219,40 @@ __device__ __forceinline__ void family_pair(unsigned long long x, int j, R s, C2
     }
 }
 
+// log2 on the MUFU unit, subnormal inputs flushed (callers keep x >= FLT_MIN)
+__device__ __forceinline__ float lg2_ftz(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Fused moment sums of Algorithm 1 over one thread's E transformed elements:
+// c = sc * h (a pair of Pauli expectations), q = c^2, and packed running
+// sums of q, q^2, q^3 and q log2 q. FLT_MIN is added inside the log only:
+// it leaves every q >= 2^-102 unchanged and makes q = 0 contribute 0.
+// SWAP orders each pair so that c(z0) comes first (bit k of pm set: swap);
+// CAND keeps the running maximum of q for the nullity candidates.
+template <int E, bool SWAP, bool CAND>
+__device__ __forceinline__ void moment_sums(const float2 (&h)[E], float2 sc, uint32_t pm, float2 &s2, float2 &s4,
+                                            float2 &s6, float2 &sl, float &qmax) {
+    const float2 tiny = make_float2(1.17549435e-38f, 1.17549435e-38f);
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        float2 c = mul2(sc, h[k]);
+        if constexpr (SWAP) {
+            if ((pm >> k) & 1u) c = make_float2(c.y, c.x);
+        }
+        const float2 q = mul2(c, c);
+        const float2 q2 = mul2(q, q);
+        s2 = add2(s2, q);
+        s4 = add2(s4, q2);
+        s6 = fma2(q2, q, s6);
+        const float2 qt = add2(q, tiny);
+        sl = fma2(q, make_float2(lg2_ftz(qt.x), lg2_ftz(qt.y)), sl);
+        if constexpr (CAND) qmax = fmaxf(qmax, fmaxf(q.x, q.y));
+    }
+}
+
 template <class Cfg, int SRC, int DST, int PREC = 0>
 __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const PassArgs a) {
     typedef typename Cfg::Real R;
@@ -237,6 +271,10 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const Pas
     if constexpr (Cfg::G > 1) {
         slot = (long long)blockIdx.x * Cfg::G + grp;
         tile = 0;
+    } else if (a.fam_fast) {
+        const unsigned long long L = blockIdx.x;
+        slot = (long long)(L % (unsigned long long)a.n_fam);
+        tile = L / (unsigned long long)a.n_fam;
     } else {
         slot = (long long)blockIdx.y + 65535LL * (long long)blockIdx.z;
         tile = blockIdx.x;
@@ -352,59 +390,57 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const Pas
         static_assert(Cfg::LO == 0 && AL == 0, "moments epilogue runs on last-pass tiles");
         // z' = zb | k for slot k (last mapping: slot bits are the low RB bits).
         // q = (c(z0)^2, c(z1)^2) up to the order fixed by the parity, kept as
-        // a packed pair: moments only need the unordered pair.
+        // a packed pair: moments only need the unordered pair. The z-range
+        // weights are read off the packed sum of q: a tile spans two ranges
+        // of 2^M consecutive z (range A, then range B).
         float s;
         if constexpr (S_SHARED) s = s_sh[grp];
         else s = (float)(*s_ptr);
-        const int RL = a.range_log2;
         const uint32_t zb = (uint32_t)gbase | Cfg::elem(t, 0, 0);
         float2 s2 = make_float2(0.f, 0.f), s4 = s2, s6 = s2, sl = s2, w = s2;
         float qmax = 0.f;
-        const float tiny = 1.17549435e-38f;
-        const bool wr = a.want_ranges;
+        const bool wr = a.want_ranges, cand = a.want_cand;
         if (x) {
             const float2 sc = make_float2(2.0f * s, 2.0f * s);
-            const uint32_t xd = (uint32_t)((x & ((1ULL << j) - 1ULL)) | ((x >> (j + 1)) << j));
-            // bit k: parity of |x & z0| for z' = zb | k (z0 carries Im when odd)
-            const uint32_t pm = walsh_mask5(xd & (Cfg::E - 1)) ^ ((__popc(xd & zb) & 1) ? 0xFFFFFFFFu : 0u);
-            const bool jge = j >= RL;
-#pragma unroll
-            for (int k = 0; k < Cfg::E; ++k) {
-                const float2 c = mul2(sc, v[k]);
-                const float2 q = mul2(c, c);
-                const float2 q2 = mul2(q, q);
-                s2 = add2(s2, q);
-                s4 = add2(s4, q2);
-                s6 = fma2(q2, q, s6);
-                const float2 lg = make_float2(__log2f(fmaxf(q.x, tiny)), __log2f(fmaxf(q.y, tiny)));
-                sl = fma2(q, lg, sl);
-                qmax = fmaxf(qmax, fmaxf(q.x, q.y));
+            if (wr && j >= Cfg::M) {
+                // range A holds every c(z0), range B every c(z1): order each
+                // pair as (c(z0)^2, c(z1)^2) and s2 is the pair of weights.
+                // Bit k of pm: parity of |x & z0| for z' = zb | k (z0 then
+                // carries the Im part).
+                const uint32_t xd = (uint32_t)((x & ((1ULL << j) - 1ULL)) | ((x >> (j + 1)) << j));
+                const uint32_t pm = walsh_mask5(xd & (Cfg::E - 1)) ^ ((__popc(xd & zb) & 1) ? 0xFFFFFFFFu : 0u);
+                if (cand) moment_sums<Cfg::E, true, true>(v, sc, pm, s2, s4, s6, sl, qmax);
+                else moment_sums<Cfg::E, true, false>(v, sc, pm, s2, s4, s6, sl, qmax);
+                w = s2;
+            } else {
+                if (cand) moment_sums<Cfg::E, false, true>(v, sc, 0u, s2, s4, s6, sl, qmax);
+                else moment_sums<Cfg::E, false, false>(v, sc, 0u, s2, s4, s6, sl, qmax);
                 if (wr) {
-                    if (jge) {   // (range A, range B) = (z0, z1)
-                        const bool odd = (pm >> k) & 1u;
-                        w = add2(w, make_float2(odd ? q.y : q.x, odd ? q.x : q.y));
-                    } else {     // both into the range picked by bit RL-1 of z'
-                        const bool hi = ((zb | (uint32_t)k) >> (RL - 1)) & 1u;
-                        const float qq = q.x + q.y;
-                        w = add2(w, make_float2(hi ? 0.f : qq, hi ? qq : 0.f));
+                    // both c of a pair lie in the range picked by bit M-1 of z'
+                    constexpr int RBIT = Cfg::M > 0 ? Cfg::M - 1 : 0;
+                    if constexpr (RBIT >= Cfg::RB) {
+                        const float all = s2.x + s2.y;
+                        w = ((zb >> RBIT) & 1u) ? make_float2(0.f, all) : make_float2(all, 0.f);
+                    } else {
+                        // tiles of at most 2 RB bits: the range bit is a slot bit
+#pragma unroll
+                        for (int k = 0; k < Cfg::E; ++k) {
+                            const float2 c = mul2(sc, v[k]);
+                            const float qq = c.x * c.x + c.y * c.y;
+                            if ((k >> RBIT) & 1) w.y += qq;
+                            else w.x += qq;
+                        }
                     }
                 }
             }
         } else {
             const float2 sc = make_float2(s, s);
+            typename Cfg::C2 hs[Cfg::E];
 #pragma unroll
-            for (int k = 0; k < Cfg::E; ++k) {
-                const float2 c = mul2(sc, make_float2(v[k].x + v[k].y, v[k].x - v[k].y));
-                const float2 q = mul2(c, c);
-                const float2 q2 = mul2(q, q);
-                s2 = add2(s2, q);
-                s4 = add2(s4, q2);
-                s6 = fma2(q2, q, s6);
-                const float2 lg = make_float2(__log2f(fmaxf(q.x, tiny)), __log2f(fmaxf(q.y, tiny)));
-                sl = fma2(q, lg, sl);
-                qmax = fmaxf(qmax, fmaxf(q.x, q.y));
-                w = add2(w, q);        // z' -> range A, z' + d/2 -> range B
-            }
+            for (int k = 0; k < Cfg::E; ++k) hs[k] = make_float2(v[k].x + v[k].y, v[k].x - v[k].y);
+            if (cand) moment_sums<Cfg::E, false, true>(hs, sc, 0u, s2, s4, s6, sl, qmax);
+            else moment_sums<Cfg::E, false, false>(hs, sc, 0u, s2, s4, s6, sl, qmax);
+            w = s2;                    // z' -> range A, z' + d/2 -> range B
         }
         float acc[6] = {s2.x + s2.y, s4.x + s4.y, s6.x + s6.y, sl.x + sl.y, w.x, w.y};
         double out[6];
@@ -415,7 +451,7 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const Pas
             TilePartial &tp = a.tile_out[(size_t)slot * (size_t)tiles + tile];
             tp.m[0] = out[0]; tp.m[1] = out[1]; tp.m[2] = out[2]; tp.m[3] = out[3];
             tp.w[0] = out[4]; tp.w[1] = out[5];
-            tp.cand = omx > a.cand_thr * a.cand_thr ? 1u : 0u;
+            tp.cand = (cand && omx > a.cand_thr * a.cand_thr) ? 1u : 0u;
         }
     }
 }
@@ -432,13 +468,22 @@ cudaError_t launch_cfg(const PassArgs &a, int tiles, cudaStream_t st) {
         attr_done = true;
     }
     dim3 grid;
+    PassArgs b = a;
+    b.fam_fast = 0;
     if constexpr (Cfg::G > 1) {
         grid = dim3((unsigned)((a.n_fam + Cfg::G - 1) / Cfg::G), 1, 1);
     } else {
         const long long nf = a.n_fam;
-        grid = dim3((unsigned)tiles, (unsigned)(nf < 65535 ? nf : 65535), (unsigned)((nf + 65534) / 65535));
+        const long long total = nf * (long long)tiles;
+        if ((SRC == SRC_PSI_FAMILY || SRC == SRC_PSI_Q) && nf > 1 && tiles > 1 &&
+            total < 0x7fffffffLL) {
+            b.fam_fast = 1;
+            grid = dim3((unsigned)total, 1, 1);
+        } else {
+            grid = dim3((unsigned)tiles, (unsigned)(nf < 65535 ? nf : 65535), (unsigned)((nf + 65534) / 65535));
+        }
     }
-    fwht_pass_kernel<Cfg, SRC, DST, PREC><<<grid, Cfg::NT, smem, st>>>(a);
+    fwht_pass_kernel<Cfg, SRC, DST, PREC><<<grid, Cfg::NT, smem, st>>>(b);
     return cudaGetLastError();
 }
 

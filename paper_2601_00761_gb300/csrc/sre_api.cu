@@ -44,7 +44,7 @@ sre_status fail(sre_status st, const char *fmt, ...) {
         if (s_ != SRE_OK) return s_;      \
     } while (0)
 
-constexpr size_t BATCH_BYTES = 2ULL << 30;   // intermediate budget per launch sequence
+constexpr size_t BATCH_BYTES = 8ULL << 30;   // intermediate budget per launch sequence
 
 // kernels issued by this library since load (all entry points)
 std::atomic<unsigned long long> g_launches{0};
@@ -322,6 +322,7 @@ PassArgs base_args(const Plan &P, const void *psi, const double *scal) {
     a.range_log2 = P.M_last;
     a.s_ptr = scal + SCAL_S;
     a.cand_thr = 1.0f - 1e-4f;
+    a.want_cand = 1;
     a.precision = 0;
     return a;
 }
@@ -1023,6 +1024,7 @@ sre_status sre_mc(const void *psi, int N, int mode, long long n_x, int z_per_x, 
     a.xs = w.xs;
     a.tile_out = w.tiles;
     a.want_ranges = marg ? 1 : 0;
+    a.want_cand = 0;                 // the estimators need no nullity candidates
     const long long step = P.B < n_x ? P.B : n_x;
     const long long nr = 1LL << (N - P.M_last);
     bool timing;

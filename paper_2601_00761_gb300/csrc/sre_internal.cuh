@@ -215,6 +215,7 @@ struct PassArgs {
     double eps;                        // nullity tolerance
     float cand_thr;                    // FP32 candidate threshold
     int want_ranges;                   // DST_MOMENTS: also produce the z-range weights
+    int want_cand;                     // DST_MOMENTS: also flag nullity candidates (exact sweeps)
     // Several states of the same N in one launch: the family index F (from xs
     // or fam_base + slot) is (state << N) | x; psi and s come from these
     // per-state device arrays. NULL for the one-state entry points.
@@ -222,6 +223,10 @@ struct PassArgs {
     const double *s_list;
     int precision;                     // 0: FP32 butterflies; 2, 3: split-BF16 tensor cores (FP32 tiles)
     int *err_flag;                     // device error word (bounds checks)
+    // CTA order: 0 = tile-major (blockIdx.x = tile, y/z = family); 1 = one
+    // linear grid with the family fastest, so that the families in flight
+    // work on the same tile at once and share its psi lines in L2.
+    int fam_fast;
 };
 
 // host launchers (k_passes*.cu)
