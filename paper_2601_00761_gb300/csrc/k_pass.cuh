@@ -123,10 +123,20 @@ __device__ __forceinline__ uint32_t walsh_mask5(uint32_t a) {
     return m;
 }
 
-// Packed global index of tile element e (see PassArgs::lo_g and TileCfg).
+// 32-bit packed global indices of a thread's slots (N <= 31, so every packed
+// index and every psi index is below 2^31). The thread's slot-0 index is
+// base; slot k of the mapping whose slot bits start at tile bit A adds the
+// column part of k << A and its row part times 2^lo_g (all bit fields
+// disjoint, so the OR of the fields is their sum).
 template <class Cfg>
-__device__ __forceinline__ unsigned long long tile_gidx(unsigned long long gbase, int lo_g, uint32_t e) {
-    return gbase | ((unsigned long long)(e >> Cfg::LO) << lo_g) | (e & ((1u << Cfg::LO) - 1u));
+__device__ __forceinline__ uint32_t thread_gidx(unsigned long long gbase, int lo_g, uint32_t e) {
+    return (uint32_t)gbase | ((e >> Cfg::LO) << lo_g) | (e & ((1u << Cfg::LO) - 1u));
+}
+template <class Cfg, int A>
+__device__ __forceinline__ uint32_t slot_gidx(uint32_t base, uint32_t rs, int k) {
+    constexpr uint32_t CM = (1u << Cfg::LO) - 1u;
+    const uint32_t e = (uint32_t)k << A;
+    return base + (e & CM) + (e >> Cfg::LO) * rs;
 }
 
 // Load the tile in the first round's mapping (prologue of every pass).
@@ -137,20 +147,24 @@ __device__ __forceinline__ void pass_prologue(typename Cfg::C2 (&v)[Cfg::E], con
     typedef typename Cfg::Real R;
     typedef typename Cfg::C2 C2;
     constexpr int A0 = Maps<Cfg>::first;
+    const uint32_t base = thread_gidx<Cfg>(gbase, a.lo_g, Cfg::elem(t, 0, A0));
+    const uint32_t rs = 1u << a.lo_g;
     if constexpr (SRC == SRC_PSI_FAMILY) {
         // loads issued in batches of LB slots (2 LB independent 8-byte loads in
         // flight per thread) before any of them is used
         constexpr int LB = Cfg::E < 8 ? Cfg::E : 8;
         if (x != 0) {
+            // b = g with 0 inserted at bit j = g + (g & ~(2^j - 1)); partner b ^ x
+            const uint32_t hm = ~((1u << j) - 1u), x32 = (uint32_t)x;
 #pragma unroll
             for (int k0 = 0; k0 < Cfg::E; k0 += LB) {
                 float2 u[LB], w[LB];
 #pragma unroll
                 for (int q = 0; q < LB; ++q) {
-                    const unsigned long long g = tile_gidx<Cfg>(gbase, a.lo_g, Cfg::elem(t, k0 + q, A0));
-                    const unsigned long long b = insert0(g, j);
+                    const uint32_t g = slot_gidx<Cfg, A0>(base, rs, k0 + q);
+                    const uint32_t b = g + (g & hm);
                     u[q] = __ldg(psi + b);
-                    w[q] = __ldg(psi + (b ^ x));
+                    w[q] = __ldg(psi + (b ^ x32));
                 }
 #pragma unroll
                 for (int q = 0; q < LB; ++q) {
@@ -160,14 +174,15 @@ __device__ __forceinline__ void pass_prologue(typename Cfg::C2 (&v)[Cfg::E], con
                 }
             }
         } else {
+            const uint32_t h32 = (uint32_t)half;
 #pragma unroll
             for (int k0 = 0; k0 < Cfg::E; k0 += LB) {
                 float2 u[LB], w[LB];
 #pragma unroll
                 for (int q = 0; q < LB; ++q) {
-                    const unsigned long long g = tile_gidx<Cfg>(gbase, a.lo_g, Cfg::elem(t, k0 + q, A0));
+                    const uint32_t g = slot_gidx<Cfg, A0>(base, rs, k0 + q);
                     u[q] = __ldg(psi + g);
-                    w[q] = __ldg(psi + (g | half));
+                    w[q] = __ldg(psi + (g | h32));
                 }
 #pragma unroll
                 for (int q = 0; q < LB; ++q) {
@@ -178,11 +193,12 @@ __device__ __forceinline__ void pass_prologue(typename Cfg::C2 (&v)[Cfg::E], con
             }
         }
     } else if constexpr (SRC == SRC_PSI_Q) {
+        const uint32_t h32 = (uint32_t)half;
 #pragma unroll
         for (int k = 0; k < Cfg::E; ++k) {
-            const unsigned long long g = tile_gidx<Cfg>(gbase, a.lo_g, Cfg::elem(t, k, A0));
+            const uint32_t g = slot_gidx<Cfg, A0>(base, rs, k);
             const float2 u = __ldg(psi + g);
-            const float2 w = __ldg(psi + (g | half));
+            const float2 w = __ldg(psi + (g | h32));
             const R ux = u.x, uy = u.y, wx = w.x, wy = w.y;
             v[k].x = fma(ux, ux, uy * uy);
             v[k].y = fma(wx, wx, wy * wy);
@@ -196,7 +212,7 @@ __device__ __forceinline__ void pass_prologue(typename Cfg::C2 (&v)[Cfg::E], con
     } else {
         const C2 *src = reinterpret_cast<const C2 *>(a.src) + (size_t)slot * (size_t)a.slot_elems;
 #pragma unroll
-        for (int k = 0; k < Cfg::E; ++k) v[k] = src[tile_gidx<Cfg>(gbase, a.lo_g, Cfg::elem(t, k, A0))];
+        for (int k = 0; k < Cfg::E; ++k) v[k] = src[slot_gidx<Cfg, A0>(base, rs, k)];
     }
 }
 
@@ -332,8 +348,10 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const Pas
     if constexpr (DST == DST_BUF) {
         if (active) {
             C2 *dst = reinterpret_cast<C2 *>(a.dst) + (size_t)slot * (size_t)a.slot_elems;
+            const uint32_t base = thread_gidx<Cfg>(gbase, a.lo_g, Cfg::elem(t, 0, AL));
+            const uint32_t rs = 1u << a.lo_g;
 #pragma unroll
-            for (int k = 0; k < Cfg::E; ++k) dst[gidx(Cfg::elem(t, k, AL))] = v[k];
+            for (int k = 0; k < Cfg::E; ++k) dst[slot_gidx<Cfg, AL>(base, rs, k)] = v[k];
         }
     } else if constexpr (DST == DST_SQMAP) {
         if (active) {

@@ -95,10 +95,11 @@ cudaError_t launch_f64_single(int M, int src, int dst, const PassArgs &a, cudaSt
 cudaError_t launch_f64_strided(int K, int src, int dst, const PassArgs &a, int tiles, cudaStream_t st);
 cudaError_t launch_f64_row(int M, int src, int dst, const PassArgs &a, int tiles, cudaStream_t st);
 
-// strided tile: 2^K rows x 2^(MS-K) columns; FP32 MS = 13 (K <= 9, 64 KB) or
-// 14 (K = 10, 128 KB); FP64 MS = 13 (128 KB)
+// strided tile: 2^K rows x 2^(MS-K) columns; FP32 MS = 13 for every K (64 KB,
+// at least 8 columns = 64 contiguous bytes per row, two CTAs per SM so one
+// CTA's loads overlap the other's butterflies); FP64 MS = 13 (128 KB)
 constexpr int F32_STRIDED_KMAX = 10, F32_ROW_MMIN = 10, F32_ROW_MMAX = 14, F32_SINGLE_MMAX = 14;
-__host__ __device__ constexpr int f32_strided_ms(int K) { return K + 4 > 13 ? K + 4 : 13; }
+__host__ __device__ constexpr int f32_strided_ms(int K) { return K + 3 > 13 ? K + 3 : 13; }
 constexpr int F64_STRIDED_M = 13, F64_STRIDED_KMAX = 9, F64_ROW_M = 12, F64_SINGLE_MMAX = 12;
 
 } // namespace sre
