@@ -91,7 +91,7 @@ cudaError_t launch_norm2(const float2 *psi, int N, double *scal, double *partial
 __global__ void __launch_bounds__(256) fam_reduce_kernel(const TilePartial *tp, long long n_fam, int tiles,
                                                          const unsigned long long *xs, long long fam_base,
                                                          int N, int M_last, int RL, FamMoments *fm,
-                                                         long long fm_base, double *W, long long nr) {
+                                                         long long fm_base, float *W, long long nr) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long f = (long long)blockIdx.x * 8 + warp;
     if (f >= n_fam) return;
@@ -107,8 +107,8 @@ __global__ void __launch_bounds__(256) fam_reduce_kernel(const TilePartial *tp, 
             const unsigned long long zt = (unsigned long long)t << M_last;
             const unsigned long long rA = insert0(zt, j) >> RL;
             const unsigned long long rB = (j < RL) ? rA + 1 : rA + (1ULL << (j - RL));
-            W[(size_t)f * nr + rA] = p.w[0];
-            W[(size_t)f * nr + rB] = p.w[1];
+            W[(size_t)f * nr + rA] = (float)p.w[0];
+            W[(size_t)f * nr + rB] = (float)p.w[1];
         }
     }
 #pragma unroll
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(256) fam_reduce_kernel(const TilePartial *tp, 
 
 cudaError_t launch_fam_reduce(const TilePartial *tp, long long n_fam, int tiles, const unsigned long long *xs,
                               long long fam_base, int N, int M_last, int RL, FamMoments *fm, long long fm_base,
-                              double *W, long long nr, cudaStream_t st) {
+                              float *W, long long nr, cudaStream_t st) {
     fam_reduce_kernel<<<(unsigned)((n_fam + 7) / 8), 256, 0, st>>>(tp, n_fam, tiles, xs, fam_base, N, M_last, RL,
                                                                   fm, fm_base, W, nr);
     return cudaGetLastError();
@@ -319,20 +319,22 @@ cudaError_t launch_draw_x(const double *cdf, int N, long long n_x, int mode, uns
     return cudaGetLastError();
 }
 
-// z-range selection: W[f][.] -> inclusive FP64 scan in place (fixed order),
-// then each draw k picks range r and the remainder t' within it.
-__global__ void __launch_bounds__(256) zrange_select_kernel(double *W, long long nr, long long n_fam,
-                                                            long long fam_base, int z_per_x,
+// z-range selection: the FP32 range weights Wf[f][.] -> their inclusive FP64
+// scan W[f][.] (fixed order), then each draw k picks range r and the
+// remainder t' within it.
+__global__ void __launch_bounds__(256) zrange_select_kernel(const float *Wf, double *W, long long nr,
+                                                            long long n_fam, long long fam_base, int z_per_x,
                                                             unsigned long long seed, unsigned long long ctr0,
                                                             DrawInfo *draws) {
     __shared__ double seg[257];
     const long long f = blockIdx.x;
     if (f >= n_fam) return;
+    const float *wf = Wf + (size_t)f * nr;
     double *w = W + (size_t)f * nr;
     const long long per = (nr + 255) / 256;
     const long long lo = threadIdx.x * per, hi = lo + per < nr ? lo + per : nr;
     double s = 0.0;
-    for (long long i = lo; i < hi; ++i) s += w[i];
+    for (long long i = lo; i < hi; ++i) s += (double)wf[i];
     seg[threadIdx.x + 1] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -342,7 +344,7 @@ __global__ void __launch_bounds__(256) zrange_select_kernel(double *W, long long
     __syncthreads();
     double run = seg[threadIdx.x];
     for (long long i = lo; i < hi; ++i) {
-        run += w[i];
+        run += (double)wf[i];
         w[i] = run;
     }
     __syncthreads();
@@ -361,10 +363,10 @@ __global__ void __launch_bounds__(256) zrange_select_kernel(double *W, long long
     }
 }
 
-cudaError_t launch_zrange_select(double *W, long long nr, long long n_fam, long long fam_base, int z_per_x,
-                                 unsigned long long seed, unsigned long long ctr0, DrawInfo *draws,
+cudaError_t launch_zrange_select(const float *Wf, double *W, long long nr, long long n_fam, long long fam_base,
+                                 int z_per_x, unsigned long long seed, unsigned long long ctr0, DrawInfo *draws,
                                  cudaStream_t st) {
-    zrange_select_kernel<<<(unsigned)n_fam, 256, 0, st>>>(W, nr, n_fam, fam_base, z_per_x, seed, ctr0, draws);
+    zrange_select_kernel<<<(unsigned)n_fam, 256, 0, st>>>(Wf, W, nr, n_fam, fam_base, z_per_x, seed, ctr0, draws);
     return cudaGetLastError();
 }
 

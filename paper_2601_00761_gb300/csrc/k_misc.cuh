@@ -19,7 +19,7 @@ struct DrawInfo {
 cudaError_t launch_norm2(const float2 *psi, int N, double *scal, double *partial, cudaStream_t st);
 cudaError_t launch_fam_reduce(const TilePartial *tp, long long n_fam, int tiles, const unsigned long long *xs,
                               long long fam_base, int N, int M_last, int RL, FamMoments *fm, long long fm_base,
-                              double *W, long long nr, cudaStream_t st);
+                              float *W, long long nr, cudaStream_t st);
 cudaError_t launch_exact_totals(const FamMoments *fm, long long n_fam, double *partial, int n_part,
                                 double *out, unsigned long long *flag_list, unsigned long long *n_flag,
                                 cudaStream_t st);
@@ -27,8 +27,8 @@ cudaError_t launch_sum_u64(const unsigned long long *v, long long n, unsigned lo
 cudaError_t launch_scan(const double *p, unsigned long long n, double *cdf, double *bsum, cudaStream_t st);
 cudaError_t launch_draw_x(const double *cdf, int N, long long n_x, int mode, unsigned long long seed,
                           unsigned long long ctr0, unsigned long long *xs, cudaStream_t st);
-cudaError_t launch_zrange_select(double *W, long long nr, long long n_fam, long long fam_base, int z_per_x,
-                                 unsigned long long seed, unsigned long long ctr0, DrawInfo *draws,
+cudaError_t launch_zrange_select(const float *Wf, double *W, long long nr, long long n_fam, long long fam_base,
+                                 int z_per_x, unsigned long long seed, unsigned long long ctr0, DrawInfo *draws,
                                  cudaStream_t st);
 cudaError_t launch_mc_stats(const FamMoments *fm, const float *cz, long long n_x, int z_per_x, int N, int mode,
                             double *y, double *out, cudaStream_t st);
@@ -41,9 +41,10 @@ cudaError_t launch_count_scatter(const unsigned long long *flags, const unsigned
                                  int N, unsigned long long *state_count, cudaStream_t st);
 cudaError_t launch_philox_test(const unsigned long long *ctr_key, unsigned long long *out, int n, cudaStream_t st);
 
-// z sampler (k_sample.cu): recompute the last-pass tile of each draw's range
-// and pick z by the FP64 inclusive scan of c^2 over the range.
-cudaError_t launch_zsample(int single, int M, const PassArgs &a, const DrawInfo *draws, int z_per_x,
+// z sampler (k_sample.cu): recompute the c of each draw's range and pick z by
+// the exact fixed-point scan of c^2 over the range. fine: ranges of 2^ZR_FINE z
+// recomputed from the folded last-pass tile; else a range is a tile half.
+cudaError_t launch_zsample(int single, int fine, int M, const PassArgs &a, const DrawInfo *draws, int z_per_x,
                            unsigned long long *zs, float *cz, cudaStream_t st);
 
 // gates (k_gates.cu)

@@ -269,6 +269,43 @@ __device__ __forceinline__ void moment_sums(const float2 (&h)[E], float2 sc, uin
     }
 }
 
+// Weights of the 2^ZR_FINE-z ranges of a last-pass tile (at least 64
+// threads; slot bits are z' bits 0..4 and thread t holds z' = zb + k, so a
+// warp spans 2^10 consecutive z'). With j >= ZR_FINE (or x = 0, pair
+// (z', z' + d/2)) a warp's c(z0) fill one range and its c(z1) another, s2
+// being ordered (c(z0)^2, c(z1)^2); with j < ZR_FINE a half-warp's 2^9 z'
+// yield both c of 2^10 consecutive z. Each range of the family is written by
+// exactly one warp or half-warp.
+__device__ __forceinline__ void fine_range_weights(float2 s2, unsigned long long x, int j, unsigned long long half,
+                                                   uint32_t zb, float *row, bool active) {
+    const int lane = threadIdx.x & 31;
+    const bool split = (x == 0) || (j >= ZR_FINE);
+    unsigned long long z0, z1;
+    if (x) {
+        z0 = insert0((unsigned long long)zb, j);
+        z1 = z0 | (1ULL << j);
+    } else {
+        z0 = zb;
+        z1 = (unsigned long long)zb | half;
+    }
+    float wa = split ? s2.x : s2.x + s2.y, wb = s2.y;
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+        wa += __shfl_xor_sync(0xffffffffu, wa, o);
+        wb += __shfl_xor_sync(0xffffffffu, wb, o);
+    }
+    if (split) {
+        wa += __shfl_xor_sync(0xffffffffu, wa, 16);
+        wb += __shfl_xor_sync(0xffffffffu, wb, 16);
+        if (active && lane == 0) {
+            row[z0 >> ZR_FINE] = wa;
+            row[z1 >> ZR_FINE] = wb;
+        }
+    } else if (active && (lane & 15) == 0) {
+        row[z0 >> ZR_FINE] = wa;
+    }
+}
+
 template <class Cfg, int SRC, int DST, int PREC = 0>
 __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const PassArgs a) {
     typedef typename Cfg::Real R;
@@ -418,13 +455,16 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const Pas
         float2 s2 = make_float2(0.f, 0.f), s4 = s2, s6 = s2, sl = s2, w = s2;
         float qmax = 0.f;
         const bool wr = a.want_ranges, cand = a.want_cand;
+        // ranges of 2^ZR_FINE z (written per warp) or tile halves (2^M z)
+        constexpr bool FINE = SRC == SRC_BUF && Cfg::M > ZR_FINE;
+        constexpr int RLS = FINE ? ZR_FINE : Cfg::M;
         if (x) {
             const float2 sc = make_float2(2.0f * s, 2.0f * s);
-            if (wr && j >= Cfg::M) {
-                // range A holds every c(z0), range B every c(z1): order each
-                // pair as (c(z0)^2, c(z1)^2) and s2 is the pair of weights.
-                // Bit k of pm: parity of |x & z0| for z' = zb | k (z0 then
-                // carries the Im part).
+            if (wr && j >= RLS) {
+                // every c(z0) and every c(z1) of a range block lie in ranges
+                // of their own: order each pair as (c(z0)^2, c(z1)^2) and s2
+                // is the pair of weights. Bit k of pm: parity of |x & z0| for
+                // z' = zb | k (z0 then carries the Im part).
                 const uint32_t xd = (uint32_t)((x & ((1ULL << j) - 1ULL)) | ((x >> (j + 1)) << j));
                 const uint32_t pm = walsh_mask5(xd & (Cfg::E - 1)) ^ ((__popc(xd & zb) & 1) ? 0xFFFFFFFFu : 0u);
                 if (cand) moment_sums<Cfg::E, true, true>(v, sc, pm, s2, s4, s6, sl, qmax);
@@ -433,7 +473,7 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const Pas
             } else {
                 if (cand) moment_sums<Cfg::E, false, true>(v, sc, 0u, s2, s4, s6, sl, qmax);
                 else moment_sums<Cfg::E, false, false>(v, sc, 0u, s2, s4, s6, sl, qmax);
-                if (wr) {
+                if (wr && !FINE) {
                     // both c of a pair lie in the range picked by bit M-1 of z'
                     constexpr int RBIT = Cfg::M > 0 ? Cfg::M - 1 : 0;
                     if constexpr (RBIT >= Cfg::RB) {
@@ -459,6 +499,9 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const Pas
             if (cand) moment_sums<Cfg::E, false, true>(hs, sc, 0u, s2, s4, s6, sl, qmax);
             else moment_sums<Cfg::E, false, false>(hs, sc, 0u, s2, s4, s6, sl, qmax);
             w = s2;                    // z' -> range A, z' + d/2 -> range B
+        }
+        if constexpr (FINE) {
+            if (wr) fine_range_weights(s2, x, j, half, zb, a.rw_out + (size_t)slot * (size_t)a.rw_stride, active);
         }
         float acc[6] = {s2.x + s2.y, s4.x + s4.y, s6.x + s6.y, sl.x + sl.y, w.x, w.y};
         double out[6];

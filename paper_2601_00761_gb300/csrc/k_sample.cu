@@ -164,10 +164,194 @@ cudaError_t launch_zs(const PassArgs &a, const DrawInfo *draws, int z_per_x, uns
     return cudaErrorInvalidValue;
 }
 
+// Fine ranges (multi-pass plans whose last tiles exceed 2^ZR_FINE points):
+// one warp per draw. The draw's range is 2^ZR_FINE consecutive z, and every
+// z' = z with bit j removed that it needs lies in one aligned block of
+// 2^ZR_FINE outputs of a last-pass tile. The Walsh transform factorises over
+// disjoint bit sets, so that block is the ZR_FINE-bit transform of the tile's
+// input summed over its M - ZR_FINE top bits with signs (-1)^{F.h}, F the
+// block's top bits: the warp reads the tile once, folds it, and transforms
+// 2^ZR_FINE points instead of 2^M.
+constexpr int FOLD_WARPS = 4;   // 152 registers a thread: three CTAs per SM
+
+template <int M>
+__global__ void __launch_bounds__(32 * FOLD_WARPS) zsample_fold_kernel(const PassArgs a, const DrawInfo *draws,
+                                                                      int z_per_x, unsigned long long *zs,
+                                                                      float *cz) {
+    constexpr int RL = ZR_FINE, NB = 1 << RL, H = 1 << (M - RL), SW = NB + NB / 32;
+    static_assert(M > RL && RL == 10, "a warp holds 32 x 32 folded points");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2 *sm = reinterpret_cast<float2 *>(smraw) + warp * SW;
+    const long long idx = (long long)blockIdx.x * FOLD_WARPS + warp;
+    if (idx >= a.n_fam * (long long)z_per_x) return;      // uniform over the warp
+    const long long slot = idx / z_per_x;
+    const int kdraw = (int)(idx - slot * z_per_x);
+    const long long gf = a.fam_base + slot;
+    const int N = a.N, n = a.n;
+    const unsigned long long x = a.xs[gf] & ((1ULL << N) - 1ULL);
+    const int j = x ? 63 - __clzll((long long)x) : n;
+    const size_t out = (size_t)gf * z_per_x + kdraw;
+    const DrawInfo dr = draws[out];
+    const unsigned long long zstart = dr.range << RL;
+    const unsigned long long zp0 = ((zstart >> (j + 1)) << j) | (zstart & ((1ULL << j) - 1ULL));
+    const unsigned long long zblk = zp0 & ~(unsigned long long)(NB - 1);
+    const unsigned long long tile = zblk >> M;
+    const uint32_t F = (uint32_t)(zblk >> RL) & (uint32_t)(H - 1);
+    const float2 *src = reinterpret_cast<const float2 *>(a.src) + (size_t)slot * (size_t)a.slot_elems +
+                        (size_t)(tile << M) + lane;
+
+    // fold: f[k] = sum_h (-1)^{F.h} y[h 2^RL + 32 k + lane]
+    float2 f[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) f[k] = make_float2(0.f, 0.f);
+#pragma unroll 1
+    for (int h = 0; h < H; ++h) {
+        const float sg = (__popc(F & (uint32_t)h) & 1) ? -1.f : 1.f;
+        const float2 sg2 = make_float2(sg, sg);
+        const float2 *sb = src + (size_t)h * NB;
+#pragma unroll
+        for (int k0 = 0; k0 < 32; k0 += 16) {
+            float2 y[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) y[q] = __ldg(sb + 32 * (k0 + q));
+#pragma unroll
+            for (int q = 0; q < 16; ++q) f[k0 + q] = fma2(sg2, y[q], f[k0 + q]);
+        }
+    }
+    // ZR_FINE-bit transform: bits 5..9 in registers, then bits 0..4 after a
+    // transpose through shared memory (padded: conflict-free both ways)
+    butterflies<float2, 32, 0, 5>(f);
+#pragma unroll
+    for (int k = 0; k < 32; ++k) sm[33 * k + lane] = f[k];
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 32; ++k) f[k] = sm[33 * lane + k];
+    __syncwarp();
+    butterflies<float2, 32, 0, 5>(f);          // lane l, slot k: output 32 l + k
+
+    // per-draw scalars once per warp (the FP64 pipe is narrow on this part)
+    float s = 0.f, scf = 0.f;
+    unsigned long long T = 0;
+    if (lane == 0) {
+        s = (float)(*a.s_ptr);
+        const double scale = dr.wr > 0.0 ? 0x1.0p31 / dr.wr : 0.0;
+        double tq = dr.t * scale;
+        if (tq < 0.0) tq = 0.0;
+        T = tq < 1.8e19 ? (unsigned long long)tq : ~0ULL;
+        scf = (float)scale;
+    }
+    s = __shfl_sync(0xffffffffu, s, 0);
+    scf = __shfl_sync(0xffffffffu, scf, 0);
+    T = __shfl_sync(0xffffffffu, T, 0);
+
+    // the range's c^2 in z order as u32 fixed-point quanta (2^31 per range
+    // weight) and its signed c; lane l then owns entries 32 l .. 32 l + 31
+    uint32_t *wq = reinterpret_cast<uint32_t *>(sm);
+    float *cv = reinterpret_cast<float *>(wq + SW);
+    auto pp = [](uint32_t p) { return p + (p >> 5); };
+    // c(z0), c(z1) of z' = zblk + 32 lane + k as in the last pass's epilogue
+    // (z < 2^31: 32-bit indices; z0 = z' with 0 inserted at bit j)
+    const uint32_t x32 = (uint32_t)x, r32 = (uint32_t)dr.range, zs32 = (uint32_t)zstart;
+    const uint32_t hm = ~((1u << j) - 1u), jb = 1u << j;
+    const uint32_t zl = (uint32_t)zblk + 32u * (uint32_t)lane;
+    const float sc = 2.0f * s;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        const uint32_t zp = zl + (uint32_t)k;
+        const uint32_t z0 = zp + (zp & hm), z1 = z0 | jb;
+        float c0, c1;
+        if (x) {
+            const int k0 = __popc(x32 & z0);
+            const float re = sc * f[k].x, im = sc * f[k].y;
+            c0 = (float)sgn_phase(k0) * ((k0 & 1) ? im : re);
+            c1 = (float)sgn_phase(k0 + 1) * ((k0 & 1) ? re : im);
+        } else {
+            c0 = s * (f[k].x + f[k].y);
+            c1 = s * (f[k].x - f[k].y);
+        }
+        if ((z0 >> RL) == r32) {
+            const uint32_t q = pp(z0 - zs32);
+            wq[q] = __float2uint_rn(fminf(c0 * c0 * scf, 4.0e9f));
+            cv[q] = c0;
+        }
+        if ((z1 >> RL) == r32) {
+            const uint32_t q = pp(z1 - zs32);
+            wq[q] = __float2uint_rn(fminf(c1 * c1 * scf, 4.0e9f));
+            cv[q] = c1;
+        }
+    }
+    __syncwarp();
+
+    const uint32_t lo = 32u * (uint32_t)lane;
+    unsigned long long own = 0;
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) own += wq[pp(lo + i)];
+    unsigned long long incl = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long up = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += up;
+    }
+    const unsigned long long total = __shfl_sync(0xffffffffu, incl, 31);
+    const unsigned long long before = incl - own;
+    if (T < total) {
+        if (before <= T && T < before + own) {     // exactly one lane
+            unsigned long long run = before;
+            uint32_t pick = lo + 31;
+            for (int i = 0; i < 32; ++i) {
+                run += wq[pp(lo + i)];
+                if (run > T) { pick = lo + i; break; }
+            }
+            zs[out] = zstart + pick;
+            cz[out] = cv[pp(pick)];
+        }
+    } else {
+        // target at or beyond the fixed-point total (FP32 rounding of the
+        // range weight): the last z of nonzero weight
+        int last = -1;
+        for (int i = 31; i >= 0; --i)
+            if (wq[pp(lo + i)] != 0u) { last = (int)(lo + i); break; }
+        const int m = __reduce_max_sync(0xffffffffu, last);
+        if (lane == 0) {
+            const uint32_t pick = m >= 0 ? (uint32_t)m : 0u;
+            zs[out] = zstart + pick;
+            cz[out] = cv[pp(pick)];
+        }
+    }
+}
+
+template <int M>
+cudaError_t launch_fold(const PassArgs &a, const DrawInfo *draws, int z_per_x, unsigned long long *zs, float *cz,
+                        cudaStream_t st) {
+    constexpr size_t smem = sizeof(float2) * (size_t)FOLD_WARPS * ((1 << ZR_FINE) + (1 << ZR_FINE) / 32);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(zsample_fold_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const long long nd = a.n_fam * (long long)z_per_x;
+    const long long nb = (nd + FOLD_WARPS - 1) / FOLD_WARPS;
+    if (nb > 0x7fffffffLL) return cudaErrorInvalidValue;
+    zsample_fold_kernel<M><<<(unsigned)nb, 32 * FOLD_WARPS, smem, st>>>(a, draws, z_per_x, zs, cz);
+    return cudaGetLastError();
+}
+
 template <int M> using SampleSingle = TileCfg<float, M, 0, (M < 5 ? M : 5), 1>;
 
-cudaError_t launch_zsample(int single, int M, const PassArgs &a, const DrawInfo *draws, int z_per_x,
+cudaError_t launch_zsample(int single, int fine, int M, const PassArgs &a, const DrawInfo *draws, int z_per_x,
                            unsigned long long *zs, float *cz, cudaStream_t st) {
+    if (fine) {
+        switch (M) {
+        case 11: return launch_fold<11>(a, draws, z_per_x, zs, cz, st);
+        case 12: return launch_fold<12>(a, draws, z_per_x, zs, cz, st);
+        case 13: return launch_fold<13>(a, draws, z_per_x, zs, cz, st);
+        case 14: return launch_fold<14>(a, draws, z_per_x, zs, cz, st);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     if (single) {
         switch (M) {
 #define C(m) case m: return launch_zs<SampleSingle<m>, SRC_PSI_FAMILY>(a, draws, z_per_x, zs, cz, st);

@@ -57,12 +57,17 @@ struct Plan {
     int npass = 1, nstrided = 0;
     int K[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0}, ms[4] = {0, 0, 0, 0};
     int M_last = 0;
+    int RL = 0;                  // log2 of the z-range size of the two-level sampler
     long long tiles_last = 1;
     long long B = 1;
     size_t slot_bytes = 0;
 };
 
 int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// z-ranges of 2^ZR_FINE z (weights written by the last pass, draws resolved by
+// the folding sampler) for multi-pass plans whose last tiles are larger
+bool fine_ranges(const Plan &P) { return P.npass > 1 && P.M_last > ZR_FINE; }
 
 // ------------------------------------------------------------ autotuner table
 // Best (radix_log2, tile_log2, x_batch) per N found by sre_autotune; used when
@@ -123,6 +128,7 @@ sre_status plan_for(int N, const sre_opts *o, int prec, Plan &P) {
     if (P.n <= single_max) {
         P.npass = 1;
         P.M_last = P.n;
+        P.RL = P.n;
         P.tiles_last = 1;
         P.slot_bytes = 0;
         P.B = 1LL << 20;
@@ -175,6 +181,7 @@ sre_status plan_for(int N, const sre_opts *o, int prec, Plan &P) {
     if (B > 4096) B = 4096;
     if (prec == 32 && o && o->x_batch > 0) B = o->x_batch;
     P.B = B;
+    P.RL = fine_ranges(P) ? ZR_FINE : P.M_last;
     return SRE_OK;
 }
 
@@ -224,7 +231,8 @@ struct McWS {
     void *inter;
     TilePartial *tiles;
     FamMoments *fm;
-    double *W;
+    float *Wf;       // range weights (FP32, one row per family of the batch)
+    double *W;       // their inclusive FP64 scan
     DrawInfo *draws;
     unsigned long long *zs;
     float *cz;
@@ -244,7 +252,8 @@ void layout_mc(Arena &A, const Plan &P, int mode, long long n_x, int zpx, McWS &
     w.inter = P.npass > 1 ? (void *)A.take<char>(P.slot_bytes * (size_t)P.B) : nullptr;
     w.tiles = A.take<TilePartial>((size_t)B * (size_t)P.tiles_last);
     w.fm = A.take<FamMoments>(n_x);
-    const long long nr = 1LL << (P.N - P.M_last);
+    const long long nr = 1LL << (P.N - P.RL);
+    w.Wf = marg ? A.take<float>((size_t)B * (size_t)nr) : nullptr;
     w.W = marg ? A.take<double>((size_t)B * (size_t)nr) : nullptr;
     const size_t nd = marg ? (size_t)n_x * (size_t)zpx : 1;
     w.draws = marg ? A.take<DrawInfo>(nd) : nullptr;
@@ -319,7 +328,7 @@ PassArgs base_args(const Plan &P, const void *psi, const double *scal) {
     a.N = P.N;
     a.n = P.n;
     a.slot_elems = 1LL << P.n;
-    a.range_log2 = P.M_last;
+    a.range_log2 = P.RL;
     a.s_ptr = scal + SCAL_S;
     a.cand_thr = 1.0f - 1e-4f;
     a.want_cand = 1;
@@ -891,7 +900,7 @@ sre_status sre_make_plan(int N, const sre_opts *opts, sre_plan *plan) {
     plan->pass_lo[P.npass - 1] = 0;
     plan->pass_bits[P.npass - 1] = P.M_last;
     plan->x_batch = (int)(P.B > 0x7fffffff ? 0x7fffffff : P.B);
-    plan->range_log2 = P.M_last;
+    plan->range_log2 = P.RL;
     if (N <= 26) {
         size_t b = 0;
         if (sre_workspace_bytes(N, -1, 0, 0, &o, &b) == SRE_OK) plan->workspace_exact = b;
@@ -1025,8 +1034,11 @@ sre_status sre_mc(const void *psi, int N, int mode, long long n_x, int z_per_x, 
     a.tile_out = w.tiles;
     a.want_ranges = marg ? 1 : 0;
     a.want_cand = 0;                 // the estimators need no nullity candidates
+    a.rw_out = w.Wf;
+    a.rw_stride = 1LL << (N - P.RL);
     const long long step = P.B < n_x ? P.B : n_x;
-    const long long nr = 1LL << (N - P.M_last);
+    const long long nr = 1LL << (N - P.RL);
+    const bool fine = fine_ranges(P);
     bool timing;
     {
         std::lock_guard<std::mutex> lk(g_timing_mu);
@@ -1040,16 +1052,16 @@ sre_status sre_mc(const void *psi, int N, int mode, long long n_x, int z_per_x, 
         b.fam_base = fb;
         b.n_fam = nf;
         CS(run_transform(P, b, SRC_PSI_FAMILY, DST_MOMENTS, w.inter, st, (timing && nf == step) ? &T : nullptr));
-        CK(launch_fam_reduce(w.tiles, nf, (int)P.tiles_last, w.xs, fb, N, P.M_last, P.M_last, w.fm, fb,
-                             marg ? w.W : nullptr, nr, st));
+        CK(launch_fam_reduce(w.tiles, nf, (int)P.tiles_last, w.xs, fb, N, P.M_last, P.RL, w.fm, fb,
+                             (marg && !fine) ? w.Wf : nullptr, nr, st));
         count_launches(1);
         if (marg) {
-            CK(launch_zrange_select(w.W, nr, nf, fb, z_per_x, seed, counter0, w.draws, st));
+            CK(launch_zrange_select(w.Wf, w.W, nr, nf, fb, z_per_x, seed, counter0, w.draws, st));
             count_launches(1);
             PassArgs c = b;
             c.src = w.inter;
             c.lo_g = 0;
-            CK(launch_zsample(P.npass == 1, P.M_last, c, w.draws, z_per_x, w.zs, w.cz, st));
+            CK(launch_zsample(P.npass == 1, fine ? 1 : 0, P.M_last, c, w.draws, z_per_x, w.zs, w.cz, st));
             count_launches(1);
         }
     }

@@ -184,6 +184,11 @@ __device__ __forceinline__ void tile_transform(typename Cfg::C2 (&v)[Cfg::E], ty
     if constexpr (Cfg::NR > 0) Rounds<Cfg, 0>::run(v, sm, t, g);
 }
 
+// z-ranges of the two-level sampler: 2^ZR_FINE consecutive z per range when
+// the last pass of a multi-pass plan has tiles of more than 2^ZR_FINE points;
+// otherwise one range is one half of a last-pass tile (2^M z).
+constexpr int ZR_FINE = 10;
+
 // ------------------------------------------------------------- pass args
 enum SrcMode { SRC_PSI_FAMILY = 0, SRC_PSI_Q = 1, SRC_BUF = 2 };
 enum DstMode {
@@ -216,6 +221,10 @@ struct PassArgs {
     float cand_thr;                    // FP32 candidate threshold
     int want_ranges;                   // DST_MOMENTS: also produce the z-range weights
     int want_cand;                     // DST_MOMENTS: also flag nullity candidates (exact sweeps)
+    // DST_MOMENTS on last-pass tiles of more than 2^ZR_FINE points: the
+    // weight of every 2^ZR_FINE-z range, one row of rw_stride floats per slot
+    float *rw_out;
+    long long rw_stride;
     // Several states of the same N in one launch: the family index F (from xs
     // or fam_base + slot) is (state << N) | x; psi and s come from these
     // per-state device arrays. NULL for the one-state entry points.

@@ -320,7 +320,7 @@ def test_mc_n24_full_size_sampled(sre):
     closed form."""
     N = 24
     psi = inputs.haar_state(N, 24)
-    n_x, zpx = 48, 16
+    n_x, zpx = 48, 32
     r = sre.sre_mc(dev(psi), sre.SRE_MC_MARGINAL, n_x, zpx, seed=24, return_samples=True)
     xs = r["xs"].cpu().numpy().astype(np.uint64)
     zs = r["zs"].cpu().numpy().astype(np.uint64)
@@ -330,24 +330,68 @@ def test_mc_n24_full_size_sampled(sre):
     assert xs[0] == 0
     for i in range(1, n_x):
         assert int(xs[i]) == oracle.inverse_cdf(p, oracle.mc_draw(24, 0, i, 0))
+    rl = sre.sre_make_plan(N)["range_log2"]
     n_exact = n_total = 0
-    for i in (0, 7):
+    for i in (0, 7, 13, 21):
         x = int(xs[i])
         cf = oracle.family_spectrum(psi, x)
         cg = sre.sre_family_spectrum(dev(psi), x).cpu().numpy().astype(np.float64)
         for k in range(zpx):
             u = oracle.mc_draw(24, 0, i, 1 + k)
             zo = oracle.inverse_cdf(cf * cf, u)
-            ok, exact = draw_within_bound(int(zs[i, k]), zo, cf * cf, cg * cg, u)
+            ok, exact = draw_within_bound(int(zs[i, k]), zo, cf * cf, cg * cg, u, rl)
             assert ok, (i, k, int(zs[i, k]), zo)
             n_exact += exact
             n_total += 1
-    assert n_exact >= 0.9 * n_total
-    for i, k in ((1, 0), (5, 3), (40, 15)):
+    # Every draw is valid (above). Identity with the FP64 draw is a rate: the
+    # FP32 spectrum's running sums differ from the oracle's by ~1e-7 of the
+    # total, a few entries of 2^24, so a few percent of draws land 1-7 z
+    # later (measured 95-96% identical over 384 draws); 85% of 128 draws is
+    # five standard deviations below that.
+    assert n_exact >= 0.85 * n_total
+    for i, k in ((1, 0), (5, 3), (40, 31)):
         assert abs(c[i, k] - oracle.pauli_expectation(psi, int(xs[i]), int(zs[i, k]))) < TOL_C
     m2_haar = math.log2(2**N + 3) - 2
     assert abs(r["M_rb"][1] - m2_haar) < 4 * r["err_rb"][1] + 1e-4
     assert abs(r["M"][1] - m2_haar) < 5 * r["err_M"][1] + 1e-3
+
+
+@pytest.mark.parametrize("k_low", [16, 12, 8])
+def test_mc_marginal_fine_ranges(sre, k_low):
+    """Multi-pass plan (N=16: a 13-bit last pass, z-ranges of 2^10): a Haar
+    state on the low k_low qubits with the rest in |0>, so the families' top
+    X bit j falls above the last tile (k_low = 16), inside it above the range
+    size (12) or below the range size (8) -- the three ways a range maps to
+    last-pass outputs. Draws against the oracle's inverse CDF, sampled c
+    against brute force."""
+    N = 16
+    assert sre.sre_make_plan(N)["range_log2"] == 10 and sre.sre_make_plan(N)["pass_bits"][-1] == 13
+    psi = np.zeros(1 << N, dtype=np.complex128)
+    psi[: 1 << k_low] = inputs.haar_state(k_low, 900 + k_low)
+    n_x, zpx = 24, 24
+    r = sre.sre_mc(dev(psi), sre.SRE_MC_MARGINAL, n_x, zpx, seed=5, return_samples=True)
+    xs = r["xs"].cpu().numpy().astype(np.uint64)
+    zs = r["zs"].cpu().numpy().astype(np.uint64)
+    c = r["c"].cpu().numpy()
+    ref = oracle.mc_marginal(psi, n_x, zpx, 5, 0)
+    assert np.array_equal(xs, ref["xs"])
+    assert all(int(x) < (1 << k_low) for x in xs)
+    ref_zs = ref["zs"].reshape(n_x, zpx)
+    n_exact = n_total = 0
+    for i in range(n_x):
+        x = int(xs[i])
+        cf = oracle.family_spectrum(psi, x)
+        cg = sre.sre_family_spectrum(dev(psi), x).cpu().numpy().astype(np.float64)
+        for k in range(zpx):
+            u = oracle.mc_draw(5, 0, i, 1 + k)
+            zo = int(ref_zs[i, k])
+            assert zo == oracle.inverse_cdf(cf * cf, u)
+            ok, exact = draw_within_bound(int(zs[i, k]), zo, cf * cf, cg * cg, u, 10)
+            assert ok, (i, k, int(zs[i, k]), zo)
+            n_exact += exact
+            n_total += 1
+            assert abs(c[i, k] - cf[int(zs[i, k])]) < TOL_C
+    assert n_exact >= 0.9 * n_total
 
 
 # ----------------------------------------------------------------- gates
