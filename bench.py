@@ -65,7 +65,7 @@ def profiled_traffic(N, dom_pass):
         txt = open(os.path.join(ROOT, "profiles", "strided_pass_n24.md")).read()
         vals = dict(l.split(": ", 1) for l in txt.splitlines() if l.startswith(("traffic_bytes", "source_sha")))
         h = hashlib.sha256()
-        for f in ("k_pass.cuh", "sre_internal.cuh", "k_pass_f32_multi.cu"):
+        for f in ("k_pass.cuh", "sre_internal.cuh", "k_pass_f32_multi.cu", "k_pass_dispatch.cuh"):
             h.update(open(os.path.join(ROOT, "paper_2601_00761_gb300", "csrc", f), "rb").read())
         if h.hexdigest()[:16] != vals["source_sha256_16"].strip():
             return None
@@ -275,7 +275,7 @@ def run_cuda(a):
     traffic = tpf * fam_per_launch if (tpf is not None and fam_per_launch) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic,
-                "traffic_note": "ncu dram read+write of a 4-family capture scaled to the launch's families "
+                "traffic_note": "ncu dram read+write of a 32-family capture scaled to the launch's families "
                                 "(profiles/strided_pass_n24.md)" if traffic else None, "kernel": ["strided pass 0 (reads psi, writes the packed intermediate)",
                                             "row pass (reads the intermediate, fused moments)"][min(dom, 1)]
                 if npass == 2 else f"pass {dom}",
