@@ -106,6 +106,10 @@ typedef struct {
     long long n_families; /* families transformed */
     long long n_samples;  /* (x, z) pairs drawn (MC marginal), else 0 */
     long long n_boundary; /* reserved (0) */
+    double r2;          /* fluctuation ratio Std_{x != 0}(m_x) / E_x[m_x] of the per-family sums
+                           m_x = sum_z c_{x,z}^4 that govern the uniform-x Monte Carlo estimator
+                           (Supplemental Material, Clifford preconditioning): exact sweeps over all x;
+                           sre_mc UNIFORM, the estimate from its sampled families; NaN otherwise */
 } sre_result;
 
 typedef struct {

@@ -84,6 +84,8 @@ def lib():
             L.or_apply_gates.argtypes = [_c_dp, ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong]
             L.or_apply_gates.restype = ctypes.c_int
             L.or_set_mutation.argtypes = [ctypes.c_int]
+            L.or_fluctuation_ratio.argtypes = [_c_fp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+            L.or_fluctuation_ratio.restype = ctypes.c_int
             L.or_clifford_conjugate.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_uint64,
                                                 ctypes.c_uint64, _c_u64p, _c_u64p, ctypes.POINTER(ctypes.c_int)]
             L.or_clifford_conjugate.restype = ctypes.c_int
@@ -199,6 +201,16 @@ def sre_exact(psi, eps: float = 1e-6, per_family: bool = False) -> dict:
     if fam is not None:
         out["family"] = fam
     return out
+
+
+def fluctuation_ratio(psi) -> float:
+    """r_2 = Std_{x != 0}(m_{2;x}) / E_x[m_{2;x}] over all X-masks (SM,
+    Clifford preconditioning), m_{2;x} from the family's FP64 spectrum."""
+    a = _psi(psi)
+    r = ctypes.c_double(0.0)
+    if lib().or_fluctuation_ratio(_fp(a), _nq(a), ctypes.byref(r)) != 0:
+        raise MemoryError("oracle allocation failed")
+    return r.value
 
 
 def sre_bruteforce(psi, eps: float = 1e-6) -> dict:

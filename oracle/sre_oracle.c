@@ -14,6 +14,7 @@
  *   - one Walsh-Hadamard transform per X-mask x              (Eq. Z-FWHT, Algorithm 1)
  *   - M_alpha and the stabilizer nullity                      (Eq. SRE-def, nullity def.)
  *   - the MC estimator with x = 0 forced                      (SM Sec. I)
+ *   - the fluctuation ratio r_2 of the per-family sums        (SM, Clifford preconditioning)
  *   - the x-marginal p(x) and the sampling of (x, z) ~ c^2/d  (SM Sec. III target pi(P))
  *   - H, S, S^dag, CNOT, T, T^dag gates on a state vector     (Clifford preconditioning, T doping)
  *   - Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11)
@@ -251,6 +252,36 @@ int or_sre_exact(const float *psi, int N, double eps, double *M, double *S,
     *stab_count = count;
     *nullity = -1;
     if (count > 0 && (count & (count - 1)) == 0) *nullity = N - (63 - __builtin_clzll((uint64_t)count));
+    free(c); free(w);
+    return 0;
+}
+
+/* Fluctuation ratio of the per-family sums (SM, Clifford preconditioning:
+ * r_2 := Std_{x != 0}(m_{2;x}) / E_x[m_{2;x}], with m_{2;x} proportional to
+ * sum_z |c_{x,z}|^4). E_x is the mean over all d X-masks, Std_{x != 0} the
+ * population standard deviation over the d - 1 masks x != 0; the ratio does
+ * not depend on the normalisation of m. Returns 0, or -1 on allocation
+ * failure. */
+int or_fluctuation_ratio(const float *psi, int N, double *r2) {
+    uint64_t d = 1ULL << N;
+    double s = 1.0 / or_norm2(psi, N);
+    double *c = (double *)malloc(d * sizeof(double));
+    cplx *w = (cplx *)malloc(d * sizeof(cplx));
+    if (!c || !w) { free(c); free(w); return -1; }
+    ksum all = {0, 0}, nz = {0, 0}, nz2 = {0, 0};
+    for (uint64_t x = 0; x < d; ++x) {
+        or_family_spectrum(psi, N, x, s, c, NULL, w);
+        ksum m = {0, 0};
+        for (uint64_t z = 0; z < d; ++z) kadd(&m, c[z] * c[z] * c[z] * c[z]);
+        double mx = kval(&m);
+        kadd(&all, mx);
+        if (x != 0) { kadd(&nz, mx); kadd(&nz2, mx * mx); }
+    }
+    double mean_all = kval(&all) / (double)d;
+    double mean_nz = kval(&nz) / (double)(d - 1);
+    double var = kval(&nz2) / (double)(d - 1) - mean_nz * mean_nz;
+    if (var < 0.0) var = 0.0;
+    *r2 = sqrt(var) / mean_all;
     free(c); free(w);
     return 0;
 }

@@ -51,13 +51,13 @@ class Result(ctypes.Structure):
                 ("M_rb", ctypes.c_double * 3), ("err_rb", ctypes.c_double * 3), ("parseval", ctypes.c_double),
                 ("stab_count", ctypes.c_longlong), ("nullity", ctypes.c_int), ("n_passes", ctypes.c_int),
                 ("n_flagged", ctypes.c_longlong), ("n_families", ctypes.c_longlong),
-                ("n_samples", ctypes.c_longlong), ("n_boundary", ctypes.c_longlong)]
+                ("n_samples", ctypes.c_longlong), ("n_boundary", ctypes.c_longlong), ("r2", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {"M": list(self.M), "S": list(self.S), "err_M": list(self.err_M), "M_rb": list(self.M_rb),
                 "err_rb": list(self.err_rb), "parseval": self.parseval, "stab_count": self.stab_count,
                 "nullity": self.nullity, "n_passes": self.n_passes, "n_flagged": self.n_flagged,
-                "n_families": self.n_families, "n_samples": self.n_samples}
+                "n_families": self.n_families, "n_samples": self.n_samples, "r2": self.r2}
 
 
 class Plan(ctypes.Structure):

@@ -143,10 +143,11 @@ __global__ void __launch_bounds__(256) exact_partial_kernel(const FamMoments *fm
     __shared__ double red[8];
     const long long per = (n_fam + gridDim.x - 1) / gridDim.x;
     const long long lo = (long long)blockIdx.x * per, hi = lo + per < n_fam ? lo + per : n_fam;
-    double a0 = 0, a1 = 0, a2 = 0, a3 = 0, c = 0;
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0, c = 0, q = 0;
     for (long long f = lo + threadIdx.x; f < hi; f += 256) {
         const FamMoments &m = fm[f];
         a0 += m.m[0]; a1 += m.m[1]; a2 += m.m[2]; a3 += m.m[3]; c += (double)m.cand;
+        if (f > 0) q += m.m[1] * m.m[1];
         if (m.cand && flag_list) {
             unsigned long long pos = atomicAdd(n_flag, 1ULL);
             flag_list[pos] = (unsigned long long)f;
@@ -157,27 +158,30 @@ __global__ void __launch_bounds__(256) exact_partial_kernel(const FamMoments *fm
     a2 = block_sum<256>(a2, red);
     a3 = block_sum<256>(a3, red);
     c = block_sum<256>(c, red);
+    q = block_sum<256>(q, red);
     if (threadIdx.x == 0) {
-        double *o = partial + 5 * blockIdx.x;
-        o[0] = a0; o[1] = a1; o[2] = a2; o[3] = a3; o[4] = c;
+        double *o = partial + 6 * blockIdx.x;
+        o[0] = a0; o[1] = a1; o[2] = a2; o[3] = a3; o[4] = c; o[5] = q;
     }
 }
 
-__global__ void __launch_bounds__(256) exact_final_kernel(const double *partial, int n_part, double *out) {
+__global__ void __launch_bounds__(256) exact_final_kernel(const double *partial, int n_part, const FamMoments *fm0,
+                                                          double *out) {
     __shared__ double red[8];
-    for (int a = 0; a < 5; ++a) {
+    for (int a = 0; a < 6; ++a) {
         double s = 0.0;
-        for (int i = threadIdx.x; i < n_part; i += 256) s += partial[5 * i + a];
+        for (int i = threadIdx.x; i < n_part; i += 256) s += partial[6 * i + a];
         s = block_sum<256>(s, red);
         if (threadIdx.x == 0) out[a] = s;
     }
+    if (threadIdx.x == 0) out[6] = fm0[0].m[1];
 }
 
 cudaError_t launch_exact_totals(const FamMoments *fm, long long n_fam, double *partial, int n_part,
                                 double *out, unsigned long long *flag_list, unsigned long long *n_flag,
                                 cudaStream_t st) {
     exact_partial_kernel<<<n_part, 256, 0, st>>>(fm, n_fam, partial, flag_list, n_flag);
-    exact_final_kernel<<<1, 256, 0, st>>>(partial, n_part, out);
+    exact_final_kernel<<<1, 256, 0, st>>>(partial, n_part, fm, out);
     return cudaGetLastError();
 }
 
@@ -480,10 +484,11 @@ __global__ void __launch_bounds__(256) state_totals_kernel(const FamMoments *fm,
     const int st = s0 + blockIdx.x;
     const long long nf = 1LL << N;
     const long long f0 = ((long long)st << N) - fm_first_family;
-    double a0 = 0, a1 = 0, a2 = 0, a3 = 0, c = 0;
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0, c = 0, q = 0;
     for (long long f = threadIdx.x; f < nf; f += 256) {
         const FamMoments &m = fm[f0 + f];
         a0 += m.m[0]; a1 += m.m[1]; a2 += m.m[2]; a3 += m.m[3]; c += (double)m.cand;
+        if (f > 0) q += m.m[1] * m.m[1];
         if (m.cand) {
             const unsigned long long pos = atomicAdd(n_flag, 1ULL);
             flags[pos] = ((unsigned long long)st << N) | (unsigned long long)f;
@@ -494,9 +499,10 @@ __global__ void __launch_bounds__(256) state_totals_kernel(const FamMoments *fm,
     a2 = block_sum<256>(a2, red);
     a3 = block_sum<256>(a3, red);
     c = block_sum<256>(c, red);
+    q = block_sum<256>(q, red);
     if (threadIdx.x == 0) {
-        double *o = totals + 5 * (size_t)st;
-        o[0] = a0; o[1] = a1; o[2] = a2; o[3] = a3; o[4] = c;
+        double *o = totals + TOT_N * (size_t)st;
+        o[0] = a0; o[1] = a1; o[2] = a2; o[3] = a3; o[4] = c; o[5] = q; o[6] = fm[f0].m[1];
     }
 }
 

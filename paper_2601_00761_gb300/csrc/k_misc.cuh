@@ -8,6 +8,10 @@ namespace sre {
 enum { SCAL_NORM2 = 0, SCAL_S = 1, SCAL_N = 8 };
 constexpr int NORM_BLOCKS = 1216;          // 152 SMs x 8
 constexpr unsigned long long SCAN_CHUNK = 4096;
+// totals of an exact sweep (per state): sum over families of c^2, c^4, c^6,
+// c^2 log2 c^2 sums, candidate count, sum over x != 0 of (sum_z c^4)^2, and
+// the x = 0 family's sum_z c^4 (the last two give the fluctuation ratio r_2)
+constexpr int TOT_N = 7;
 
 struct DrawInfo {
     unsigned long long range;   // z-range (size 2^RL) of the draw

@@ -2,6 +2,7 @@
 // workspace layout and the launch sequences of each entry point.
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
@@ -211,7 +212,7 @@ void layout_exact(Arena &A, const Plan &P, const Plan &P64, ExactWS &w) {
     const unsigned long long d = 1ULL << P.N;
     w.scal = A.take<double>(SCAL_N);
     w.npart = A.take<double>(NORM_BLOCKS);
-    w.epart = A.take<double>(5 * EXACT_PARTS);
+    w.epart = A.take<double>(6 * EXACT_PARTS);
     w.etot = A.take<double>(8);
     w.inter = P.npass > 1 ? (void *)A.take<char>(P.slot_bytes * (size_t)P.B) : nullptr;
     const long long nb = P.npass > 1 ? P.B : (long long)d;
@@ -449,7 +450,24 @@ sre_status run_marginal(const void *psi, int N, const double *scal, double *p, d
     return SRE_OK;
 }
 
-void finalize_exact(const double T[5], int N, sre_result *r) {
+static_assert(offsetof(sre_result, stab_count) == 128 && offsetof(sre_result, r2) == 176 &&
+                  sizeof(sre_result) == 184, "sre_result layout is part of the ABI");
+
+// Fluctuation ratio of the per-family sums m_x = sum_z c_{x,z}^4 (SM, Clifford
+// preconditioning): r_2 = Std_{x != 0}(m_x) / E_x[m_x], population moments over
+// the d - 1 families x != 0 and the mean over all d (a ratio: the
+// normalisation of m_x cancels). sum_all = sum_x m_x, sq_nz = sum_{x != 0} m_x^2.
+double fluctuation_ratio(double sum_all, double sq_nz, double m_x0, double d) {
+    if (d < 2.0) return std::nan("");
+    const double mean_nz = (sum_all - m_x0) / (d - 1.0);
+    double var = sq_nz / (d - 1.0) - mean_nz * mean_nz;
+    if (var < 0.0) var = 0.0;
+    const double mean_all = sum_all / d;
+    return mean_all > 0.0 ? std::sqrt(var) / mean_all : std::nan("");
+}
+
+// T: the TOT_N totals of an exact sweep (k_misc.cuh)
+void finalize_exact(const double *T, int N, sre_result *r) {
     const double d = std::ldexp(1.0, N);
     const double H = N * (T[0] / d) - T[3] / d;
     r->S[0] = H;
@@ -465,12 +483,14 @@ void finalize_exact(const double T[5], int N, sre_result *r) {
     r->err_M[1] = 4.0 * ec / std::log(2.0);
     r->err_M[2] = 6.0 * ec / (2.0 * std::log(2.0));
     for (int a = 0; a < 3; ++a) { r->M_rb[a] = r->M[a]; r->err_rb[a] = r->err_M[a]; }
+    r->r2 = fluctuation_ratio(T[1], T[5], T[6], d);
 }
 
 void init_result(sre_result *r) {
     memset(r, 0, sizeof *r);
     r->stab_count = -1;
     r->nullity = -1;
+    r->r2 = std::nan("");
 }
 
 sre_status nullity_from_count(long long cnt, int N, sre_result *r) {
@@ -519,13 +539,13 @@ sre_status exact_impl(const void *psi, int N, const sre_opts &o, void *ws, size_
     CK(cudaMemsetAsync(w.nflag, 0, sizeof(unsigned long long), st));
     CK(launch_exact_totals(w.fm, (long long)d, w.epart, EXACT_PARTS, w.etot, w.flags, w.nflag, st));
     count_launches(2);
-    double host[8];
+    double host[TOT_N + 1];
     unsigned long long nflag = 0;
-    CK(cudaMemcpyAsync(host, w.etot, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(host, w.etot, TOT_N * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&nflag, w.nflag, sizeof nflag, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(host + 5, w.scal + SCAL_NORM2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(host + TOT_N, w.scal + SCAL_NORM2, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (!(host[5] > 0.0)) return fail(SRE_EZERO, "psi has zero norm");
+    if (!(host[TOT_N] > 0.0)) return fail(SRE_EZERO, "psi has zero norm");
 
     // FP64 recheck of the candidate families
     unsigned long long cnt = 0;
@@ -604,7 +624,7 @@ void layout_batch(Arena &A, int count, std::vector<BucketPlan> &B, BatchWS &w) {
     w.s_list = A.take<double>(count);
     w.norm_list = A.take<double>(count);
     w.npart = A.take<double>((size_t)count * BATCH_NORM_BLOCKS);
-    w.totals = A.take<double>(5 * (size_t)count);
+    w.totals = A.take<double>(TOT_N * (size_t)count);
     w.state_count = A.take<unsigned long long>(count);
     w.nflag = A.take<unsigned long long>(B.size());
     size_t fm_n = 0, tiles_n = 0, inter_b = 0, inter64_b = 0, counts_n = 0;
@@ -658,7 +678,7 @@ sre_status batch_main(const std::vector<BucketPlan> &B, const BatchWS &w, int co
                                      w.fm, fb - f0, nullptr, 0, st));
                 count_launches(1);
             }
-            CK(launch_state_totals(w.fm, f0, b.N, c0, c1 - c0, w.totals + 5 * (size_t)b.off, b.flags,
+            CK(launch_state_totals(w.fm, f0, b.N, c0, c1 - c0, w.totals + TOT_N * (size_t)b.off, b.flags,
                                    w.nflag + bi, st));
             count_launches(1);
         }
@@ -770,9 +790,9 @@ sre_status batched_impl(const void *const *psi_ptrs, const int *Ns, int count, c
         CK(launch_count_scatter(b.flags, w.counts, nf, b.N, w.state_count + b.off, st));
         count_launches(1);
     }
-    std::vector<double> tot(5 * (size_t)count), nrm(count);
+    std::vector<double> tot(TOT_N * (size_t)count), nrm(count);
     std::vector<unsigned long long> cnt(count);
-    CK(cudaMemcpyAsync(tot.data(), w.totals, sizeof(double) * 5 * count, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(tot.data(), w.totals, sizeof(double) * TOT_N * count, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(nrm.data(), w.norm_list, sizeof(double) * count, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(cnt.data(), w.state_count, sizeof(unsigned long long) * count, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -782,7 +802,7 @@ sre_status batched_impl(const void *const *psi_ptrs, const int *Ns, int count, c
             const int slot = b.off + (int)k;
             sre_result *r = out + b.idx[k];
             init_result(r);
-            finalize_exact(&tot[5 * (size_t)slot], b.N, r);
+            finalize_exact(&tot[TOT_N * (size_t)slot], b.N, r);
             r->n_families = 1LL << b.N;
             r->n_passes = b.P.npass;
             if (!(nrm[slot] > 0.0)) { zero = true; continue; }
@@ -1100,6 +1120,7 @@ sre_status sre_mc(const void *psi, int N, int mode, long long n_x, int z_per_x, 
                 out->S[k] = shat;
                 const double r = std::sqrt(var) / (shat / dd);
                 out->err_M[k] = r / (std::fabs(1.0 - alpha) * std::log(2.0) * std::sqrt((double)n_x));
+                if (k == 1) out->r2 = r;      // sampled Std_{x != 0}(m_x) / E_x[m_x]
             }
             out->M_rb[k] = out->M[k];
             out->err_rb[k] = out->err_M[k];

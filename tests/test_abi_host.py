@@ -126,6 +126,7 @@ def test_structs_match_header_layout():
     assert ctypes.sizeof(sre.Gate) == 3
     assert sre.Result.M.offset == 0 and sre.Result.parseval.offset == 15 * 8
     assert sre.Result.stab_count.offset == 16 * 8
+    assert sre.Result.r2.offset == 22 * 8 and ctypes.sizeof(sre.Result) == 23 * 8
 
 
 def test_oracle_not_imported_by_the_package():

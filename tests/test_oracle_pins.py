@@ -462,3 +462,45 @@ def test_mutations(m):
     finally:
         oracle.set_mutation(0)
     assert _pins_pass()
+
+
+# ------------------------------------------------ fluctuation ratio r_2
+def _r2_psi_m_closed_form(N):
+    """SM, analytic fluctuation ratio (Eq. sm-psi-m-ratio-exact) for
+    |T>^{N/2} (x) |0>^{N/2}, even N."""
+    h = N // 2
+    a = (5 / 4) ** h - 1
+    b = 4 ** h - 1
+    c = (3 / 2) ** h - 1
+    return (8 / 3) ** h * math.sqrt(a / b - c * c / (b * b))
+
+
+@pytest.mark.parametrize("N", [2, 4, 6, 8, 10])
+def test_r2_product_magic_state_closed_form(N):
+    psi = inputs.t_product_state(N, N // 2)
+    assert abs(oracle.fluctuation_ratio(psi) - _r2_psi_m_closed_form(N)) < 1e-9 * _r2_psi_m_closed_form(N)
+
+
+def test_r2_closed_form_large_n_asymptote():
+    # the closed form's leading term grows as (20/9)^{N/4} (SM, Eq. sm-psi-m-ratio-asym)
+    r40, r44 = _r2_psi_m_closed_form(40), _r2_psi_m_closed_form(44)
+    assert abs(r44 / r40 - (20 / 9)) < 1e-2
+
+
+@pytest.mark.parametrize("N", [4, 6, 8])
+def test_r2_family_values_product_magic_state(N):
+    """SM Eq. sm-psi-m-m2x: m_{2;x} = 4^{-N} sum_z c^4 = 2^{-3N/2-k} when x has
+    weight k on the |T> qubits and none on the |0> qubits, else 0."""
+    h = N // 2
+    fam = oracle.sre_exact(inputs.t_product_state(N, h), per_family=True)["family"]
+    for x in range(1 << N):
+        m = fam[x, 1] / 4.0 ** N
+        if x >> h:
+            assert m < 1e-15
+        else:
+            assert abs(m - 2.0 ** (-1.5 * N - bin(x).count("1"))) < 1e-12 * 2.0 ** (-1.5 * N)
+
+
+def test_r2_stabilizer_state_is_zero():
+    # |0>^N: only the x = 0 family is nonzero, so every x != 0 has m_x = 0
+    assert oracle.fluctuation_ratio(inputs.basis_state(6, 0)) == 0.0
