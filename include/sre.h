@@ -226,6 +226,20 @@ SRE_API sre_status stabilizer_nullity(const void *psi_c64_dev, int N, double eps
 SRE_API sre_status apply_clifford_tdoped_circuit(void *psi_c64_dev, int N, const sre_gate *gates_host,
                                          long long n_gates, void *stream);
 
+/* Apply general two-qubit gates in order, in place, to psi: the random
+ * brick-wall circuits of the Supplemental Material (Haar-random two-qubit
+ * gates; uniformly random two-qubit Cliffords as the preconditioner C of the
+ * main text). Gate k is the 4x4 complex matrix
+ *   U_k[out][in] = (mats_host[32k + 2(4 out + in)], mats_host[32k + 2(4 out + in) + 1])
+ * (row-major, interleaved re, im, FP32) on the ordered qubit pair
+ * (pairs_host[2k], pairs_host[2k+1]) = (q0, q1), local index l = bit(q0) +
+ * 2 bit(q1). Both arrays are host memory, read during the call. Runs of gates
+ * inside 12 qubits are fused into one pass over psi in shared memory. N in
+ * 2..32; q0 != q1, both < N, else SRE_EINVAL with psi untouched. The matrices
+ * are applied as given (unitarity is the caller's). Synchronises the stream. */
+SRE_API sre_status apply_two_qubit_gates(void *psi_c64_dev, int N, const float *mats_host, const int *pairs_host,
+                                         long long n_gates, void *stream);
+
 /* One X-mask family (Eq. Pxz-corr for one x): c_dev[z] = c_{x,z} for all z,
  * d floats, by the same transform kernels as sre_exact (precision from
  * opts, NULL = FP32). N in 1..30. */

@@ -12,6 +12,7 @@ pins for every function are in ``tests/test_oracle_pins.py``.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -85,6 +86,8 @@ def lib():
             L.or_apply_gates.restype = ctypes.c_int
             L.or_set_mutation.argtypes = [ctypes.c_int]
             L.or_fluctuation_ratio.argtypes = [_c_fp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+            L.or_apply_two_qubit.argtypes = [_c_dp, ctypes.c_int, _c_dp, ctypes.c_void_p, ctypes.c_longlong]
+            L.or_apply_two_qubit.restype = ctypes.c_int
             L.or_fluctuation_ratio.restype = ctypes.c_int
             L.or_clifford_conjugate.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_uint64,
                                                 ctypes.c_uint64, _c_u64p, _c_u64p, ctypes.POINTER(ctypes.c_int)]
@@ -201,6 +204,21 @@ def sre_exact(psi, eps: float = 1e-6, per_family: bool = False) -> dict:
     if fam is not None:
         out["family"] = fam
     return out
+
+
+def apply_two_qubit(psi, mats, pairs) -> np.ndarray:
+    """The state after the two-qubit gates (mats (n, 4, 4) U[out][in], local
+    index bit(q0) + 2 bit(q1); pairs (n, 2) = (q0, q1)), in complex128."""
+    v = np.ascontiguousarray(np.asarray(psi, dtype=np.complex128)).copy()
+    N = int(round(math.log2(v.size)))
+    m = np.ascontiguousarray(np.asarray(mats, dtype=np.complex128).reshape(-1, 4, 4))
+    mm = np.ascontiguousarray(np.stack([m.real, m.imag], axis=-1).reshape(-1))
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    rc = lib().or_apply_two_qubit(v.ctypes.data_as(_c_dp), N, mm.ctypes.data_as(_c_dp),
+                                  pr.ctypes.data_as(ctypes.c_void_p), pr.shape[0])
+    if rc != 0:
+        raise ValueError("bad qubit pair")
+    return v
 
 
 def fluctuation_ratio(psi) -> float:

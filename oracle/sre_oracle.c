@@ -15,6 +15,7 @@
  *   - M_alpha and the stabilizer nullity                      (Eq. SRE-def, nullity def.)
  *   - the MC estimator with x = 0 forced                      (SM Sec. I)
  *   - the fluctuation ratio r_2 of the per-family sums        (SM, Clifford preconditioning)
+ *   - dense two-qubit gates of brick-wall circuits            (SM, brick-wall circuits)
  *   - the x-marginal p(x) and the sampling of (x, z) ~ c^2/d  (SM Sec. III target pi(P))
  *   - H, S, S^dag, CNOT, T, T^dag gates on a state vector     (Clifford preconditioning, T doping)
  *   - Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11)
@@ -253,6 +254,35 @@ int or_sre_exact(const float *psi, int N, double eps, double *M, double *S,
     *nullity = -1;
     if (count > 0 && (count & (count - 1)) == 0) *nullity = N - (63 - __builtin_clzll((uint64_t)count));
     free(c); free(w);
+    return 0;
+}
+
+/* Two-qubit gates (SM, brick-wall circuits): gate k is the 4x4 complex
+ * matrix U_k = mats[32 k + 2 (4 out + in) + {0: re, 1: im}] acting on the
+ * ordered qubit pair (pairs[2k], pairs[2k+1]) = (q0, q1), with local index
+ * l = bit(q0) + 2 bit(q1):  psi'(b) = sum_l U[l(b)][l] psi(b with bits set
+ * to l). Applied in list order to psi_c128 (interleaved re, im) in place.
+ * Returns 0, or -1 on a bad qubit pair. */
+int or_apply_two_qubit(double *psi_c128, int N, const double *mats, const int *pairs, long long n_gates) {
+    uint64_t d = 1ULL << N;
+    cplx *psi = (cplx *)psi_c128;
+    for (long long k = 0; k < n_gates; ++k) {
+        int q0 = pairs[2 * k], q1 = pairs[2 * k + 1];
+        if (q0 < 0 || q1 < 0 || q0 >= N || q1 >= N || q0 == q1) return -1;
+        const double *m = mats + 32 * k;
+        uint64_t m0 = 1ULL << q0, m1 = 1ULL << q1;
+        for (uint64_t b = 0; b < d; ++b) {
+            if (b & (m0 | m1)) continue;
+            uint64_t idx[4] = {b, b | m0, b | m1, b | m0 | m1};
+            cplx v[4], o[4];
+            for (int l = 0; l < 4; ++l) v[l] = psi[idx[l]];
+            for (int r = 0; r < 4; ++r) {
+                o[r] = 0;
+                for (int l = 0; l < 4; ++l) o[r] += (m[2 * (4 * r + l)] + I * m[2 * (4 * r + l) + 1]) * v[l];
+            }
+            for (int l = 0; l < 4; ++l) psi[idx[l]] = o[l];
+        }
+    }
     return 0;
 }
 

@@ -108,6 +108,7 @@ def load():
         "stabilizer_nullity": ([_vp, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(ctypes.c_longlong), _vp], st),
         "apply_clifford_tdoped_circuit": ([_vp, ctypes.c_int, _vp, ctypes.c_longlong, _vp], st),
+        "apply_two_qubit_gates": ([_vp, ctypes.c_int, _vp, _vp, ctypes.c_longlong, _vp], st),
         "sre_family_spectrum": ([_vp, ctypes.c_int, ctypes.c_ulonglong, ctypes.POINTER(Opts), _vp, _vp], st),
         "sre_family_spectrum_f64": ([_vp, ctypes.c_int, ctypes.c_ulonglong, _vp, _vp], st),
         "sre_philox_blocks": ([_vp, _vp, ctypes.c_int, _vp], st),
@@ -300,6 +301,19 @@ def apply_clifford_tdoped_circuit(psi, gates) -> None:
     p, N = _psi_ptr(psi)
     g = np.ascontiguousarray(np.asarray(gates, dtype=np.uint8).reshape(-1, 3))
     _check(load().apply_clifford_tdoped_circuit(p, N, g.ctypes.data_as(ctypes.c_void_p), g.shape[0], _stream()))
+
+
+def apply_two_qubit_gates(psi, mats, pairs) -> None:
+    """Apply 4x4 gates in order, in place: mats (n, 4, 4) complex U[out][in]
+    with local index bit(q0) + 2 bit(q1), pairs (n, 2) = (q0, q1)."""
+    p, N = _psi_ptr(psi)
+    m = np.asarray(mats, dtype=np.complex64).reshape(-1, 4, 4)
+    mm = np.ascontiguousarray(np.stack([m.real, m.imag], axis=-1).astype(np.float32).reshape(-1))
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    if pr.shape[0] != m.shape[0]:
+        raise ValueError("one qubit pair per matrix")
+    _check(load().apply_two_qubit_gates(p, N, mm.ctypes.data_as(ctypes.c_void_p), pr.ctypes.data_as(ctypes.c_void_p),
+                                        pr.shape[0], _stream()))
 
 
 def sre_family_spectrum(psi, x: int, out=None, **kw):

@@ -1,5 +1,6 @@
-// k_gates.cu -- H, S, S^dag, T, T^dag and CNOT on a complex64 state vector
-// (the Clifford preconditioning circuits and T doping of the paper), applied
+// k_gates.cu -- H, S, S^dag, T, T^dag, CNOT and general two-qubit gates
+// (4x4 complex matrices) on a complex64 state vector (the Clifford
+// preconditioning circuits, T doping and brick-wall circuits of the paper), applied
 // in fused blocks: a run of consecutive gates acting inside a set of at most
 // GATE_BLOCK_Q qubits (always containing qubits 0..4, so every tile is made of
 // 256-byte contiguous runs) is applied to each 2^Q-amplitude tile in shared
@@ -16,7 +17,8 @@ struct GateBlockParams {
     int g0, ng;                  // gate rows [g0, g0 + ng) of the translated list
 };
 
-__global__ void __launch_bounds__(256) gate_block_kernel(float2 *psi, const GateRow *gates, GateBlockParams p) {
+__global__ void __launch_bounds__(256) gate_block_kernel(float2 *psi, const GateRow *gates, const float2 *mats,
+                                                         GateBlockParams p) {
     extern __shared__ __align__(16) float2 amp[];
     const unsigned long long tile = blockIdx.x + ((unsigned long long)blockIdx.y << 15);
     if (tile >= (1ULL << p.n_other)) return;   // uniform over the CTA
@@ -33,7 +35,32 @@ __global__ void __launch_bounds__(256) gate_block_kernel(float2 *psi, const Gate
         const GateRow G = gates[p.g0 + gi];
         __syncthreads();
         const int b0 = 1 << G.q0;
-        if (G.op == 0) {   // H
+        if (G.op == GATE_OP_U2) {   // 4x4 matrix of row p.g0 + gi, local index bit(q0) + 2 bit(q1)
+            const float2 *u = mats + 16 * (size_t)(p.g0 + gi);
+            float2 m[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) m[e] = __ldg(u + e);
+            const int b1 = 1 << G.q1;
+            const int lo = G.q0 < G.q1 ? G.q0 : G.q1, hi = G.q0 < G.q1 ? G.q1 : G.q0;
+            for (int pi = threadIdx.x; pi < L / 4; pi += 256) {
+                int i = ((pi >> lo) << (lo + 1)) | (pi & ((1 << lo) - 1));
+                i = ((i >> hi) << (hi + 1)) | (i & ((1 << hi) - 1));
+                const int idx[4] = {i, i | b0, i | b1, i | b0 | b1};
+                float2 v[4];
+#pragma unroll
+                for (int l = 0; l < 4; ++l) v[l] = amp[idx[l]];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    float re = 0.f, im = 0.f;
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) {
+                        re = fmaf(m[4 * r + l].x, v[l].x, fmaf(-m[4 * r + l].y, v[l].y, re));
+                        im = fmaf(m[4 * r + l].x, v[l].y, fmaf(m[4 * r + l].y, v[l].x, im));
+                    }
+                    amp[idx[r]] = make_float2(re, im);
+                }
+            }
+        } else if (G.op == 0) {   // H
             for (int pi = threadIdx.x; pi < L / 2; pi += 256) {
                 const int i = ((pi >> G.q0) << (G.q0 + 1)) | (pi & (b0 - 1));
                 const float2 u = amp[i], w = amp[i | b0];
@@ -75,8 +102,9 @@ __global__ void __launch_bounds__(256) gate_block_kernel(float2 *psi, const Gate
 // blocks_host: n_blocks x (g0, ng); block_qubits_host: n_blocks x GATE_BLOCK_Q
 // global qubits (ascending, 255 = unused). Gate rows in gates_dev carry local
 // qubit positions.
-cudaError_t launch_gate_blocks(float2 *psi, int N, const GateRow *gates_dev, const int *blocks_host, int n_blocks,
-                               const unsigned char *block_qubits_host, cudaStream_t st) {
+cudaError_t launch_gate_blocks(float2 *psi, int N, const GateRow *gates_dev, const float2 *mats_dev,
+                               const int *blocks_host, int n_blocks, const unsigned char *block_qubits_host,
+                               cudaStream_t st) {
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(gate_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -101,7 +129,7 @@ cudaError_t launch_gate_blocks(float2 *psi, int N, const GateRow *gates_dev, con
             if (!in[q]) p.other[p.n_other++] = (unsigned char)q;
         const unsigned long long tiles = 1ULL << p.n_other;
         dim3 grid((unsigned)(tiles < 32768 ? tiles : 32768), (unsigned)(tiles < 32768 ? 1 : tiles >> 15));
-        gate_block_kernel<<<grid, 256, sizeof(float2) << p.Q, st>>>(psi, gates_dev, p);
+        gate_block_kernel<<<grid, 256, sizeof(float2) << p.Q, st>>>(psi, gates_dev, mats_dev, p);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

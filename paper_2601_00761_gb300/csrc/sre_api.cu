@@ -884,6 +884,79 @@ sre_status autotune_impl(const void *psi, int N, cudaStream_t st, sre_opts *best
     return SRE_OK;
 }
 
+// Runs of consecutive gates acting inside <= GATE_BLOCK_Q qubits (qubits
+// 0..GATE_BLOCK_LOW-1 always included) become one pass over psi in shared
+// memory. Rows: op, q0, q1 (global qubits; q1 used by CNOT and U2);
+// mats_host: 32 floats per row (U2 rows only; NULL when there are none).
+sre_status run_gate_list(void *psi, int N, const std::vector<GateRow> &in_rows, const float *mats_host,
+                         cudaStream_t st) {
+    const long long n_gates = (long long)in_rows.size();
+    if (n_gates == 0) return SRE_OK;
+    const int low = N < GATE_BLOCK_LOW ? N : GATE_BLOCK_LOW;
+    const int qmax = N < GATE_BLOCK_Q ? N : GATE_BLOCK_Q;
+    auto two = [](const GateRow &G) { return G.op == SRE_GATE_CNOT || G.op == GATE_OP_U2; };
+    std::vector<int> blocks;
+    std::vector<unsigned char> bq;
+    std::vector<GateRow> rows(n_gates);
+    long long g0 = 0;
+    while (g0 < n_gates) {
+        bool in[64] = {false};
+        int cnt = 0;
+        for (int q = 0; q < low; ++q) { in[q] = true; ++cnt; }
+        long long g = g0;
+        for (; g < n_gates; ++g) {
+            const GateRow &G = in_rows[g];
+            const int add = (!in[G.q0]) + (two(G) && !in[G.q1] && G.q1 != G.q0 ? 1 : 0);
+            if (cnt + add > qmax) break;
+            if (!in[G.q0]) { in[G.q0] = true; ++cnt; }
+            if (two(G) && !in[G.q1]) { in[G.q1] = true; ++cnt; }
+        }
+        unsigned char loc[64];
+        unsigned char list[GATE_BLOCK_Q];
+        int m = 0;
+        for (int q = 0; q < N; ++q)
+            if (in[q]) { loc[q] = (unsigned char)m; list[m++] = (unsigned char)q; }
+        for (int i = m; i < GATE_BLOCK_Q; ++i) list[i] = 255;
+        for (long long k = g0; k < g; ++k) {
+            rows[k].op = in_rows[k].op;
+            rows[k].q0 = loc[in_rows[k].q0];
+            rows[k].q1 = two(in_rows[k]) ? loc[in_rows[k].q1] : 0;
+        }
+        blocks.push_back((int)g0);
+        blocks.push_back((int)(g - g0));
+        bq.insert(bq.end(), list, list + GATE_BLOCK_Q);
+        g0 = g;
+    }
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    GateRow *dg = nullptr;
+    float2 *dm = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_ws_mu);
+        if ((int)g_gatebuf.size() <= dev) g_gatebuf.resize(dev + 1);
+        DevBuf &b = g_gatebuf[dev];
+        const size_t rows_bytes = (sizeof(GateRow) * (size_t)n_gates + 255) & ~(size_t)255;
+        const size_t need = rows_bytes + (mats_host ? sizeof(float2) * 16 * (size_t)n_gates : 0);
+        if (b.n < need) {
+            if (b.p) CK(cudaFree(b.p));
+            b.p = nullptr;
+            b.n = 0;
+            cudaError_t e = cudaMalloc(&b.p, need);
+            if (e != cudaSuccess) return fail(SRE_ENOMEM, "gate buffer: %s", cudaGetErrorString(e));
+            b.n = need;
+        }
+        dg = (GateRow *)b.p;
+        if (mats_host) dm = (float2 *)((char *)b.p + rows_bytes);
+    }
+    CK(cudaMemcpyAsync(dg, rows.data(), sizeof(GateRow) * (size_t)n_gates, cudaMemcpyHostToDevice, st));
+    if (mats_host)
+        CK(cudaMemcpyAsync(dm, mats_host, sizeof(float2) * 16 * (size_t)n_gates, cudaMemcpyHostToDevice, st));
+    CK(launch_gate_blocks((float2 *)psi, N, dg, dm, blocks.data(), (int)(blocks.size() / 2), bq.data(), st));
+    count_launches(blocks.size() / 2);
+    CK(cudaStreamSynchronize(st));
+    return SRE_OK;
+}
+
 } // namespace
 
 namespace sre {
@@ -1255,66 +1328,29 @@ sre_status apply_clifford_tdoped_circuit(void *psi, int N, const sre_gate *gates
         if (G.op == SRE_GATE_CNOT && (G.q1 >= N || G.q1 == G.q0))
             return fail(SRE_EINVAL, "gate %lld: bad CNOT target %d", g, G.q1);
     }
-    if (n_gates == 0) return SRE_OK;
-    // split into blocks of consecutive gates acting inside <= GATE_BLOCK_Q qubits
-    const int low = N < GATE_BLOCK_LOW ? N : GATE_BLOCK_LOW;
-    const int qmax = N < GATE_BLOCK_Q ? N : GATE_BLOCK_Q;
-    std::vector<int> blocks;
-    std::vector<unsigned char> bq;
-    std::vector<GateRow> rows(n_gates);
-    long long g0 = 0;
-    while (g0 < n_gates) {
-        bool in[64] = {false};
-        int cnt = 0;
-        for (int q = 0; q < low; ++q) { in[q] = true; ++cnt; }
-        long long g = g0;
-        for (; g < n_gates; ++g) {
-            const sre_gate &G = gates[g];
-            int add = (!in[G.q0]) + (G.op == SRE_GATE_CNOT && !in[G.q1] && G.q1 != G.q0 ? 1 : 0);
-            if (cnt + add > qmax) break;
-            if (!in[G.q0]) { in[G.q0] = true; ++cnt; }
-            if (G.op == SRE_GATE_CNOT && !in[G.q1]) { in[G.q1] = true; ++cnt; }
-        }
-        unsigned char loc[64];
-        unsigned char list[GATE_BLOCK_Q];
-        int m = 0;
-        for (int q = 0; q < N; ++q)
-            if (in[q]) { loc[q] = (unsigned char)m; list[m++] = (unsigned char)q; }
-        for (int i = m; i < GATE_BLOCK_Q; ++i) list[i] = 255;
-        for (long long k = g0; k < g; ++k) {
-            rows[k].op = gates[k].op;
-            rows[k].q0 = loc[gates[k].q0];
-            rows[k].q1 = gates[k].op == SRE_GATE_CNOT ? loc[gates[k].q1] : 0;
-        }
-        blocks.push_back((int)g0);
-        blocks.push_back((int)(g - g0));
-        bq.insert(bq.end(), list, list + GATE_BLOCK_Q);
-        g0 = g;
+    std::vector<GateRow> rows((size_t)n_gates);
+    for (long long g = 0; g < n_gates; ++g) {
+        rows[g].op = gates[g].op;
+        rows[g].q0 = gates[g].q0;
+        rows[g].q1 = gates[g].op == SRE_GATE_CNOT ? gates[g].q1 : 0;
     }
-    cudaStream_t st = (cudaStream_t)stream;
-    int dev = 0;
-    CK(cudaGetDevice(&dev));
-    GateRow *dg = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_ws_mu);
-        if ((int)g_gatebuf.size() <= dev) g_gatebuf.resize(dev + 1);
-        DevBuf &b = g_gatebuf[dev];
-        const size_t need = sizeof(GateRow) * (size_t)n_gates;
-        if (b.n < need) {
-            if (b.p) CK(cudaFree(b.p));
-            b.p = nullptr;
-            b.n = 0;
-            cudaError_t e = cudaMalloc(&b.p, need);
-            if (e != cudaSuccess) return fail(SRE_ENOMEM, "gate buffer: %s", cudaGetErrorString(e));
-            b.n = need;
-        }
-        dg = (GateRow *)b.p;
+    return run_gate_list(psi, N, rows, nullptr, (cudaStream_t)stream);
+}
+
+sre_status apply_two_qubit_gates(void *psi, int N, const float *mats, const int *pairs, long long n_gates,
+                                 void *stream) {
+    CS(check_psi(psi, N, 2, 32));
+    if (n_gates < 0 || (n_gates > 0 && (!mats || !pairs))) return fail(SRE_EINVAL, "bad gate list");
+    std::vector<GateRow> rows((size_t)n_gates);
+    for (long long g = 0; g < n_gates; ++g) {
+        const int q0 = pairs[2 * g], q1 = pairs[2 * g + 1];
+        if (q0 < 0 || q1 < 0 || q0 >= N || q1 >= N || q0 == q1)
+            return fail(SRE_EINVAL, "gate %lld: bad qubit pair (%d, %d) for N=%d", g, q0, q1, N);
+        rows[g].op = GATE_OP_U2;
+        rows[g].q0 = (unsigned char)q0;
+        rows[g].q1 = (unsigned char)q1;
     }
-    CK(cudaMemcpyAsync(dg, rows.data(), sizeof(GateRow) * (size_t)n_gates, cudaMemcpyHostToDevice, st));
-    CK(launch_gate_blocks((float2 *)psi, N, dg, blocks.data(), (int)(blocks.size() / 2), bq.data(), st));
-    count_launches(blocks.size() / 2);
-    CK(cudaStreamSynchronize(st));
-    return SRE_OK;
+    return run_gate_list(psi, N, rows, mats, (cudaStream_t)stream);
 }
 
 unsigned long long sre_kernel_launches(void) { return g_launches.load(); }

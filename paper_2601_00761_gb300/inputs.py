@@ -147,6 +147,83 @@ def random_clifford_gates(N: int, n_gates: int, seed: int) -> np.ndarray:
     return random_clifford_tdoped_gates(N, n_gates, 0, seed)
 
 
+# --------------------------------------------- two-qubit gates, brick walls
+# A two-qubit gate is a 4x4 complex matrix U[out][in] on an ordered pair of
+# qubits (q0, q1); its local basis index is l = bit(q0) + 2 bit(q1), the same
+# layout as the matrices apply_two_qubit_gates takes.
+
+def _key(u: np.ndarray) -> tuple:
+    """A matrix modulo global phase: divided by the phase of its first entry
+    of modulus above 1/4, rounded."""
+    f = u.reshape(-1)
+    k = int(np.argmax(np.abs(f) > 0.25))
+    v = f * (abs(f[k]) / f[k])
+    return tuple(np.round(np.concatenate([v.real, v.imag]) * 1e6).astype(np.int64))
+
+
+_CLIFFORD2 = None
+
+
+def two_qubit_clifford_table() -> np.ndarray:
+    """All 11520 two-qubit Clifford unitaries modulo global phase (complex128,
+    (11520, 4, 4)), by breadth-first closure of H and S on either qubit and
+    CNOT in both directions."""
+    global _CLIFFORD2
+    if _CLIFFORD2 is not None:
+        return _CLIFFORD2
+    h = np.array([[1, 1], [1, -1]]) / np.sqrt(2)
+    sg = np.diag([1, 1j])
+    i2 = np.eye(2)
+    cx01 = np.zeros((4, 4)); cx10 = np.zeros((4, 4))
+    for l in range(4):
+        b0, b1 = l & 1, l >> 1
+        cx01[b0 + 2 * (b1 ^ b0), l] = 1      # control q0, target q1
+        cx10[(b0 ^ b1) + 2 * b1, l] = 1      # control q1, target q0
+    gens = [np.kron(i2, h), np.kron(h, i2), np.kron(i2, sg), np.kron(sg, i2), cx01, cx10]
+    seen = {_key(np.eye(4)): np.eye(4, dtype=np.complex128)}
+    frontier = [np.eye(4, dtype=np.complex128)]
+    while frontier:
+        nxt = []
+        for u in frontier:
+            for g in gens:
+                v = g @ u
+                k = _key(v)
+                if k not in seen:
+                    seen[k] = v
+                    nxt.append(v)
+        frontier = nxt
+    _CLIFFORD2 = np.stack(list(seen.values()))
+    return _CLIFFORD2
+
+
+def haar_two_qubit(g: np.random.Generator) -> np.ndarray:
+    """Haar-random U(4): QR of a complex Gaussian matrix, R's diagonal phases
+    moved into Q."""
+    z = (g.standard_normal((4, 4)) + 1j * g.standard_normal((4, 4))) / np.sqrt(2)
+    q, r = np.linalg.qr(z)
+    ph = np.diag(r) / np.abs(np.diag(r))
+    return q * ph
+
+
+def brickwall_circuit(N: int, depth: int, kind: str, seed: int, first_layer: int = 0):
+    """Brick-wall circuit of random two-qubit gates on nearest neighbours
+    (SM, brick-wall circuits; even and odd layers count separately): layer t
+    acts on the pairs (i, i + 1) with i = (t + first_layer) mod 2, i + 2, ...
+    kind "clifford": uniform two-qubit Cliffords; "haar": Haar-random U(4).
+    Returns (mats complex64 (n, 4, 4), pairs int32 (n, 2))."""
+    g = _rng(seed)
+    table = two_qubit_clifford_table() if kind == "clifford" else None
+    mats, pairs = [], []
+    for t in range(depth):
+        for i in range((t + first_layer) % 2, N - 1, 2):
+            u = table[g.integers(0, len(table))] if table is not None else haar_two_qubit(g)
+            mats.append(u)
+            pairs.append((i, i + 1))
+    if not mats:
+        return np.zeros((0, 4, 4), np.complex64), np.zeros((0, 2), np.int32)
+    return np.asarray(mats, np.complex64), np.asarray(pairs, np.int32)
+
+
 def uniform_inputs_u64(n: int, seed: int) -> np.ndarray:
     """Raw 64-bit words for host-side tests of sampling helpers."""
     return _rng(seed).integers(0, 2**63, size=n, dtype=np.int64).astype(np.uint64)

@@ -114,6 +114,12 @@ def test_argument_errors_do_not_touch_the_gpu(L):
     assert L.apply_clifford_tdoped_circuit(_fake_ptr(0x1000), 4, g, 1, None) == sre.SRE_EINVAL
     g = (sre.Gate * 1)(sre.Gate(0, 4, 0))
     assert L.apply_clifford_tdoped_circuit(_fake_ptr(0x1000), 4, g, 1, None) == sre.SRE_EINVAL
+    mats = (ctypes.c_float * 32)()
+    for bad in ((1, 1), (0, 4), (-1, 2)):
+        pr = (ctypes.c_int * 2)(*bad)
+        assert L.apply_two_qubit_gates(_fake_ptr(0x1000), 4, mats, pr, 1, None) == sre.SRE_EINVAL
+    assert L.apply_two_qubit_gates(_fake_ptr(0x1000), 1, mats, (ctypes.c_int * 2)(0, 1), 1, None) == sre.SRE_EINVAL
+    assert L.apply_two_qubit_gates(_fake_ptr(0x1000), 4, None, None, 1, None) == sre.SRE_EINVAL
     assert L.sre_family_spectrum(_fake_ptr(0x1000), 4, 16, None, _fake_ptr(0x2000), None) == sre.SRE_EINVAL
     assert L.pauli_x_marginal(_fake_ptr(0x1000), 4, None, None, 0, None) == sre.SRE_EINVAL
     p = sre.Plan()

@@ -504,3 +504,74 @@ def test_r2_family_values_product_magic_state(N):
 def test_r2_stabilizer_state_is_zero():
     # |0>^N: only the x = 0 family is nonzero, so every x != 0 has m_x = 0
     assert oracle.fluctuation_ratio(inputs.basis_state(6, 0)) == 0.0
+
+
+# ------------------------------------------------- two-qubit gates (brick walls)
+_PAULI1 = [np.eye(2), np.array([[0, 1], [1, 0]]), np.array([[0, -1j], [1j, 0]]), np.diag([1, -1])]
+
+
+def test_two_qubit_clifford_table_is_the_group():
+    """11520 = |C_2| modulo phase; every element unitary and mapping Pauli
+    operators to signed Pauli operators; closed under products."""
+    t = inputs.two_qubit_clifford_table()
+    assert t.shape == (11520, 4, 4)
+    paulis = [np.kron(a, b) for a in _PAULI1 for b in _PAULI1]
+    g = np.random.default_rng(3)
+    for u in t[g.integers(0, len(t), 64)]:
+        assert np.allclose(u.conj().T @ u, np.eye(4), atol=1e-12)
+        for p in paulis[1:]:
+            q = u @ p @ u.conj().T
+            assert any(np.allclose(q, s * r, atol=1e-9) for r in paulis for s in (1, -1))
+    keys = {inputs._key(u) for u in t}
+    for _ in range(64):
+        a, b = t[g.integers(0, len(t))], t[g.integers(0, len(t))]
+        assert inputs._key(a @ b) in keys
+
+
+def _dense_two_qubit(N, u, q0, q1):
+    """The 2^N x 2^N matrix of u on (q0, q1), built from index arithmetic."""
+    d = 1 << N
+    full = np.zeros((d, d), dtype=np.complex128)
+    for b in range(d):
+        lin = ((b >> q0) & 1) + 2 * ((b >> q1) & 1)
+        rest = b & ~((1 << q0) | (1 << q1))
+        for lo in range(4):
+            bo = rest | ((lo & 1) << q0) | ((lo >> 1) << q1)
+            full[bo, b] += u[lo, lin]
+    return full
+
+
+@pytest.mark.parametrize("pair", [(0, 1), (2, 0), (1, 3), (3, 2)])
+def test_two_qubit_gate_vs_dense(pair):
+    N = 4
+    g = np.random.default_rng(sum(pair))
+    psi = g.standard_normal(16) + 1j * g.standard_normal(16)
+    u = inputs.haar_two_qubit(g)
+    out = oracle.apply_two_qubit(psi, u[None], [pair])
+    assert np.allclose(out, _dense_two_qubit(N, u, *pair) @ psi, atol=1e-12)
+
+
+def test_two_qubit_gate_kron_of_one_qubit_gates():
+    # kron(B, A) on (q0, q1) is A on q0 and B on q1 (local index bit(q0) + 2 bit(q1))
+    g = np.random.default_rng(9)
+    psi = g.standard_normal(8) + 1j * g.standard_normal(8)
+    a = inputs.haar_two_qubit(g)[:2, :2]
+    a = np.linalg.qr(a)[0]
+    out = oracle.apply_two_qubit(psi, np.kron(np.eye(2), a)[None], [(2, 0)])
+    ref = np.einsum("ij,jab->iab", a, psi.reshape(2, 2, 2)).reshape(-1)   # axis 0 of the C-order reshape is qubit 2
+    assert np.allclose(out, ref, atol=1e-12)
+
+
+def test_brickwall_clifford_preserves_sre_and_haar_norm():
+    N = 6
+    psi = inputs.t_product_state(N, 3).astype(np.complex128)
+    m, p = inputs.brickwall_circuit(N, 2 * N, "clifford", 5)
+    after = oracle.apply_two_qubit(psi, m, p)
+    a, b = oracle.sre_exact(psi.astype(np.complex64)), oracle.sre_exact(after.astype(np.complex64))
+    assert np.allclose(a["M"], b["M"], atol=1e-6)
+    assert abs(b["M"][1] - 3 * math.log2(4 / 3)) < 1e-6
+    zero = oracle.apply_two_qubit(inputs.basis_state(N, 0), m, p)
+    assert oracle.sre_exact(zero.astype(np.complex64))["nullity"] == 0
+    mh, ph = inputs.brickwall_circuit(N, 5, "haar", 6)
+    out = oracle.apply_two_qubit(inputs.haar_state(N, 2), mh, ph)
+    assert abs(np.vdot(out, out).real - 1.0) < 1e-6
