@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tc", action="store_true")
-    ap.add_argument("--workload", default="mc24", choices=["mc24", "batched"],
+    ap.add_argument("--workload", default="mc24", choices=["mc24", "batched", "precondition"],
                     help="mc24: the headline N=24 MC step; batched: exact M_2/nullity of 4096 T-doped states "
                          "with N ~ U{8..16} in one sre_exact_batched call, against a per-state loop")
     ap.add_argument("--count", type=int, default=4096)
@@ -426,12 +426,104 @@ def run_batched(a):
     return 0
 
 
+def run_precondition(a):
+    """Clifford preconditioning (main text and SM): the product magic state
+    |T>^{N/2}|0>^{N/2}, a random brick-wall Clifford circuit of depth
+    N_C = 2N applied on the device (timed: K applications after W warm-up
+    applications, each one host call including its gate-table upload), and
+    the uniform-x estimator's fluctuation ratio r_2 and M_2 before and after
+    (n_x families each)."""
+    import torch
+    from paper_2601_00761_gb300 import build as sre_build
+    sre_build.build()
+    import paper_2601_00761_gb300 as sre
+    from paper_2601_00761_gb300 import inputs
+    torch.cuda.set_device(0)
+    N = a.N
+    n_x = a.nx if a.nx != 4096 else 20000
+    psi = torch.from_numpy(inputs.t_product_state(N, N // 2)).cuda()
+    mats, pairs = inputs.brickwall_circuit(N, 2 * N, "clifford", 30 + N)
+    before = sre.sre_mc(psi, sre.SRE_MC_UNIFORM, n_x, 1, seed=N)
+    scratch = psi.clone()
+    for _ in range(a.warmup):
+        sre.apply_two_qubit_gates(scratch, mats, pairs)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    l0 = sre.sre_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    e0.record(stream)
+    for _ in range(a.steps):
+        sre.apply_two_qubit_gates(scratch, mats, pairs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / a.steps
+    blocks = (sre.sre_kernel_launches() - l0) // a.steps
+    sweep_bytes = blocks * 2 * 8 * 2 ** N          # each fused block reads and writes psi once
+    gbps = sweep_bytes / (ms / 1e3) / 1e9
+    hbm, peak_kind = peaks()
+    # a general two-qubit gate is a 4x4 complex matrix on each of the 2^(N-2)
+    # amplitude quartets: 16 complex multiply-adds = 64 real FMA = 128 FLOP
+    flop = len(pairs) * 2 ** (N - 2) * 128.0
+    tflops = flop / (ms / 1e3) / 1e12
+    fp32_peak = fp32_fma_peak_tflops()
+    after_state = psi.clone()
+    sre.apply_two_qubit_gates(after_state, mats, pairs)
+    after = sre.sre_mc(after_state, sre.SRE_MC_UNIFORM, n_x, 1, seed=N)
+    m2 = (N // 2) * math.log2(4 / 3)
+    line = {"metric": f"brick-wall Clifford preconditioner (depth 2N) on psi at N={N}, two-qubit gates applied per second",
+            "value": len(pairs) / (ms / 1e3), "unit": "gates/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (|T>^{N/2}|0>^{N/2}, seeded uniform two-qubit Cliffords)",
+            "config": {"workload": f"N={N} product magic state, {len(pairs)} two-qubit Cliffords in {2 * N} "
+                                   f"brick-wall layers, then {n_x} uniform-x MC families",
+                       "N": N, "gates": int(len(pairs)), "layers": 2 * N, "n_x": n_x},
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": tflops / fp32_peak, "traffic": None,
+                         "kernel": "gate_block_kernel (13-qubit fused blocks, 4x4 complex matrices)",
+                         "flop_per_step": flop,
+                         "peak_kind": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x max SM clock (MEASURED_PEAKS.json sm_max_mhz)",
+                         "hbm": {"bytes_per_step": sweep_bytes, "achieved_GBps": gbps, "frac": gbps / hbm},
+                         "blocks_per_circuit": int(blocks)},
+            "clocks": clk, "gpu_launches": int(blocks * a.steps),
+            "study": {"M2_closed_form": m2,
+                      "before": {"r2": before["r2"], "M2": before["M"][1], "err_M2": before["err_M"][1]},
+                      "after": {"r2": after["r2"], "M2": after["M"][1], "err_M2": after["err_M"][1]},
+                      "r2_closed_form_before": r2_psi_m(N)}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def fp32_fma_peak_tflops():
+    """FP32 FMA rate from the unit counts (152 SMs x 128 FP32 lanes, 2 FLOP
+    per FMA) and the measured maximum SM clock."""
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except Exception:
+        pass
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def r2_psi_m(N):
+    """SM closed form of r_2 for |T>^{N/2}|0>^{N/2} (even N)."""
+    h = N // 2
+    x, y, z = (5 / 4) ** h - 1, 4 ** h - 1, (3 / 2) ** h - 1
+    return (8 / 3) ** h * math.sqrt(x / y - z * z / (y * y))
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
     if a.workload == "batched":
         return run_batched(a)
+    if a.workload == "precondition":
+        return run_precondition(a)
     return run_cuda(a)
 
 

@@ -234,7 +234,8 @@ SRE_API sre_status apply_clifford_tdoped_circuit(void *psi_c64_dev, int N, const
  * (row-major, interleaved re, im, FP32) on the ordered qubit pair
  * (pairs_host[2k], pairs_host[2k+1]) = (q0, q1), local index l = bit(q0) +
  * 2 bit(q1). Both arrays are host memory, read during the call. Runs of gates
- * inside 12 qubits are fused into one pass over psi in shared memory. N in
+ * inside 13 qubits are fused into one pass over psi in shared memory (gates on
+ * disjoint qubits are regrouped across layers, dependencies kept). N in
  * 2..32; q0 != q1, both < N, else SRE_EINVAL with psi untouched. The matrices
  * are applied as given (unitarity is the caller's). Synchronises the stream. */
 SRE_API sre_status apply_two_qubit_gates(void *psi_c64_dev, int N, const float *mats_host, const int *pairs_host,

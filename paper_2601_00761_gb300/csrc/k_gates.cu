@@ -20,26 +20,39 @@ struct GateBlockParams {
 __global__ void __launch_bounds__(256) gate_block_kernel(float2 *psi, const GateRow *gates, const float2 *mats,
                                                          GateBlockParams p) {
     extern __shared__ __align__(16) float2 amp[];
+    __shared__ unsigned long long hioff[1 << (GATE_BLOCK_Q - GATE_BLOCK_LOW)];
     const unsigned long long tile = blockIdx.x + ((unsigned long long)blockIdx.y << 15);
     if (tile >= (1ULL << p.n_other)) return;   // uniform over the CTA
     unsigned long long base = 0;
     for (int i = 0; i < p.n_other; ++i) base |= ((tile >> i) & 1ULL) << p.other[i];
     const int L = 1 << p.Q;
-    for (int l = threadIdx.x; l < L; l += 256) {
-        unsigned long long g = base;
-        for (int i = 0; i < p.Q; ++i) g |= (unsigned long long)((l >> i) & 1) << p.local[i];
-        amp[l] = psi[g];
+    // local bits 0..LOW-1 are global bits 0..LOW-1 (contiguous runs); the
+    // global offset of the remaining local bits h = l >> LOW, one table entry
+    // per value of h
+    const int low = p.Q < GATE_BLOCK_LOW ? p.Q : GATE_BLOCK_LOW;
+    const int nh = 1 << (p.Q - low);
+    for (int h = threadIdx.x; h < nh; h += 256) {
+        unsigned long long o = base;
+        for (int i = low; i < p.Q; ++i) o |= (unsigned long long)((h >> (i - low)) & 1) << p.local[i];
+        hioff[h] = o;
     }
+    // the block's two-qubit matrices, once per CTA (read back as broadcasts)
+    float2 *msm = amp + L;
+    if (mats)
+        for (int e = threadIdx.x; e < 16 * p.ng; e += 256) msm[e] = __ldg(mats + 16 * (size_t)p.g0 + e);
+    __syncthreads();
+    const int lm = (1 << low) - 1;
+    for (int l = threadIdx.x; l < L; l += 256) amp[l] = psi[hioff[l >> low] | (unsigned long long)(l & lm)];
     const float r2 = 0.70710678118654752440f;
     for (int gi = 0; gi < p.ng; ++gi) {
         const GateRow G = gates[p.g0 + gi];
         __syncthreads();
         const int b0 = 1 << G.q0;
         if (G.op == GATE_OP_U2) {   // 4x4 matrix of row p.g0 + gi, local index bit(q0) + 2 bit(q1)
-            const float2 *u = mats + 16 * (size_t)(p.g0 + gi);
+            const float2 *u = msm + 16 * gi;
             float2 m[16];
 #pragma unroll
-            for (int e = 0; e < 16; ++e) m[e] = __ldg(u + e);
+            for (int e = 0; e < 16; ++e) m[e] = u[e];
             const int b1 = 1 << G.q1;
             const int lo = G.q0 < G.q1 ? G.q0 : G.q1, hi = G.q0 < G.q1 ? G.q1 : G.q0;
             for (int pi = threadIdx.x; pi < L / 4; pi += 256) {
@@ -92,11 +105,7 @@ __global__ void __launch_bounds__(256) gate_block_kernel(float2 *psi, const Gate
         }
     }
     __syncthreads();
-    for (int l = threadIdx.x; l < L; l += 256) {
-        unsigned long long g = base;
-        for (int i = 0; i < p.Q; ++i) g |= (unsigned long long)((l >> i) & 1) << p.local[i];
-        psi[g] = amp[l];
-    }
+    for (int l = threadIdx.x; l < L; l += 256) psi[hioff[l >> low] | (unsigned long long)(l & lm)] = amp[l];
 }
 
 // blocks_host: n_blocks x (g0, ng); block_qubits_host: n_blocks x GATE_BLOCK_Q
@@ -105,12 +114,17 @@ __global__ void __launch_bounds__(256) gate_block_kernel(float2 *psi, const Gate
 cudaError_t launch_gate_blocks(float2 *psi, int N, const GateRow *gates_dev, const float2 *mats_dev,
                                const int *blocks_host, int n_blocks, const unsigned char *block_qubits_host,
                                cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
+    int max_ng = 0;
+    for (int b = 0; b < n_blocks; ++b) max_ng = blocks_host[2 * b + 1] > max_ng ? blocks_host[2 * b + 1] : max_ng;
+    const size_t mat_smem = mats_dev ? sizeof(float2) * 16 * (size_t)max_ng : 0;
+    const size_t smem_max = (sizeof(float2) << GATE_BLOCK_Q) + mat_smem;
+    if (smem_max > 200 * 1024) return cudaErrorInvalidValue;
+    static size_t attr = 0;
+    if (attr < smem_max) {
         cudaError_t e = cudaFuncSetAttribute(gate_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(sizeof(float2) << GATE_BLOCK_Q));
+                                             (int)smem_max);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr = smem_max;
     }
     for (int b = 0; b < n_blocks; ++b) {
         GateBlockParams p;
@@ -129,7 +143,8 @@ cudaError_t launch_gate_blocks(float2 *psi, int N, const GateRow *gates_dev, con
             if (!in[q]) p.other[p.n_other++] = (unsigned char)q;
         const unsigned long long tiles = 1ULL << p.n_other;
         dim3 grid((unsigned)(tiles < 32768 ? tiles : 32768), (unsigned)(tiles < 32768 ? 1 : tiles >> 15));
-        gate_block_kernel<<<grid, 256, sizeof(float2) << p.Q, st>>>(psi, gates_dev, mats_dev, p);
+        const size_t smem = (sizeof(float2) << p.Q) + (mats_dev ? sizeof(float2) * 16 * (size_t)p.ng : 0);
+        gate_block_kernel<<<grid, 256, smem, st>>>(psi, gates_dev, mats_dev, p);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -54,10 +54,11 @@ cudaError_t launch_zsample(int single, int fine, int M, const PassArgs &a, const
 // gates (k_gates.cu)
 struct GateRow { unsigned char op, q0, q1; };
 constexpr unsigned char GATE_OP_U2 = 6;   // general two-qubit gate (matrix table indexed by row)
+constexpr int GATE_BLOCK_MAX_U2 = 512;     // two-qubit matrices per block (64 KB of shared memory)
 cudaError_t launch_gate_blocks(float2 *psi, int N, const GateRow *gates_dev, const float2 *mats_dev,
                                const int *blocks_host, int n_blocks, const unsigned char *block_qubits_host,
                                cudaStream_t st);
-constexpr int GATE_BLOCK_Q = 12;   // qubits per fused gate block (2^12 amplitudes in shared memory)
+constexpr int GATE_BLOCK_Q = 13;   // qubits per fused gate block (2^13 amplitudes, 64 KB of shared memory)
 constexpr int GATE_BLOCK_LOW = 5;  // qubits 0..4 always in the block (256-byte contiguous runs)
 
 } // namespace sre

@@ -884,10 +884,15 @@ sre_status autotune_impl(const void *psi, int N, cudaStream_t st, sre_opts *best
     return SRE_OK;
 }
 
-// Runs of consecutive gates acting inside <= GATE_BLOCK_Q qubits (qubits
-// 0..GATE_BLOCK_LOW-1 always included) become one pass over psi in shared
-// memory. Rows: op, q0, q1 (global qubits; q1 used by CNOT and U2);
-// mats_host: 32 floats per row (U2 rows only; NULL when there are none).
+// Gates are grouped into blocks of at most GATE_BLOCK_Q qubits (qubits
+// 0..GATE_BLOCK_LOW-1 always included), each applied in one pass over psi in
+// shared memory. Grouping follows the circuit's dependencies, not only its
+// list order: a gate joins the current block once every earlier gate on its
+// qubits has been applied (in an earlier block or earlier in this one), the
+// cheapest such gate first (fewest qubits added, then the earliest), until no
+// ready gate fits. Gates on disjoint qubits commute, so any such order
+// applies the same unitary. Rows: op, q0, q1 (global qubits; q1 used by CNOT
+// and U2); mats_host: 32 floats per row (U2 rows only; NULL when there are none).
 sre_status run_gate_list(void *psi, int N, const std::vector<GateRow> &in_rows, const float *mats_host,
                          cudaStream_t st) {
     const long long n_gates = (long long)in_rows.size();
@@ -895,21 +900,49 @@ sre_status run_gate_list(void *psi, int N, const std::vector<GateRow> &in_rows, 
     const int low = N < GATE_BLOCK_LOW ? N : GATE_BLOCK_LOW;
     const int qmax = N < GATE_BLOCK_Q ? N : GATE_BLOCK_Q;
     auto two = [](const GateRow &G) { return G.op == SRE_GATE_CNOT || G.op == GATE_OP_U2; };
+    std::vector<std::vector<long long>> qlist(N);
+    for (long long g = 0; g < n_gates; ++g) {
+        qlist[in_rows[g].q0].push_back(g);
+        if (two(in_rows[g])) qlist[in_rows[g].q1].push_back(g);
+    }
+    std::vector<size_t> ptr(N, 0);
+    auto ready = [&](long long g) {
+        const GateRow &G = in_rows[g];
+        if (ptr[G.q0] >= qlist[G.q0].size() || qlist[G.q0][ptr[G.q0]] != g) return false;
+        return !two(G) || (ptr[G.q1] < qlist[G.q1].size() && qlist[G.q1][ptr[G.q1]] == g);
+    };
     std::vector<int> blocks;
     std::vector<unsigned char> bq;
-    std::vector<GateRow> rows(n_gates);
-    long long g0 = 0;
-    while (g0 < n_gates) {
+    std::vector<GateRow> rows;
+    std::vector<float> mats;
+    rows.reserve(n_gates);
+    if (mats_host) mats.reserve(32 * (size_t)n_gates);
+    long long ndone = 0;
+    while (ndone < n_gates) {
         bool in[64] = {false};
         int cnt = 0;
         for (int q = 0; q < low; ++q) { in[q] = true; ++cnt; }
-        long long g = g0;
-        for (; g < n_gates; ++g) {
-            const GateRow &G = in_rows[g];
-            const int add = (!in[G.q0]) + (two(G) && !in[G.q1] && G.q1 != G.q0 ? 1 : 0);
-            if (cnt + add > qmax) break;
+        std::vector<long long> blk;
+        for (;;) {
+            if (mats_host && (int)blk.size() >= GATE_BLOCK_MAX_U2) break;
+            long long best = -1;
+            int best_new = 3;
+            for (int q = 0; q < N; ++q) {
+                if (ptr[q] >= qlist[q].size()) continue;
+                const long long g = qlist[q][ptr[q]];
+                if (!ready(g)) continue;
+                const GateRow &G = in_rows[g];
+                const int add = (!in[G.q0]) + (two(G) && !in[G.q1] ? 1 : 0);
+                if (cnt + add > qmax) continue;
+                if (add < best_new || (add == best_new && g < best)) { best = g; best_new = add; }
+            }
+            if (best < 0) break;
+            const GateRow &G = in_rows[best];
             if (!in[G.q0]) { in[G.q0] = true; ++cnt; }
             if (two(G) && !in[G.q1]) { in[G.q1] = true; ++cnt; }
+            ++ptr[G.q0];
+            if (two(G)) ++ptr[G.q1];
+            blk.push_back(best);
         }
         unsigned char loc[64];
         unsigned char list[GATE_BLOCK_Q];
@@ -917,15 +950,19 @@ sre_status run_gate_list(void *psi, int N, const std::vector<GateRow> &in_rows, 
         for (int q = 0; q < N; ++q)
             if (in[q]) { loc[q] = (unsigned char)m; list[m++] = (unsigned char)q; }
         for (int i = m; i < GATE_BLOCK_Q; ++i) list[i] = 255;
-        for (long long k = g0; k < g; ++k) {
-            rows[k].op = in_rows[k].op;
-            rows[k].q0 = loc[in_rows[k].q0];
-            rows[k].q1 = two(in_rows[k]) ? loc[in_rows[k].q1] : 0;
+        blocks.push_back((int)rows.size());
+        blocks.push_back((int)blk.size());
+        for (long long g : blk) {
+            GateRow r;
+            r.op = in_rows[g].op;
+            r.q0 = loc[in_rows[g].q0];
+            r.q1 = two(in_rows[g]) ? loc[in_rows[g].q1] : 0;
+            rows.push_back(r);
+            if (mats_host) mats.insert(mats.end(), mats_host + 32 * g, mats_host + 32 * (g + 1));
         }
-        blocks.push_back((int)g0);
-        blocks.push_back((int)(g - g0));
         bq.insert(bq.end(), list, list + GATE_BLOCK_Q);
-        g0 = g;
+        ndone += (long long)blk.size();
+        if (blk.empty()) return fail(SRE_EINVAL, "gate planner made no progress");
     }
     int dev = 0;
     CK(cudaGetDevice(&dev));
@@ -950,7 +987,7 @@ sre_status run_gate_list(void *psi, int N, const std::vector<GateRow> &in_rows, 
     }
     CK(cudaMemcpyAsync(dg, rows.data(), sizeof(GateRow) * (size_t)n_gates, cudaMemcpyHostToDevice, st));
     if (mats_host)
-        CK(cudaMemcpyAsync(dm, mats_host, sizeof(float2) * 16 * (size_t)n_gates, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(dm, mats.data(), sizeof(float2) * 16 * (size_t)n_gates, cudaMemcpyHostToDevice, st));
     CK(launch_gate_blocks((float2 *)psi, N, dg, dm, blocks.data(), (int)(blocks.size() / 2), bq.data(), st));
     count_launches(blocks.size() / 2);
     CK(cudaStreamSynchronize(st));

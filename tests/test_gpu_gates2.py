@@ -65,3 +65,17 @@ def test_brickwall_preconditioner_r2(sre):
     after = sre.sre_exact(x, allow_nullity_error=True)
     assert abs(after["M"][1] - (N // 2) * np.log2(4 / 3)) < 1e-4
     assert before["r2"] > 20.0 and after["r2"] < 2.0
+
+
+def test_many_two_qubit_gates_on_few_qubits(sre):
+    """More two-qubit gates than one pass holds matrices for (N = 6: every
+    gate fits one 13-qubit block, so the planner splits the list by count)."""
+    N = 6
+    g = np.random.default_rng(66)
+    m = np.stack([inputs.haar_two_qubit(g) for _ in range(1300)]).astype(np.complex64)
+    p = np.asarray([tuple(int(v) for v in g.choice(N, 2, replace=False)) for _ in range(1300)], np.int32)
+    psi = inputs.haar_state(N, 6)
+    x = dev(psi)
+    sre.apply_two_qubit_gates(x, m, p)
+    ref = oracle.apply_two_qubit(psi, m, p)
+    assert np.max(np.abs(x.cpu().numpy() - ref)) < 2e-4
