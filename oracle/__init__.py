@@ -88,6 +88,12 @@ def lib():
             L.or_fluctuation_ratio.argtypes = [_c_fp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
             L.or_apply_two_qubit.argtypes = [_c_dp, ctypes.c_int, _c_dp, ctypes.c_void_p, ctypes.c_longlong]
             L.or_apply_two_qubit.restype = ctypes.c_int
+            L.or_sre_mixed.argtypes = [_c_fp, ctypes.c_int, ctypes.c_int, _c_dp, _c_dp,
+                                       ctypes.POINTER(ctypes.c_double)]
+            L.or_sre_mixed.restype = ctypes.c_int
+            L.or_sre_mixed_bruteforce.argtypes = [_c_fp, ctypes.c_int, ctypes.c_int, _c_dp, _c_dp,
+                                                  ctypes.POINTER(ctypes.c_double)]
+            L.or_sre_mixed_bruteforce.restype = None
             L.or_fluctuation_ratio.restype = ctypes.c_int
             L.or_clifford_conjugate.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_uint64,
                                                 ctypes.c_uint64, _c_u64p, _c_u64p, ctypes.POINTER(ctypes.c_int)]
@@ -219,6 +225,26 @@ def apply_two_qubit(psi, mats, pairs) -> np.ndarray:
     if rc != 0:
         raise ValueError("bad qubit pair")
     return v
+
+
+def sre_mixed(psi, NA: int, route: str = "partial") -> dict:
+    """SRE of the reduced state on the first NA qubits (SM, mixed states):
+    {"W": sums over P_A of c^2, c^4, c^6, c^2 log2 c^2, "S2": S_2(rho_A),
+    "M": [M_1 (NaN unless rho_A is pure), M_2, M_3]}. route "partial": the
+    SM's partial sums + one NA-bit transform per x_A; "bruteforce": every
+    P in P_A by its direct correlator."""
+    a = _psi(psi)
+    N = _nq(a)
+    if not 1 <= NA <= N:
+        raise ValueError("NA outside 1..N")
+    W, M = np.zeros(4), np.zeros(3)
+    S2 = ctypes.c_double(0.0)
+    if route == "partial":
+        if lib().or_sre_mixed(_fp(a), N, NA, _dp(W), _dp(M), ctypes.byref(S2)) != 0:
+            raise MemoryError("oracle allocation failed")
+    else:
+        lib().or_sre_mixed_bruteforce(_fp(a), N, NA, _dp(W), _dp(M), ctypes.byref(S2))
+    return {"W": W, "S2": S2.value, "M": M}
 
 
 def fluctuation_ratio(psi) -> float:

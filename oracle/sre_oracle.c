@@ -16,6 +16,7 @@
  *   - the MC estimator with x = 0 forced                      (SM Sec. I)
  *   - the fluctuation ratio r_2 of the per-family sums        (SM, Clifford preconditioning)
  *   - dense two-qubit gates of brick-wall circuits            (SM, brick-wall circuits)
+ *   - the SRE of a reduced state rho_A                        (SM, mixed states, Eq. Msre-mixed)
  *   - the x-marginal p(x) and the sampling of (x, z) ~ c^2/d  (SM Sec. III target pi(P))
  *   - H, S, S^dag, CNOT, T, T^dag gates on a state vector     (Clifford preconditioning, T doping)
  *   - Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11)
@@ -283,6 +284,79 @@ int or_apply_two_qubit(double *psi_c128, int N, const double *mats, const int *p
             for (int l = 0; l < 4; ++l) psi[idx[l]] = o[l];
         }
     }
+    return 0;
+}
+
+/* Mixed-state SRE (SM, "Stabilizer Renyi entropy of mixed states"): rho_A is
+ * the reduced state of the first N_A qubits, the low bits a of b = a + 2^{N_A} e.
+ * From the sums over the 4^{N_A} Pauli strings supported on A,
+ * W = [sum c^2, sum c^4, sum c^6, sum c^2 log2 c^2], c_P = Tr(rho_A P):
+ *   S_2 = -log2(W_0 / d_A)                                   (SM, S_2 of rho_A)
+ *   M_alpha = log2(W_{alpha-1} / d_A^alpha) / (1 - alpha) - N_A - S_2,
+ *             alpha = 2, 3                                     (Eq. Msre-mixed)
+ * Reading: for alpha = 1 the equation has a finite value only for a pure
+ * rho_A (its log argument tends to 2^{-S_2}); M[0] is then the Shannon limit
+ * -W_3 / d_A of the pure case, and NaN when |S_2| > 1e-9. */
+static void mixed_finalize(const double W[4], int NA, double M[3], double *S2) {
+    double dA = ldexp(1.0, NA);
+    *S2 = -log2(W[0] / dA);
+    M[1] = -log2(W[1] / (dA * dA)) - NA - *S2;
+    M[2] = -0.5 * log2(W[2] / (dA * dA * dA)) - NA - *S2;
+    M[0] = fabs(*S2) <= 1e-9 ? -W[3] / dA : NAN;
+}
+
+/* The definition: every P in P_A by the direct O(d) correlator. Out: W[4],
+ * M[3], S2. O(4^{N_A} 2^N); small sizes only. */
+void or_sre_mixed_bruteforce(const float *psi, int N, int NA, double W[4], double M[3], double *S2) {
+    uint64_t dA = 1ULL << NA;
+    ksum k[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (uint64_t x = 0; x < dA; ++x)
+        for (uint64_t z = 0; z < dA; ++z) {
+            double c = or_pauli_expectation(psi, N, x, z, NULL);
+            double c2 = c * c;
+            kadd(&k[0], c2);
+            kadd(&k[1], c2 * c2);
+            kadd(&k[2], c2 * c2 * c2);
+            if (c2 > 0.0) kadd(&k[3], c2 * log2(c2));
+        }
+    for (int i = 0; i < 4; ++i) W[i] = kval(&k[i]);
+    mixed_finalize(W, NA, M, S2);
+}
+
+/* The SM's route: h_{x_A}(a) = sum_e conj(psi(a ^ x_A, e)) psi(a, e) (the
+ * conjugation order of Eq. Pxz-corr), one N_A-bit Walsh-Hadamard transform
+ * per x_A, then the phase i^{popcount(x_A & z_A)} and s = 1/sum|psi|^2.
+ * O(2^{N + N_A}). Out as or_sre_mixed_bruteforce. Returns 0, or -1 on
+ * allocation failure. */
+int or_sre_mixed(const float *psi, int N, int NA, double W[4], double M[3], double *S2) {
+    uint64_t dA = 1ULL << NA, dB = 1ULL << (N - NA);
+    double s = 1.0 / or_norm2(psi, N);
+    cplx *h = (cplx *)malloc(dA * sizeof(cplx));
+    if (!h) return -1;
+    ksum k[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (uint64_t x = 0; x < dA; ++x) {
+        for (uint64_t a = 0; a < dA; ++a) {
+            ksum hr = {0, 0}, hi = {0, 0};
+            for (uint64_t e = 0; e < dB; ++e) {
+                cplx t = conj(amp(psi, (a ^ x) + dA * e)) * amp(psi, a + dA * e);
+                kadd(&hr, creal(t));
+                kadd(&hi, cimag(t));
+            }
+            h[a] = kval(&hr) + I * kval(&hi);
+        }
+        fwht_complex(h, NA);
+        for (uint64_t z = 0; z < dA; ++z) {
+            double c = creal(s * ipow(popc(x & z)) * h[z]);
+            double c2 = c * c;
+            kadd(&k[0], c2);
+            kadd(&k[1], c2 * c2);
+            kadd(&k[2], c2 * c2 * c2);
+            if (c2 > 0.0) kadd(&k[3], c2 * log2(c2));
+        }
+    }
+    free(h);
+    for (int i = 0; i < 4; ++i) W[i] = kval(&k[i]);
+    mixed_finalize(W, NA, M, S2);
     return 0;
 }
 

@@ -575,3 +575,63 @@ def test_brickwall_clifford_preserves_sre_and_haar_norm():
     mh, ph = inputs.brickwall_circuit(N, 5, "haar", 6)
     out = oracle.apply_two_qubit(inputs.haar_state(N, 2), mh, ph)
     assert abs(np.vdot(out, out).real - 1.0) < 1e-6
+
+
+# ---------------------------------------------------- mixed-state SRE (SM)
+@pytest.mark.parametrize("N,NA", [(3, 1), (4, 2), (5, 3), (6, 5), (5, 5), (7, 2)])
+def test_mixed_route_equals_definition(N, NA):
+    psi = inputs.unnormalised_gaussian_state(N, 70 + N + NA)
+    a = oracle.sre_mixed(psi, NA, "partial")
+    b = oracle.sre_mixed(psi, NA, "bruteforce")
+    assert np.allclose(a["W"], b["W"], rtol=1e-12, atol=1e-14)
+    assert abs(a["S2"] - b["S2"]) < 1e-12
+
+
+@pytest.mark.parametrize("N", [3, 6, 8])
+def test_mixed_full_subsystem_is_the_pure_sre(N):
+    psi = inputs.haar_state(N, 80 + N)
+    m = oracle.sre_mixed(psi, N)
+    p = oracle.sre_exact(psi)
+    assert abs(m["S2"]) < 1e-12
+    assert np.allclose(m["M"], p["M"], atol=1e-10)
+
+
+@pytest.mark.parametrize("NA,NB", [(1, 3), (3, 2), (4, 4)])
+def test_mixed_product_state_is_pure_on_a(NA, NB):
+    """|T>^{NA} (x) (Haar on B): rho_A = |T><T|^{NA}, S_2 = 0, M_2 =
+    NA log2(4/3), M_3 = NA (1/2) log2(8/5) (one |T>: sum_P c^6 = 1 + 2/8)."""
+    t = inputs.t_product_state(NA, NA).astype(np.complex128)
+    b = inputs.haar_state(NB, 90 + NB).astype(np.complex128)
+    psi = np.kron(b, t)                            # A = the low NA qubits
+    m = oracle.sre_mixed(psi, NA)
+    assert abs(m["S2"]) < 1e-9
+    assert abs(m["M"][1] - NA * math.log2(4 / 3)) < 1e-9
+    assert abs(m["M"][2] - NA * 0.5 * math.log2(8 / 5)) < 1e-9
+
+
+@pytest.mark.parametrize("NA", [1, 2, 4])
+def test_mixed_bell_pairs_maximally_mixed(NA):
+    """Qubit i of A in |Phi+> with qubit NA + i of B: rho_A = I / d_A, so only
+    the identity has c != 0: S_2 = N_A, and Eq. Msre-mixed (which subtracts
+    S_2 for every alpha) gives M_alpha = N_A (2 - alpha)/(alpha - 1): M_2 = 0,
+    M_3 = -N_A / 2."""
+    N = 2 * NA
+    psi = np.zeros(1 << N, dtype=np.complex128)
+    for a in range(1 << NA):
+        psi[a | (a << NA)] = 1.0
+    psi /= np.linalg.norm(psi)
+    m = oracle.sre_mixed(psi, NA)
+    assert abs(m["S2"] - NA) < 1e-12
+    assert abs(m["M"][1]) < 1e-12 and abs(m["M"][2] + NA / 2) < 1e-12
+    assert np.allclose(m["W"][:3], 1.0) and math.isnan(m["M"][0])
+
+
+def test_mixed_ghz_two_component_mixture():
+    """GHZ on 6 qubits, A = 3 qubits: rho_A = (|000><000| + |111><111|)/2;
+    the even-weight Z strings have c = 1, all else 0: S_2 = 1, M_2 = 0 and
+    M_3 = -log2(4 / 8^3) / 2 - 3 - 1 = -1/2."""
+    psi = np.zeros(64, dtype=np.complex128)
+    psi[0] = psi[63] = 1 / math.sqrt(2)
+    m = oracle.sre_mixed(psi, 3)
+    assert abs(m["S2"] - 1.0) < 1e-12 and abs(m["M"][1]) < 1e-12 and abs(m["M"][2] + 0.5) < 1e-12
+    assert np.allclose(m["W"][:3], 4.0)
