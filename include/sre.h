@@ -226,6 +226,31 @@ SRE_API sre_status stabilizer_nullity(const void *psi_c64_dev, int N, double eps
 SRE_API sre_status apply_clifford_tdoped_circuit(void *psi_c64_dev, int N, const sre_gate *gates_host,
                                          long long n_gates, void *stream);
 
+/* Stabilizer Renyi entropy of a reduced state (Supplemental Material,
+ * "Stabilizer Renyi entropy of mixed states", Eq. Msre-mixed). */
+typedef struct {
+    double M[3];        /* M_alpha(rho_A), alpha = 1, 2, 3, as printed (S_2 subtracted for every
+                           alpha); M_1 only for a pure rho_A (Shannon limit -W[3]/d_A), else NaN */
+    double S2;          /* second Renyi entropy of rho_A, -log2(W[0] / d_A) */
+    double W[4];        /* over the 4^{N_A} Pauli strings supported on A: sum c^2, c^4, c^6, c^2 log2 c^2 */
+    double err_M[3];    /* a-priori bound on |dM| from FP32 rounding */
+    int N_A;
+} sre_mixed_result;
+
+/* Workspace bytes of sre_mixed (dominated by the d_A x d_A Gram matrix, 8 d_A^2 bytes). */
+SRE_API sre_status sre_mixed_workspace_bytes(int N, int N_A, size_t *bytes);
+
+/* SRE of rho_A, the reduced state of the first N_A qubits (the low N_A bits of
+ * the basis index, b = a + 2^{N_A} e) of psi: c_P = Tr(rho_A P) for the
+ * 4^{N_A} Pauli strings on A. The family x_A needs h(a) = sum_e
+ * conj(psi(a ^ x_A, e)) psi(a, e), an entry of the Gram matrix C = Psi Psi^H
+ * of psi viewed as a d_A x d_B matrix (computed by cuBLAS CHERK, FP32), then
+ * one N_A-bit transform per x_A with the moments fused (O(2^{N+N_A}) overall).
+ * N in 1..30, N_A in 1..min(N, 15). workspace: >= sre_mixed_workspace_bytes,
+ * 256-byte aligned, or NULL (library-owned). out: host. Synchronises the stream. */
+SRE_API sre_status sre_mixed(const void *psi_c64_dev, int N, int N_A, void *workspace, size_t workspace_bytes,
+                             void *stream, sre_mixed_result *out);
+
 /* Apply general two-qubit gates in order, in place, to psi: the random
  * brick-wall circuits of the Supplemental Material (Haar-random two-qubit
  * gates; uniformly random two-qubit Cliffords as the preconditioner C of the

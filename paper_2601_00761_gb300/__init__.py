@@ -60,6 +60,11 @@ class Result(ctypes.Structure):
                 "n_families": self.n_families, "n_samples": self.n_samples, "r2": self.r2}
 
 
+class MixedResult(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_double * 3), ("S2", ctypes.c_double), ("W", ctypes.c_double * 4),
+                ("err_M", ctypes.c_double * 3), ("N_A", ctypes.c_int)]
+
+
 class Plan(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("n_bits", ctypes.c_int), ("n_passes", ctypes.c_int),
                 ("pass_lo", ctypes.c_int * 4), ("pass_bits", ctypes.c_int * 4), ("x_batch", ctypes.c_int),
@@ -109,6 +114,8 @@ def load():
                                 ctypes.POINTER(ctypes.c_longlong), _vp], st),
         "apply_clifford_tdoped_circuit": ([_vp, ctypes.c_int, _vp, ctypes.c_longlong, _vp], st),
         "apply_two_qubit_gates": ([_vp, ctypes.c_int, _vp, _vp, ctypes.c_longlong, _vp], st),
+        "sre_mixed_workspace_bytes": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)], st),
+        "sre_mixed": ([_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(MixedResult)], st),
         "sre_family_spectrum": ([_vp, ctypes.c_int, ctypes.c_ulonglong, ctypes.POINTER(Opts), _vp, _vp], st),
         "sre_family_spectrum_f64": ([_vp, ctypes.c_int, ctypes.c_ulonglong, _vp, _vp], st),
         "sre_philox_blocks": ([_vp, _vp, ctypes.c_int, _vp], st),
@@ -301,6 +308,22 @@ def apply_clifford_tdoped_circuit(psi, gates) -> None:
     p, N = _psi_ptr(psi)
     g = np.ascontiguousarray(np.asarray(gates, dtype=np.uint8).reshape(-1, 3))
     _check(load().apply_clifford_tdoped_circuit(p, N, g.ctypes.data_as(ctypes.c_void_p), g.shape[0], _stream()))
+
+
+def sre_mixed_workspace_bytes(N: int, N_A: int) -> int:
+    b = ctypes.c_size_t(0)
+    _check(load().sre_mixed_workspace_bytes(N, N_A, ctypes.byref(b)))
+    return b.value
+
+
+def sre_mixed(psi, N_A: int, workspace=None) -> dict:
+    """SRE of the reduced state on the first N_A qubits (SM, mixed states):
+    {"M": [M_1 (NaN unless rho_A is pure), M_2, M_3], "S2", "W", "err_M"}."""
+    p, N = _psi_ptr(psi)
+    r = MixedResult()
+    ws, wb = _workspace(workspace)
+    _check(load().sre_mixed(p, N, N_A, ws, wb, _stream(), ctypes.byref(r)))
+    return {"M": list(r.M), "S2": r.S2, "W": list(r.W), "err_M": list(r.err_M), "N_A": r.N_A}
 
 
 def apply_two_qubit_gates(psi, mats, pairs) -> None:

@@ -4,6 +4,7 @@
 //   prologue  SRC_PSI_FAMILY : h(b') = conj(psi[b^x]) psi[b], b = b' with 0 at bit j
 //             SRC_PSI_Q      : h(g)  = (|psi[g]|^2, |psi[g + d/2]|^2)  (x = 0 family / marginal)
 //             SRC_BUF        : the previous pass's output
+//             SRC_GRAM       : h(a) = C[a][a ^ x] of a reduced state (C = Psi Psi^H)
 //   epilogue  DST_BUF        : store for the next pass
 //             DST_MOMENTS    : fused reduction of Algorithm 1 (sum c^2, c^4, c^6,
 //                              c^2 log2 c^2, FP32 nullity candidates, z-range weights)
@@ -190,6 +191,37 @@ __device__ __forceinline__ void pass_prologue(typename Cfg::C2 (&v)[Cfg::E], con
                     v[k0 + q].x = fma(ux, ux, uy * uy);
                     v[k0 + q].y = fma(wx, wx, wy * wy);
                 }
+            }
+        }
+    } else if constexpr (SRC == SRC_GRAM) {
+        // h(a) = sum_e conj(psi(a ^ x, e)) psi(a, e) = C[a][a ^ x]; the lower
+        // triangle is the conjugate of the stored upper one. x = 0: the
+        // diagonal pair (C[g][g], C[g + d/2][g + d/2]).
+        const float2 *C = a.gram;
+        const unsigned long long ld = (unsigned long long)a.gram_ld;
+        if (x != 0) {
+            const uint32_t hm = ~((1u << j) - 1u), x32 = (uint32_t)x;
+#pragma unroll
+            for (int k = 0; k < Cfg::E; ++k) {
+                const uint32_t g = slot_gidx<Cfg, A0>(base, rs, k);
+                const uint32_t r = g + (g & hm), c = r ^ x32;
+                if (r <= c) {
+                    const float2 h = __ldg(C + r + ld * c);
+                    v[k].x = h.x;
+                    v[k].y = h.y;
+                } else {
+                    const float2 h = __ldg(C + c + ld * r);
+                    v[k].x = h.x;
+                    v[k].y = -h.y;
+                }
+            }
+        } else {
+            const uint32_t h32 = (uint32_t)half;
+#pragma unroll
+            for (int k = 0; k < Cfg::E; ++k) {
+                const uint32_t g = slot_gidx<Cfg, A0>(base, rs, k), gh = g | h32;
+                v[k].x = __ldg(C + g + ld * g).x;
+                v[k].y = __ldg(C + gh + ld * gh).x;
             }
         }
     } else if constexpr (SRC == SRC_PSI_Q) {

@@ -16,6 +16,8 @@ struct AllowedK { static constexpr bool value = false; };
 
 SRE_ALLOW(float, KIND_SINGLE, SRC_PSI_FAMILY, DST_MOMENTS)
 SRE_ALLOW(float, KIND_SINGLE, SRC_PSI_FAMILY, DST_SPECTRUM)
+SRE_ALLOW(float, KIND_SINGLE, SRC_GRAM, DST_MOMENTS)
+SRE_ALLOW(float, KIND_SINGLE, SRC_GRAM, DST_SPECTRUM)
 SRE_ALLOW(float, KIND_STRIDED, SRC_PSI_FAMILY, DST_BUF)
 SRE_ALLOW(float, KIND_STRIDED, SRC_BUF, DST_BUF)
 SRE_ALLOW(float, KIND_ROW, SRC_BUF, DST_MOMENTS)
@@ -70,6 +72,7 @@ cudaError_t launch_sd(int src, int dst, const PassArgs &a, int tiles, cudaStream
     case SRC_PSI_FAMILY: SRE_D(SRC_PSI_FAMILY)
     case SRC_PSI_Q: SRE_D(SRC_PSI_Q)
     case SRC_BUF: SRE_D(SRC_BUF)
+    case SRC_GRAM: SRE_D(SRC_GRAM)
     default: return cudaErrorInvalidValue;
     }
 #undef SRE_D

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdlib>
+#include <cublas_v2.h>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -994,6 +995,108 @@ sre_status run_gate_list(void *psi, int N, const std::vector<GateRow> &in_rows, 
     return SRE_OK;
 }
 
+// ------------------------------------------------------ mixed states
+struct MixedWS {
+    double *scal, *npart, *epart, *etot;
+    float2 *C;
+    TilePartial *tiles;
+    FamMoments *fm;
+};
+
+void layout_mixed(Arena &A, int NA, MixedWS &w) {
+    const unsigned long long dA = 1ULL << NA;
+    w.scal = A.take<double>(SCAL_N);
+    w.npart = A.take<double>(NORM_BLOCKS);
+    w.epart = A.take<double>(6 * EXACT_PARTS);
+    w.etot = A.take<double>(8);
+    w.C = A.take<float2>(dA * dA);
+    w.tiles = A.take<TilePartial>(dA);
+    w.fm = A.take<FamMoments>(dA);
+}
+
+std::mutex g_blas_mu;
+std::vector<cublasHandle_t> g_blas;
+
+sre_status blas_handle(cublasHandle_t *h) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_blas_mu);
+    if ((int)g_blas.size() <= dev) g_blas.resize(dev + 1, nullptr);
+    if (!g_blas[dev]) {
+        cublasHandle_t nh = nullptr;
+        if (cublasCreate(&nh) != CUBLAS_STATUS_SUCCESS) return fail(SRE_ECUDA, "cublasCreate failed");
+        g_blas[dev] = nh;
+    }
+    *h = g_blas[dev];
+    return SRE_OK;
+}
+
+// SRE of the reduced state on the first N_A qubits (SM, mixed states):
+// C = Psi Psi^H by cuBLAS CHERK (Psi = psi viewed column-major d_A x d_B), then
+// every family x_A of the N_A-qubit system through the single-pass transform
+// with the h(a) = C[a][a ^ x_A] prologue and the fused moments, then the
+// fixed-order FP64 totals; Eq. Msre-mixed on the host.
+sre_status mixed_impl(const void *psi, int N, int NA, void *ws, size_t ws_bytes, cudaStream_t st,
+                      sre_mixed_result *out) {
+    Arena dry(nullptr);
+    MixedWS w;
+    layout_mixed(dry, NA, w);
+    void *base = nullptr;
+    CS(resolve_workspace(ws, ws_bytes, dry.off, &base));
+    Arena A(base);
+    layout_mixed(A, NA, w);
+    const unsigned long long dA = 1ULL << NA, dB = 1ULL << (N - NA);
+    CK(launch_norm2((const float2 *)psi, N, w.scal, w.npart, st));
+    count_launches(2);
+    cublasHandle_t h = nullptr;
+    CS(blas_handle(&h));
+    if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) return fail(SRE_ECUDA, "cublasSetStream failed");
+    const float one = 1.0f, zero = 0.0f;
+    if (cublasCherk(h, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, (int)dA, (int)dB, &one, (const cuComplex *)psi,
+                    (int)dA, &zero, (cuComplex *)w.C, (int)dA) != CUBLAS_STATUS_SUCCESS)
+        return fail(SRE_ECUDA, "cublasCherk failed (N=%d, N_A=%d)", N, NA);
+    PassArgs a;
+    memset(&a, 0, sizeof a);
+    a.N = NA;
+    a.n = NA - 1;
+    a.slot_elems = 1LL << (NA - 1);
+    a.range_log2 = NA - 1;
+    a.s_ptr = w.scal + SCAL_S;
+    a.tile_out = w.tiles;
+    a.cand_thr = 1.0f;
+    a.gram = w.C;
+    a.gram_ld = (long long)dA;
+    a.fam_base = 0;
+    a.n_fam = (long long)dA;
+    cudaError_t e = launch_f32_single(NA - 1, SRC_GRAM, DST_MOMENTS, a, st);
+    if (e != cudaSuccess) return fail(SRE_ECUDA, "mixed-state transform (N_A=%d): %s", NA, cudaGetErrorString(e));
+    count_launches(1);
+    CK(launch_fam_reduce(w.tiles, (long long)dA, 1, nullptr, 0, NA, NA - 1, NA - 1, w.fm, 0, nullptr, 0, st));
+    count_launches(1);
+    unsigned long long *no_flags = nullptr;
+    CK(launch_exact_totals(w.fm, (long long)dA, w.epart, EXACT_PARTS, w.etot, no_flags, nullptr, st));
+    count_launches(2);
+    double T[TOT_N + 1];
+    CK(cudaMemcpyAsync(T, w.etot, TOT_N * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(T + TOT_N, w.scal + SCAL_NORM2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (!(T[TOT_N] > 0.0)) return fail(SRE_EZERO, "psi has zero norm");
+    memset(out, 0, sizeof *out);
+    const double da = (double)dA;
+    for (int i = 0; i < 4; ++i) out->W[i] = T[i];
+    out->S2 = -std::log2(T[0] / da);
+    out->M[1] = -std::log2(T[1] / (da * da)) - NA - out->S2;
+    out->M[2] = -0.5 * std::log2(T[2] / (da * da * da)) - NA - out->S2;
+    // a-priori FP32 rounding estimate, as for the pure sweep over N_A + log2 d_B sums
+    const double ec = (N + 2) * std::ldexp(1.0, -24);
+    out->M[0] = std::fabs(out->S2) <= 64.0 * ec ? -T[3] / da : std::nan("");
+    out->err_M[0] = 2.0 * ec * (N + 2);
+    out->err_M[1] = 4.0 * ec / std::log(2.0) + 2.0 * ec / std::log(2.0);
+    out->err_M[2] = 6.0 * ec / (2.0 * std::log(2.0)) + 2.0 * ec / std::log(2.0);
+    out->N_A = NA;
+    return SRE_OK;
+}
+
 } // namespace
 
 namespace sre {
@@ -1388,6 +1491,30 @@ sre_status apply_two_qubit_gates(void *psi, int N, const float *mats, const int 
         rows[g].q1 = (unsigned char)q1;
     }
     return run_gate_list(psi, N, rows, mats, (cudaStream_t)stream);
+}
+
+sre_status sre_mixed_workspace_bytes(int N, int N_A, size_t *bytes) {
+    if (N < 1 || N > 30) return fail(SRE_EINVAL, "N=%d outside 1..30", N);
+    if (N_A < 1 || N_A > N || N_A > 15) return fail(SRE_EINVAL, "N_A=%d outside 1..min(N, 15)", N_A);
+    if (!bytes) return fail(SRE_EINVAL, "bytes is NULL");
+    Arena dry(nullptr);
+    MixedWS w;
+    layout_mixed(dry, N_A, w);
+    *bytes = dry.off;
+    return SRE_OK;
+}
+
+sre_status sre_mixed(const void *psi, int N, int N_A, void *workspace, size_t workspace_bytes, void *stream,
+                     sre_mixed_result *out) {
+    CS(check_psi(psi, N, 1, 30));
+    if (N_A < 1 || N_A > N || N_A > 15) return fail(SRE_EINVAL, "N_A=%d outside 1..min(N, 15)", N_A);
+    if (!out) return fail(SRE_EINVAL, "out is NULL");
+    size_t need = 0;
+    CS(sre_mixed_workspace_bytes(N, N_A, &need));
+    void *ws = workspace;
+    if (!ws) CS(own_workspace(need, &ws));
+    else if (workspace_bytes < need) return fail(SRE_EINVAL, "workspace of %zu bytes, %zu needed", workspace_bytes, need);
+    return mixed_impl(psi, N, N_A, ws, need, (cudaStream_t)stream, out);
 }
 
 unsigned long long sre_kernel_launches(void) { return g_launches.load(); }

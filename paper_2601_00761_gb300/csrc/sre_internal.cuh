@@ -190,7 +190,7 @@ __device__ __forceinline__ void tile_transform(typename Cfg::C2 (&v)[Cfg::E], ty
 constexpr int ZR_FINE = 10;
 
 // ------------------------------------------------------------- pass args
-enum SrcMode { SRC_PSI_FAMILY = 0, SRC_PSI_Q = 1, SRC_BUF = 2 };
+enum SrcMode { SRC_PSI_FAMILY = 0, SRC_PSI_Q = 1, SRC_BUF = 2, SRC_GRAM = 3 };
 enum DstMode {
     DST_BUF = 0,        // store the partially transformed tile
     DST_MOMENTS = 1,    // family epilogue: moments, candidates, z-range weights
@@ -225,6 +225,11 @@ struct PassArgs {
     // weight of every 2^ZR_FINE-z range, one row of rw_stride floats per slot
     float *rw_out;
     long long rw_stride;
+    // SRC_GRAM (reduced state of the low N qubits of a larger state): the
+    // upper triangle of C = Psi Psi^H, column-major with leading dimension
+    // gram_ld, C[r][c] = sum_e psi(r, e) conj(psi(c, e))
+    const float2 *gram;
+    long long gram_ld;
     // Several states of the same N in one launch: the family index F (from xs
     // or fam_base + slot) is (state << N) | x; psi and s come from these
     // per-state device arrays. NULL for the one-state entry points.

@@ -124,7 +124,18 @@ def test_argument_errors_do_not_touch_the_gpu(L):
     assert L.pauli_x_marginal(_fake_ptr(0x1000), 4, None, None, 0, None) == sre.SRE_EINVAL
     p = sre.Plan()
     assert L.sre_make_plan(33, None, ctypes.byref(p)) == sre.SRE_EINVAL
+    mr = sre.MixedResult()
+    for N, NA in ((8, 0), (8, 9), (20, 16), (31, 4)):
+        assert L.sre_mixed(_fake_ptr(0x1000), N, NA, None, 0, None, ctypes.byref(mr)) == sre.SRE_EINVAL
+    assert L.sre_mixed(_fake_ptr(0x1000), 8, 4, _fake_ptr(0x1000), 16, None, ctypes.byref(mr)) == sre.SRE_EINVAL
+    assert "workspace" in sre.sre_last_error()
     assert L.sre_workspace_bytes(10, 5, 10, 1, None, ctypes.byref(ctypes.c_size_t())) == sre.SRE_EINVAL
+
+
+def test_mixed_workspace_bytes(L):
+    # dominated by the d_A x d_A complex64 Gram matrix
+    assert sre.sre_mixed_workspace_bytes(20, 10) > 8 * 4 ** 10
+    assert sre.sre_mixed_workspace_bytes(20, 10) < 8 * 4 ** 10 + (1 << 20)
 
 
 def test_structs_match_header_layout():
