@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tc", action="store_true")
-    ap.add_argument("--workload", default="mc24", choices=["mc24", "batched", "precondition"],
+    ap.add_argument("--workload", default="mc24", choices=["mc24", "batched", "precondition", "mixed"],
                     help="mc24: the headline N=24 MC step; batched: exact M_2/nullity of 4096 T-doped states "
                          "with N ~ U{8..16} in one sre_exact_batched call, against a per-state loop")
     ap.add_argument("--count", type=int, default=4096)
@@ -497,6 +497,57 @@ def run_precondition(a):
     return 0
 
 
+def run_mixed(a):
+    """SRE of the reduced state of the first N_A = N/2 qubits of an N-qubit
+    Haar state (SM, mixed states): one step = one sre_mixed call (Gram matrix
+    by CHERK, 2^{N_A} family transforms with fused moments, totals)."""
+    import torch
+    from paper_2601_00761_gb300 import build as sre_build
+    sre_build.build()
+    import paper_2601_00761_gb300 as sre
+    from paper_2601_00761_gb300 import inputs
+    torch.cuda.set_device(0)
+    N = a.N
+    NA = N // 2
+    psi = torch.from_numpy(inputs.haar_state(N, N)).cuda()
+    ws = torch.empty(sre.sre_mixed_workspace_bytes(N, NA), dtype=torch.uint8, device="cuda")
+    for _ in range(a.warmup):
+        r = sre.sre_mixed(psi, NA, workspace=ws)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    l0 = sre.sre_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    e0.record(stream)
+    for _ in range(a.steps):
+        r = sre.sre_mixed(psi, NA, workspace=ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / a.steps
+    launches = sre.sre_kernel_launches() - l0
+    dA, dB = 2 ** NA, 2 ** (N - NA)
+    flop = 4.0 * dA * dA * dB           # Hermitian rank-d_B update: half of 8 d_A^2 d_B real FLOP
+    tflops = flop / (ms / 1e3) / 1e12
+    peak = fp32_fma_peak_tflops()
+    line = {"metric": f"Pauli expectations/s on a subsystem: Tr(rho_A P) for all 4^{NA} P on the first {NA} of {N} qubits",
+            "value": 4.0 ** NA / (ms / 1e3), "unit": "Pauli expectations/s", "n_gpus": 1, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Haar state)",
+            "config": {"workload": f"N={N} Haar state, reduced state of the first {NA} qubits, one sre_mixed call",
+                       "N": N, "N_A": NA},
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+                         "traffic": None, "kernel": "Gram matrix Psi Psi^H (cuBLAS CHERK, FP32); the step also holds "
+                                                    "the 2^N_A family transforms",
+                         "flop_per_step": flop,
+                         "peak_kind": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x max SM clock (MEASURED_PEAKS.json sm_max_mhz)"},
+            "clocks": clk, "gpu_launches": int(launches),
+            "estimates": {"S2": r["S2"], "M": r["M"], "err_M": r["err_M"]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def fp32_fma_peak_tflops():
     """FP32 FMA rate from the unit counts (152 SMs x 128 FP32 lanes, 2 FLOP
     per FMA) and the measured maximum SM clock."""
@@ -524,6 +575,8 @@ def main():
         return run_batched(a)
     if a.workload == "precondition":
         return run_precondition(a)
+    if a.workload == "mixed":
+        return run_mixed(a)
     return run_cuda(a)
 
 
