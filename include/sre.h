@@ -244,7 +244,8 @@ SRE_API sre_status sre_mixed_workspace_bytes(int N, int N_A, size_t *bytes);
  * the basis index, b = a + 2^{N_A} e) of psi: c_P = Tr(rho_A P) for the
  * 4^{N_A} Pauli strings on A. The family x_A needs h(a) = sum_e
  * conj(psi(a ^ x_A, e)) psi(a, e), an entry of the Gram matrix C = Psi Psi^H
- * of psi viewed as a d_A x d_B matrix (computed by cuBLAS CHERK, FP32), then
+ * of psi viewed as a d_A x d_B matrix (one cuBLAS GEMM, FP32 emulated on the
+ * BF16 tensor cores with each input split into three BF16 parts), then
  * one N_A-bit transform per x_A with the moments fused (O(2^{N+N_A}) overall).
  * N in 1..30, N_A in 1..min(N, 15). workspace: >= sre_mixed_workspace_bytes,
  * 256-byte aligned, or NULL (library-owned). out: host. Synchronises the stream. */

@@ -194,9 +194,8 @@ __device__ __forceinline__ void pass_prologue(typename Cfg::C2 (&v)[Cfg::E], con
             }
         }
     } else if constexpr (SRC == SRC_GRAM) {
-        // h(a) = sum_e conj(psi(a ^ x, e)) psi(a, e) = C[a][a ^ x]; the lower
-        // triangle is the conjugate of the stored upper one. x = 0: the
-        // diagonal pair (C[g][g], C[g + d/2][g + d/2]).
+        // h(a) = sum_e conj(psi(a ^ x, e)) psi(a, e) = C[a][a ^ x]; x = 0: the
+        // diagonal pair (C[g][g], C[g + d/2][g + d/2])
         const float2 *C = a.gram;
         const unsigned long long ld = (unsigned long long)a.gram_ld;
         if (x != 0) {
@@ -204,16 +203,10 @@ __device__ __forceinline__ void pass_prologue(typename Cfg::C2 (&v)[Cfg::E], con
 #pragma unroll
             for (int k = 0; k < Cfg::E; ++k) {
                 const uint32_t g = slot_gidx<Cfg, A0>(base, rs, k);
-                const uint32_t r = g + (g & hm), c = r ^ x32;
-                if (r <= c) {
-                    const float2 h = __ldg(C + r + ld * c);
-                    v[k].x = h.x;
-                    v[k].y = h.y;
-                } else {
-                    const float2 h = __ldg(C + c + ld * r);
-                    v[k].x = h.x;
-                    v[k].y = -h.y;
-                }
+                const uint32_t r = g + (g & hm);
+                const float2 h = __ldg(C + r + ld * (r ^ x32));
+                v[k].x = h.x;
+                v[k].y = h.y;
             }
         } else {
             const uint32_t h32 = (uint32_t)half;

@@ -1032,7 +1032,7 @@ sre_status blas_handle(cublasHandle_t *h) {
 }
 
 // SRE of the reduced state on the first N_A qubits (SM, mixed states):
-// C = Psi Psi^H by cuBLAS CHERK (Psi = psi viewed column-major d_A x d_B), then
+// C = Psi Psi^H by one cuBLAS GEMM (Psi = psi viewed column-major d_A x d_B), then
 // every family x_A of the N_A-qubit system through the single-pass transform
 // with the h(a) = C[a][a ^ x_A] prologue and the fused moments, then the
 // fixed-order FP64 totals; Eq. Msre-mixed on the host.
@@ -1051,10 +1051,13 @@ sre_status mixed_impl(const void *psi, int N, int NA, void *ws, size_t ws_bytes,
     cublasHandle_t h = nullptr;
     CS(blas_handle(&h));
     if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) return fail(SRE_ECUDA, "cublasSetStream failed");
-    const float one = 1.0f, zero = 0.0f;
-    if (cublasCherk(h, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, (int)dA, (int)dB, &one, (const cuComplex *)psi,
-                    (int)dA, &zero, (cuComplex *)w.C, (int)dA) != CUBLAS_STATUS_SUCCESS)
-        return fail(SRE_ECUDA, "cublasCherk failed (N=%d, N_A=%d)", N, NA);
+    // C = Psi Psi^H as one complex GEMM (both triangles), FP32 emulated on the
+    // BF16 tensor cores: cuBLAS splits each FP32 input into three BF16 parts
+    const cuComplex one = make_cuComplex(1.0f, 0.0f), zero = make_cuComplex(0.0f, 0.0f);
+    if (cublasGemmEx(h, CUBLAS_OP_N, CUBLAS_OP_C, (int)dA, (int)dA, (int)dB, &one, psi, CUDA_C_32F, (int)dA, psi,
+                     CUDA_C_32F, (int)dA, &zero, w.C, CUDA_C_32F, (int)dA, CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
+                     CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
+        return fail(SRE_ECUDA, "cublasGemmEx failed (N=%d, N_A=%d)", N, NA);
     PassArgs a;
     memset(&a, 0, sizeof a);
     a.N = NA;

@@ -225,9 +225,9 @@ struct PassArgs {
     // weight of every 2^ZR_FINE-z range, one row of rw_stride floats per slot
     float *rw_out;
     long long rw_stride;
-    // SRC_GRAM (reduced state of the low N qubits of a larger state): the
-    // upper triangle of C = Psi Psi^H, column-major with leading dimension
-    // gram_ld, C[r][c] = sum_e psi(r, e) conj(psi(c, e))
+    // SRC_GRAM (reduced state of the low N qubits of a larger state):
+    // C = Psi Psi^H, column-major with leading dimension gram_ld,
+    // C[r][c] = sum_e psi(r, e) conj(psi(c, e))
     const float2 *gram;
     long long gram_ld;
     // Several states of the same N in one launch: the family index F (from xs
