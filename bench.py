@@ -196,6 +196,30 @@ def run_reference(a):
     return 0
 
 
+# ------------------------------------------------------------ replicas
+# bench.py --gpus N under torchrun runs N independent replicas (one GPU each):
+# every rank draws from its own Philox counter range, the timed region is
+# bracketed by barriers, and the step time is the maximum over ranks.
+COUNTER_STRIDE_LOG2 = 40
+
+
+def counter_base(rank: int) -> int:
+    """First Philox counter of a rank's draws (disjoint ranges of 2^40)."""
+    return rank << COUNTER_STRIDE_LOG2
+
+
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's time (all ranks call it; barrier, then MAX all-reduce)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    dist.barrier()
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ----------------------------------------------------------------- CUDA arm
 def run_cuda(a):
     import numpy as np
@@ -226,7 +250,7 @@ def run_cuda(a):
     xs = torch.empty(n_x, dtype=torch.int64, device=dev)
     zs = torch.empty(n_x * zpx, dtype=torch.int64, device=dev)
     cs = torch.empty(n_x * zpx, dtype=torch.float32, device=dev)
-    base_ctr = rank << 40
+    base_ctr = counter_base(rank)
 
     def step(i):
         return sre.sre_mc(psi, sre.SRE_MC_MARGINAL, n_x, zpx, seed=24, counter0=base_ctr + i * n_x,
@@ -253,12 +277,7 @@ def run_cuda(a):
     clk = clocks.stop()
     timing = sre.sre_pass_timing(False)
     launches = sre.sre_kernel_launches() - launches0
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        dist.barrier()
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     total_c = world * a.steps * n_x * float(2 ** N)
     value = total_c / (ms / 1e3)
 
