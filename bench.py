@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tc", action="store_true")
-    ap.add_argument("--workload", default="mc24", choices=["mc24", "batched", "precondition", "mixed"],
+    ap.add_argument("--workload", default="mc24",
+                    choices=["mc24", "batched", "precondition", "mixed", "exact18", "n30"],
                     help="mc24: the headline N=24 MC step; batched: exact M_2/nullity of 4096 T-doped states "
                          "with N ~ U{8..16} in one sre_exact_batched call, against a per-state loop")
     ap.add_argument("--count", type=int, default=4096)
@@ -574,6 +575,136 @@ def run_mixed(a):
     return 0
 
 
+def run_exact18(a):
+    """Exact enumeration at N = 18 (all 4^18 Pauli expectations of each of the
+    twelve T-doped states: eta in {1, 4, 16} x n_T in {0, 8, 32, 64}), FP32 SIMT
+    and split-BF16 (x3) tensor-core transforms. One step = sre_exact over all
+    twelve states."""
+    import torch
+    from paper_2601_00761_gb300 import build as sre_build
+    sre_build.build()
+    import paper_2601_00761_gb300 as sre
+    from paper_2601_00761_gb300 import inputs
+    torch.cuda.set_device(0)
+    specs = inputs.workload_n18_gate_lists()
+    states = []
+    for sp in specs:
+        p = torch.zeros(1 << 18, dtype=torch.complex64, device="cuda")
+        p[0] = 1
+        sre.apply_clifford_tdoped_circuit(p, sp["gates"])
+        states.append(p)
+    stream = torch.cuda.current_stream()
+
+    def timed(prec):
+        for _ in range(a.warmup):
+            for p in states:
+                sre.sre_exact(p, allow_nullity_error=True, precision=prec)
+        torch.cuda.synchronize()
+        l0 = sre.sre_kernel_launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            res = [sre.sre_exact(p, allow_nullity_error=True, precision=prec) for p in states]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / a.steps, res, sre.sre_kernel_launches() - l0
+
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    ms, res, launches = timed(0)
+    clk = clocks.stop()
+    ms_tc, res_tc, _ = timed(2)
+    total_c = len(states) * 4.0 ** 18
+    flop = total_c * 30.0        # 18 butterfly adds + ~12 FLOP of phase, squares and moment sums per string
+    tflops = flop / (ms / 1e3) / 1e12
+    peak = fp32_fma_peak_tflops()
+    dm = max(abs(r["M"][k] - q["M"][k]) for r, q in zip(res, res_tc) for k in range(3))
+    line = {"metric": "Pauli expectations/s, exact enumeration at N=18 (12 T-doped states)",
+            "value": total_c / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded T-doped random Clifford circuits, eta x n_T grid)",
+            "config": {"workload": "N=18, eta in {1,4,16} x n_T in {0,8,32,64}, sre_exact per state",
+                       "states": len(states), "pauli_strings": total_c},
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+                         "traffic": None, "kernel": "strided + row passes (psi and the families live in L2)",
+                         "flop_per_step": flop,
+                         "peak_kind": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x max SM clock (MEASURED_PEAKS.json sm_max_mhz)"},
+            "tensor_core_form": {"precision": "split-BF16 x3", "value": total_c / (ms_tc / 1e3), "ms_per_step": ms_tc,
+                                 "max_abs_dM_vs_fp32": dm},
+            "clocks": clk, "gpu_launches": int(launches),
+            "states": [{"eta": sp["eta"], "n_t": sp["n_t"], "M": r["M"], "nullity": r["nullity"]}
+                       for sp, r in zip(specs, res)]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_n30(a):
+    """Large MC with Clifford preconditioning at N = 30 (8 GB state): a T-doped
+    random Clifford circuit (eta = 16, n_T = 60: 960 Cliffords + 60 T) from
+    |0>, then 2000 random {H, S, CNOT} gates, both applied on the device; then
+    the marginal MC, 16 z per x. A 256-family pilot gives the family count that
+    would bring the standard errors of M_1 and M_2 to 1e-3 (reported); the timed
+    step is one sre_mc call of that many families, at most --nx."""
+    import torch
+    from paper_2601_00761_gb300 import build as sre_build
+    sre_build.build()
+    import paper_2601_00761_gb300 as sre
+    from paper_2601_00761_gb300 import inputs
+    torch.cuda.set_device(0)
+    N, zpx = 30, 16
+    psi = torch.zeros(1 << N, dtype=torch.complex64, device="cuda")
+    psi[0] = 1
+    circ = inputs.random_clifford_tdoped_gates(N, 960, 16, 30)
+    pre = inputs.random_clifford_gates(N, 2000, 31)
+    stream = torch.cuda.current_stream()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    sre.apply_clifford_tdoped_circuit(psi, circ)
+    sre.apply_clifford_tdoped_circuit(psi, pre)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    ms_gates = g0.elapsed_time(g1)
+    pilot = sre.sre_mc(psi, sre.SRE_MC_MARGINAL, 256, zpx, seed=30, counter0=1 << 40)
+    need = max(max(pilot["err_rb"][0], pilot["err_rb"][1]) / 1e-3, 1.0) ** 2 * 256
+    n_x = int(min(a.nx, max(256, 256 * math.ceil(need / 256))))    # the timed run stays within a minute
+    for _ in range(a.warmup):
+        sre.sre_mc(psi, sre.SRE_MC_MARGINAL, 32, zpx, seed=30, counter0=2 << 40)
+    torch.cuda.synchronize()
+    l0 = sre.sre_kernel_launches()
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r = sre.sre_mc(psi, sre.SRE_MC_MARGINAL, n_x, zpx, seed=30)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    launches = sre.sre_kernel_launches() - l0
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    rtc = sre.sre_mc(psi, sre.SRE_MC_MARGINAL, 256, zpx, seed=30, precision=2)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms_tc = t0.elapsed_time(t1)
+    plan = sre.sre_make_plan(N)
+    line = {"metric": "Pauli expectations/s, preconditioned MC at N=30 to 1e-3 standard error",
+            "value": n_x * 2.0 ** N / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": a.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded T-doped circuit eta=16, n_T=60, then 2000 random Clifford gates)",
+            "config": {"workload": "N=30 T-doped state, 2000-gate Clifford preconditioner, marginal MC",
+                       "N": N, "n_x": n_x, "n_x_for_1e-3": int(math.ceil(need)), "z_per_x": zpx,
+                       "passes": plan["n_passes"],
+                       "x_batch": plan["x_batch"], "gates": int(len(circ) + len(pre)), "ms_gates": ms_gates},
+            "clocks": clk, "gpu_launches": int(launches),
+            "estimates": {"M": r["M"], "err_M": r["err_M"], "M_rb": r["M_rb"], "err_rb": r["err_rb"],
+                          "pilot_err_rb": pilot["err_rb"]},
+            "tensor_core_form": {"precision": "split-BF16 x3", "n_x": 256,
+                                 "value": 256 * 2.0 ** N / (ms_tc / 1e3), "M_rb": rtc["M_rb"], "err_rb": rtc["err_rb"]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def fp32_fma_peak_tflops():
     """FP32 FMA rate from the unit counts (152 SMs x 128 FP32 lanes, 2 FLOP
     per FMA) and the measured maximum SM clock."""
@@ -603,6 +734,10 @@ def main():
         return run_precondition(a)
     if a.workload == "mixed":
         return run_mixed(a)
+    if a.workload == "exact18":
+        return run_exact18(a)
+    if a.workload == "n30":
+        return run_n30(a)
     return run_cuda(a)
 
 
