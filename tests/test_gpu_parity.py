@@ -221,6 +221,20 @@ def test_exact_n18_workload(sre):
             assert np.max(np.abs(c - oracle.family_spectrum(psi, x))) < TOL_C
 
 
+@pytest.mark.parametrize("NA,NB", [(8, 8), (9, 8), (9, 9)])
+def test_exact_product_additivity(sre, NA, NB):
+    """N = 16..18, beyond the oracle's full sweep in test time: M_a, the
+    nullity and the stabilizer count of a product state are the sums
+    (product) of those of its factors, each factor's taken from the oracle."""
+    a = inputs.haar_state(NA, 500 + NA)
+    b = oracle.circuit_state(NB, inputs.random_clifford_tdoped_gates(NB, 6 * NB, 3, 600 + NB))
+    ra, rb = oracle.sre_exact(a), oracle.sre_exact(b)
+    r = sre.sre_exact(dev(np.kron(a, b)), allow_nullity_error=True)
+    assert np.max(np.abs(np.array(r["M"]) - (np.array(ra["M"]) + rb["M"]))) < TOL_M, (r["M"], ra["M"], rb["M"])
+    assert r["nullity"] == ra["nullity"] + rb["nullity"]
+    assert r["stab_count"] == ra["stab_count"] * rb["stab_count"]
+
+
 def test_exact_clifford_invariance_multipass(sre):
     N = 16
     base = inputs.random_clifford_tdoped_gates(N, 0, 4, 77, n_t=6, first_block=32)
