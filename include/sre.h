@@ -84,7 +84,8 @@ typedef int sre_status;
 
 typedef struct {
     int precision;      /* SRE_FP32_SIMT (default), SRE_BF16X2_TC, SRE_BF16X3_TC */
-    double eps_null;    /* nullity tolerance on | |c| - 1 |; <= 0 means 1e-6 */
+    double eps_null;    /* nullity tolerance on | |c| - 1 |; <= 0 means 1e-6; >= 0.5 or NaN:
+                           SRE_EINVAL */
     int radix_log2;     /* bits of the last (contiguous) transform pass; 0 = planned/tuned */
     int tile_log2;      /* bits per strided pass; 0 = planned/tuned */
     int x_batch;        /* X-mask families in flight per launch; 0 = planned/tuned */
@@ -215,7 +216,10 @@ SRE_API sre_status pauli_x_marginal(const void *psi_c64_dev, int N, double *p_de
                             void *workspace, size_t workspace_bytes, void *stream);
 
 /* Stabilizer nullity nu = N - log2 #{P : | |c_P| - 1 | < eps} (the nullity
- * definition, Algorithm 1); eps <= 0 means 1e-6. N in 1..30. */
+ * definition, Algorithm 1); eps <= 0 means 1e-6, eps >= 0.5 or NaN is
+ * SRE_EINVAL. N in 1..26. The FP32 sweep flags every family holding a
+ * |c| > 1 - eps - 1e-4; the flagged families are recounted with every
+ * | |c| - 1 | < eps decision taken in FP64. */
 SRE_API sre_status stabilizer_nullity(const void *psi_c64_dev, int N, double eps, int *nullity_host,
                               long long *stab_count_host, void *stream);
 

@@ -21,6 +21,29 @@ struct DrawInfo {
 };
 
 cudaError_t launch_norm2(const float2 *psi, int N, double *scal, double *partial, cudaStream_t st);
+
+// FP64 recount of flagged families at their listed candidates (k_null.cu).
+// Family i of the launch is xs[fam_base + i] (F = (state << N) | x when
+// psi_list is set); its candidate count and list come from the FP32
+// DST_CANDLIST pass. counts[i] receives the family's stabilizer count, or 0
+// when it had no candidate or more than kdirect (<= cand_max, <=
+// NULL_CAND_MAX) of them; in the latter case F is appended to ovf (ovf_n).
+constexpr int NULL_CAND_MAX = 32;
+struct NullDirectArgs {
+    const float2 *psi;
+    const double *s_ptr;
+    const float2 *const *psi_list;
+    const double *s_list;
+    int N;
+    const unsigned long long *xs;
+    long long fam_base;
+    const unsigned *cand_cnt;
+    const unsigned *cand_z;
+    int cand_max, kdirect;
+    double eps;
+    unsigned long long *counts, *ovf, *ovf_n;
+};
+cudaError_t launch_null_direct(const NullDirectArgs &a, long long n_fam, cudaStream_t st);
 cudaError_t launch_fam_reduce(const TilePartial *tp, long long n_fam, int tiles, const unsigned long long *xs,
                               long long fam_base, int N, int M_last, int RL, FamMoments *fm, long long fm_base,
                               float *W, long long nr, cudaStream_t st);

@@ -364,7 +364,8 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const Pas
     const int n = a.n;
     const unsigned long long dmask = (N >= 64) ? ~0ULL : ((1ULL << N) - 1ULL);
     unsigned long long x = 0, F = 0;
-    if constexpr (SRC == SRC_PSI_FAMILY || DST == DST_MOMENTS || DST == DST_SPECTRUM || DST == DST_NULLCOUNT) {
+    if constexpr (SRC == SRC_PSI_FAMILY || DST == DST_MOMENTS || DST == DST_SPECTRUM || DST == DST_NULLCOUNT ||
+                  DST == DST_CANDLIST) {
         F = a.xs ? a.xs[a.fam_base + slot] : (unsigned long long)(a.fam_base + slot);
         x = F & dmask;
     }
@@ -450,6 +451,25 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const Pas
                 family_pair<R, C2>(x, j, s, v[k], gidx(Cfg::elem(t, k, AL)), z0, z1, c0, c1);
                 out[z0] = c0;
                 out[z1] = c1;
+            }
+        }
+    } else if constexpr (DST == DST_CANDLIST) {
+        // every packed z' of a flagged family whose pair (c(z0), c(z1))
+        // holds a |c| above the candidate threshold: counted, and listed
+        // while the slot's list has room
+        if (active) {
+            const R s = (R)(*s_ptr);
+            const R thr2 = (R)a.cand_thr * (R)a.cand_thr;
+#pragma unroll
+            for (int k = 0; k < Cfg::E; ++k) {
+                R c0, c1;
+                if (x) { c0 = (R)2 * s * v[k].x; c1 = (R)2 * s * v[k].y; }
+                else { c0 = s * (v[k].x + v[k].y); c1 = s * (v[k].x - v[k].y); }
+                if (c0 * c0 > thr2 || c1 * c1 > thr2) {
+                    const unsigned i = atomicAdd(a.cand_cnt + slot, 1u);
+                    if (i < (unsigned)a.cand_max)
+                        a.cand_z[(size_t)slot * (size_t)a.cand_max + i] = (unsigned)gidx(Cfg::elem(t, k, AL));
+                }
             }
         }
     } else if constexpr (DST == DST_NULLCOUNT) {

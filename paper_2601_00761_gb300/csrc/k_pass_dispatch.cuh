@@ -22,6 +22,8 @@ SRE_ALLOW(float, KIND_STRIDED, SRC_PSI_FAMILY, DST_BUF)
 SRE_ALLOW(float, KIND_STRIDED, SRC_BUF, DST_BUF)
 SRE_ALLOW(float, KIND_ROW, SRC_BUF, DST_MOMENTS)
 SRE_ALLOW(float, KIND_ROW, SRC_BUF, DST_SPECTRUM)
+SRE_ALLOW(float, KIND_SINGLE, SRC_PSI_FAMILY, DST_CANDLIST)
+SRE_ALLOW(float, KIND_ROW, SRC_BUF, DST_CANDLIST)
 SRE_ALLOW(double, KIND_SINGLE, SRC_PSI_FAMILY, DST_NULLCOUNT)
 SRE_ALLOW(double, KIND_SINGLE, SRC_PSI_FAMILY, DST_SPECTRUM)
 SRE_ALLOW(double, KIND_SINGLE, SRC_PSI_Q, DST_SQMAP)
@@ -42,7 +44,9 @@ template <class Cfg> struct TcOK {
 
 template <int KIND, class Cfg, int SRC, int DST>
 cudaError_t launch_if(const PassArgs &a, int tiles, cudaStream_t st) {
-    if constexpr (AllowedK<typename Cfg::Real, KIND, SRC, DST, Cfg::M, Cfg::LO, Cfg::RB, Cfg::G>::value) {
+    if constexpr (DST == DST_CANDLIST && AllowedK<typename Cfg::Real, KIND, SRC, DST, Cfg::M, Cfg::LO, Cfg::RB, Cfg::G>::value) {
+        return launch_cfg<Cfg, SRC, DST, 0>(a, tiles, st);   // FP32 butterflies whatever the sweep's precision
+    } else if constexpr (AllowedK<typename Cfg::Real, KIND, SRC, DST, Cfg::M, Cfg::LO, Cfg::RB, Cfg::G>::value) {
         if (a.precision == 0) return launch_cfg<Cfg, SRC, DST, 0>(a, tiles, st);
         if constexpr (TcOK<Cfg>::value) {
             if (a.precision == 2) return launch_cfg<Cfg, SRC, DST, 2>(a, tiles, st);
@@ -66,6 +70,7 @@ cudaError_t launch_sd(int src, int dst, const PassArgs &a, int tiles, cudaStream
     case DST_NULLCOUNT: return launch_if<KIND, Cfg, S, DST_NULLCOUNT>(a, tiles, st); \
     case DST_SQMAP: return launch_if<KIND, Cfg, S, DST_SQMAP>(a, tiles, st);     \
     case DST_P: return launch_if<KIND, Cfg, S, DST_P>(a, tiles, st);             \
+    case DST_CANDLIST: return launch_if<KIND, Cfg, S, DST_CANDLIST>(a, tiles, st); \
     default: return cudaErrorInvalidValue;                                       \
     }
     switch (src) {

@@ -200,6 +200,29 @@ struct Arena {
     }
 };
 
+// Nullity recount of flagged families (FP64 decisions): an FP32 pass lists
+// each family's candidate z' (NULL_CHUNK families at a time); families with
+// few candidates are recounted by direct FP64 sums at them, the rest by the
+// FP64 transform.
+constexpr long long NULL_CHUNK = 1LL << 12;
+
+struct NullWS {
+    unsigned *cand_cnt, *cand_z;      // per chunk: counts, lists [slot][NULL_CAND_MAX]
+    unsigned long long *counts;       // per flagged family (direct recount; 0 for the overflow)
+    unsigned long long *ovf, *ovf_n;  // overflow families (capacity: the flagged families)
+    unsigned long long *counts2;      // per overflow family (FP64 transform)
+    void *inter, *inter64;
+};
+
+void layout_null(Arena &A, long long fam_cap, NullWS &w) {
+    const long long ch = std::min(fam_cap, NULL_CHUNK);
+    w.cand_cnt = A.take<unsigned>((size_t)ch);
+    w.cand_z = A.take<unsigned>((size_t)ch * NULL_CAND_MAX);
+    w.ovf = A.take<unsigned long long>((size_t)fam_cap);
+    w.ovf_n = A.take<unsigned long long>(1);
+    w.counts2 = A.take<unsigned long long>((size_t)fam_cap);
+}
+
 struct ExactWS {
     double *scal, *npart, *epart, *etot;
     void *inter;
@@ -207,6 +230,7 @@ struct ExactWS {
     FamMoments *fm;
     unsigned long long *flags, *nflag, *counts, *cnt_sum;
     void *inter64;
+    NullWS nw;
 };
 
 void layout_exact(Arena &A, const Plan &P, const Plan &P64, ExactWS &w) {
@@ -222,8 +246,12 @@ void layout_exact(Arena &A, const Plan &P, const Plan &P64, ExactWS &w) {
     w.flags = A.take<unsigned long long>(d);
     w.nflag = A.take<unsigned long long>(1);
     w.counts = A.take<unsigned long long>(d);
-    w.cnt_sum = A.take<unsigned long long>(1);
+    w.cnt_sum = A.take<unsigned long long>(2);
     w.inter64 = P64.npass > 1 ? (void *)A.take<char>(P64.slot_bytes * (size_t)P64.B) : nullptr;
+    layout_null(A, (long long)d, w.nw);
+    w.nw.counts = w.counts;
+    w.nw.inter = w.inter;
+    w.nw.inter64 = w.inter64;
 }
 
 struct McWS {
@@ -316,12 +344,22 @@ sre_status check_opts(const sre_opts *o, sre_opts &out) {
     if (!o) return SRE_OK;
     out = *o;
     if (out.eps_null <= 0) out.eps_null = 1e-6;
+    if (!(out.eps_null < 0.5)) return fail(SRE_EINVAL, "eps_null must lie in (0, 0.5)");
     if (out.precision != SRE_FP32_SIMT && out.precision != SRE_BF16X2_TC && out.precision != SRE_BF16X3_TC)
         return fail(SRE_EINVAL, "unknown precision %d", out.precision);
     if (out.x_batch < 0 || out.radix_log2 < 0 || out.tile_log2 < 0)
         return fail(SRE_EINVAL, "negative tiling option");
     return SRE_OK;
 }
+
+// FP32 candidate threshold for the nullity tolerance eps: a c with
+// | |c| - 1 | < eps has |c| > 1 - eps, and the FP32 (or split-BF16) |c| is
+// within 1e-5 of the FP64 one, so 1e-4 below 1 - eps misses none of them.
+float cand_threshold(double eps) { return (float)(1.0 - eps - 1e-4); }
+
+// Listed z' per family up to which direct FP64 sums (4 + 2k operations per
+// packed point) undercut the FP64 transform (about 2N + 8).
+int null_kdirect(int N) { return std::min(NULL_CAND_MAX, N + 2); }
 
 PassArgs base_args(const Plan &P, const void *psi, const double *scal) {
     PassArgs a;
@@ -451,6 +489,71 @@ sre_status run_marginal(const void *psi, int N, const double *scal, double *p, d
     return SRE_OK;
 }
 
+// Recount of the n flagged families xs (F, with the state in the high bits
+// when a32.psi_list is set): counts[i] per family from the direct FP64 sums;
+// the families with more than null_kdirect(N) candidates land in ovf
+// (*n_ovf of them) with their FP64-transform counts in counts2.
+sre_status null_recount(const Plan &P, const Plan &P64, const PassArgs &a32, const PassArgs &a64,
+                        const unsigned long long *xs, long long n, double eps, const NullWS &w, cudaStream_t st,
+                        long long *n_ovf) {
+    CK(cudaMemsetAsync(w.ovf_n, 0, sizeof(unsigned long long), st));
+    PassArgs c = a32;
+    c.xs = xs;
+    c.precision = 0;
+    c.want_cand = 0;
+    c.cand_thr = cand_threshold(eps);
+    c.cand_cnt = w.cand_cnt;
+    c.cand_z = w.cand_z;
+    c.cand_max = NULL_CAND_MAX;
+    NullDirectArgs q;
+    memset(&q, 0, sizeof q);
+    q.psi = a32.psi;
+    q.s_ptr = a32.s_ptr;
+    q.psi_list = a32.psi_list;
+    q.s_list = a32.s_list;
+    q.N = P.N;
+    q.xs = xs;
+    q.cand_cnt = w.cand_cnt;
+    q.cand_z = w.cand_z;
+    q.cand_max = NULL_CAND_MAX;
+    q.kdirect = null_kdirect(P.N);
+    q.eps = eps;
+    q.ovf = w.ovf;
+    q.ovf_n = w.ovf_n;
+    const long long chunk = P.npass > 1 ? std::min(P.B, NULL_CHUNK) : NULL_CHUNK;
+    for (long long fb = 0; fb < n; fb += chunk) {
+        const long long nf = std::min(chunk, n - fb);
+        CK(cudaMemsetAsync(w.cand_cnt, 0, sizeof(unsigned) * (size_t)nf, st));
+        PassArgs b = c;
+        b.fam_base = fb;
+        b.n_fam = nf;
+        CS(run_transform(P, b, SRC_PSI_FAMILY, DST_CANDLIST, w.inter, st));
+        q.fam_base = fb;
+        q.counts = w.counts + fb;
+        CK(launch_null_direct(q, nf, st));
+        count_launches(1);
+    }
+    unsigned long long no = 0;
+    CK(cudaMemcpyAsync(&no, w.ovf_n, sizeof no, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (no > 0) {
+        CK(cudaMemsetAsync(w.counts2, 0, sizeof(unsigned long long) * no, st));
+        PassArgs d = a64;
+        d.xs = w.ovf;
+        d.eps = eps;
+        const long long step64 = P64.npass > 1 ? P64.B : (1LL << 20);
+        for (long long fb = 0; fb < (long long)no; fb += step64) {
+            PassArgs e = d;
+            e.fam_base = fb;
+            e.n_fam = std::min(step64, (long long)no - fb);
+            e.count_out = w.counts2 + fb;
+            CS(run_transform(P64, e, SRC_PSI_FAMILY, DST_NULLCOUNT, w.inter64, st));
+        }
+    }
+    *n_ovf = (long long)no;
+    return SRE_OK;
+}
+
 static_assert(offsetof(sre_result, stab_count) == 128 && offsetof(sre_result, r2) == 176 &&
                   sizeof(sre_result) == 184, "sre_result layout is part of the ABI");
 
@@ -526,6 +629,7 @@ sre_status exact_impl(const void *psi, int N, const sre_opts &o, void *ws, size_
     PassArgs a = base_args(P, psi, w.scal);
     a.precision = prec_code(o);
     a.tile_out = w.tiles;
+    a.cand_thr = cand_threshold(o.eps_null);
     const long long step = P.npass > 1 ? P.B : (long long)d;
     for (long long fb = 0; fb < (long long)d; fb += step) {
         const long long nf = (long long)d - fb < step ? (long long)d - fb : step;
@@ -548,26 +652,22 @@ sre_status exact_impl(const void *psi, int N, const sre_opts &o, void *ws, size_
     CK(cudaStreamSynchronize(st));
     if (!(host[TOT_N] > 0.0)) return fail(SRE_EZERO, "psi has zero norm");
 
-    // FP64 recheck of the candidate families
+    // FP64 recount of the candidate families
     unsigned long long cnt = 0;
     if (nflag > 0) {
-        CK(cudaMemsetAsync(w.counts, 0, nflag * sizeof(unsigned long long), st));
-        PassArgs c = base_args(P64, psi, w.scal);
-        c.xs = w.flags;
-        c.eps = o.eps_null;
-        const long long step64 = P64.npass > 1 ? P64.B : (1LL << 20);
-        for (long long fb = 0; fb < (long long)nflag; fb += step64) {
-            const long long nf = (long long)nflag - fb < step64 ? (long long)nflag - fb : step64;
-            PassArgs b = c;
-            b.fam_base = fb;
-            b.n_fam = nf;
-            b.count_out = w.counts + fb;
-            CS(run_transform(P64, b, SRC_PSI_FAMILY, DST_NULLCOUNT, w.inter64, st));
-        }
+        long long no = 0;
+        CS(null_recount(P, P64, base_args(P, psi, w.scal), base_args(P64, psi, w.scal), w.flags, (long long)nflag,
+                        o.eps_null, w.nw, st, &no));
         CK(launch_sum_u64(w.counts, (long long)nflag, w.cnt_sum, st));
         count_launches(1);
-        CK(cudaMemcpyAsync(&cnt, w.cnt_sum, sizeof cnt, cudaMemcpyDeviceToHost, st));
+        unsigned long long c2[2] = {0, 0};
+        if (no > 0) {
+            CK(launch_sum_u64(w.nw.counts2, no, w.cnt_sum + 1, st));
+            count_launches(1);
+        }
+        CK(cudaMemcpyAsync(c2, w.cnt_sum, sizeof(unsigned long long) * (no > 0 ? 2 : 1), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        cnt = c2[0] + c2[1];
     }
     init_result(out);
     finalize_exact(host, N, out);
@@ -606,6 +706,7 @@ struct BatchWS {
     FamMoments *fm;
     TilePartial *tiles;
     void *inter, *inter64;
+    NullWS nw;
 };
 
 constexpr int BATCH_NORM_BLOCKS = 16;
@@ -616,6 +717,7 @@ struct BatchGraph {
     cudaGraphExec_t exec = nullptr;
     unsigned long long kernels = 0;
     int prec = 0;
+    double eps = 0.0;           // nullity tolerance (sets the candidate threshold)
 };
 std::mutex g_bgraph_mu;
 std::vector<BatchGraph> g_bgraph;
@@ -648,10 +750,15 @@ void layout_batch(Arena &A, int count, std::vector<BucketPlan> &B, BatchWS &w) {
     w.inter = inter_b ? (void *)A.take<char>(inter_b) : nullptr;
     w.inter64 = inter64_b ? (void *)A.take<char>(inter64_b) : nullptr;
     w.counts = A.take<unsigned long long>(counts_n);
+    layout_null(A, (long long)counts_n, w.nw);
+    w.nw.counts = w.counts;
+    w.nw.inter = w.inter;
+    w.nw.inter64 = w.inter64;
 }
 
 // the main launch sequence of every bucket (captured into the graph)
-sre_status batch_main(const std::vector<BucketPlan> &B, const BatchWS &w, int count, int prec, cudaStream_t st) {
+sre_status batch_main(const std::vector<BucketPlan> &B, const BatchWS &w, int count, int prec, float cand_thr,
+                      cudaStream_t st) {
     CK(cudaMemsetAsync(w.nflag, 0, sizeof(unsigned long long) * B.size(), st));
     CK(cudaMemsetAsync(w.state_count, 0, sizeof(unsigned long long) * count, st));
     for (size_t bi = 0; bi < B.size(); ++bi) {
@@ -662,6 +769,7 @@ sre_status batch_main(const std::vector<BucketPlan> &B, const BatchWS &w, int co
         count_launches(2);
         PassArgs a = base_args(b.P, nullptr, w.s_list + b.off);
         a.precision = prec;
+        a.cand_thr = cand_thr;
         a.psi_list = w.psi_list + b.off;
         a.s_list = w.s_list + b.off;
         a.tile_out = w.tiles;
@@ -734,7 +842,11 @@ sre_status batched_impl(const void *const *psi_ptrs, const int *Ns, int count, c
     {
         std::lock_guard<std::mutex> lk(g_bgraph_mu);
         for (auto &g : g_bgraph)
-            if (g.ws == base && g.shape == shape && g.prec == prec_code(o)) { exec = g.exec; kernels = g.kernels; break; }
+            if (g.ws == base && g.shape == shape && g.prec == prec_code(o) && g.eps == o.eps_null) {
+                exec = g.exec;
+                kernels = g.kernels;
+                break;
+            }
     }
     if (!exec) {
         cudaStream_t cap;
@@ -743,7 +855,7 @@ sre_status batched_impl(const void *const *psi_ptrs, const int *Ns, int count, c
         cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) { cudaStreamDestroy(cap); return fail(SRE_ECUDA, "capture: %s", cudaGetErrorString(e)); }
         const unsigned long long l0 = g_launches.load();
-        sre_status s1 = batch_main(B, w, count, prec_code(o), cap);
+        sre_status s1 = batch_main(B, w, count, prec_code(o), cand_threshold(o.eps_null), cap);
         e = cudaStreamEndCapture(cap, &graph);
         cudaStreamDestroy(cap);
         if (s1 != SRE_OK) { if (e == cudaSuccess) cudaGraphDestroy(graph); return s1; }
@@ -760,6 +872,7 @@ sre_status batched_impl(const void *const *psi_ptrs, const int *Ns, int count, c
         g.exec = exec;
         g.kernels = kernels;
         g.prec = prec_code(o);
+        g.eps = o.eps_null;
         g_bgraph.push_back(g);
     }
     CK(cudaGraphLaunch(exec, st));
@@ -769,27 +882,22 @@ sre_status batched_impl(const void *const *psi_ptrs, const int *Ns, int count, c
     CK(cudaMemcpyAsync(nflag.data(), w.nflag, sizeof(unsigned long long) * B.size(), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
 
-    // FP64 recheck of the candidate families, per bucket
+    // FP64 recount of the candidate families, per bucket
     for (size_t bi = 0; bi < B.size(); ++bi) {
         const BucketPlan &b = B[bi];
         const long long nf = (long long)nflag[bi];
         if (nf <= 0) continue;
-        CK(cudaMemsetAsync(w.counts, 0, sizeof(unsigned long long) * nf, st));
-        PassArgs c = base_args(b.P64, nullptr, w.s_list + b.off);
-        c.psi_list = w.psi_list + b.off;
-        c.s_list = w.s_list + b.off;
-        c.xs = b.flags;
-        c.eps = o.eps_null;
-        const long long step = b.P64.npass > 1 ? b.P64.B : (1LL << 20);
-        for (long long fb = 0; fb < nf; fb += step) {
-            PassArgs d = c;
-            d.fam_base = fb;
-            d.n_fam = std::min(step, nf - fb);
-            d.count_out = w.counts + fb;
-            CS(run_transform(b.P64, d, SRC_PSI_FAMILY, DST_NULLCOUNT, w.inter64, st));
-        }
+        PassArgs a32 = base_args(b.P, nullptr, w.s_list + b.off), a64 = base_args(b.P64, nullptr, w.s_list + b.off);
+        a32.psi_list = a64.psi_list = w.psi_list + b.off;
+        a32.s_list = a64.s_list = w.s_list + b.off;
+        long long no = 0;
+        CS(null_recount(b.P, b.P64, a32, a64, b.flags, nf, o.eps_null, w.nw, st, &no));
         CK(launch_count_scatter(b.flags, w.counts, nf, b.N, w.state_count + b.off, st));
         count_launches(1);
+        if (no > 0) {
+            CK(launch_count_scatter(w.nw.ovf, w.nw.counts2, no, b.N, w.state_count + b.off, st));
+            count_launches(1);
+        }
     }
     std::vector<double> tot(TOT_N * (size_t)count), nrm(count);
     std::vector<unsigned long long> cnt(count);
@@ -1400,6 +1508,7 @@ sre_status stabilizer_nullity(const void *psi, int N, double eps, int *nullity_h
     CS(check_psi(psi, N, 1, 26));
     sre_opts o;
     sre_default_opts(&o);
+    if (!(eps < 0.5)) return fail(SRE_EINVAL, "eps must lie in (0, 0.5) (or be <= 0: 1e-6)");
     o.eps_null = eps > 0 ? eps : 1e-6;
     sre_result r;
     sre_status s = exact_impl(psi, N, o, nullptr, 0, (cudaStream_t)stream, &r);

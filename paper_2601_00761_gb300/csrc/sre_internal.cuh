@@ -198,7 +198,8 @@ enum DstMode {
     DST_NULLCOUNT = 3,  // count | |c| - 1 | < eps
     DST_SQMAP = 4,      // marginal: (Hr, Hi) -> ((Hr+Hi)^2, (Hr-Hi)^2)
     DST_P = 5,          // marginal: p[g] = (Hr+Hi)/d, p[g + d/2] = (Hr-Hi)/d
-    DST_SAMPLE = 6      // z sampler: c^2 of one z-range into shared memory
+    DST_SAMPLE = 6,     // z sampler: c^2 of one z-range into shared memory
+    DST_CANDLIST = 7    // nullity candidates of flagged families: packed z' lists
 };
 
 struct PassArgs {
@@ -241,6 +242,12 @@ struct PassArgs {
     // linear grid with the family fastest, so that the families in flight
     // work on the same tile at once and share its psi lines in L2.
     int fam_fast;
+    // DST_CANDLIST: per slot, the number of packed z' whose pair holds a
+    // |c| > cand_thr (cand_cnt, counted on past cand_max) and the first
+    // cand_max of them (cand_z, [slot][cand_max], in no fixed order)
+    unsigned *cand_cnt;
+    unsigned *cand_z;
+    int cand_max;
 };
 
 // host launchers (k_passes*.cu)

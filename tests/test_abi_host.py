@@ -108,6 +108,12 @@ def test_argument_errors_do_not_touch_the_gpu(L):
     assert L.sre_exact(_fake_ptr(0x1000), 10, ctypes.byref(bad), None, 0, None, ctypes.byref(r)) == sre.SRE_EINVAL
     neg = sre.Opts(0, 1e-6, 0, 0, -1)
     assert L.sre_exact(_fake_ptr(0x1000), 10, ctypes.byref(neg), None, 0, None, ctypes.byref(r)) == sre.SRE_EINVAL
+    for eps in (0.5, 2.0, float("nan")):     # nullity tolerance outside (0, 0.5)
+        wide = sre.Opts(0, eps, 0, 0, 0)
+        assert L.sre_exact(_fake_ptr(0x1000), 10, ctypes.byref(wide), None, 0, None, ctypes.byref(r)) == sre.SRE_EINVAL
+        nu, cnt = ctypes.c_int(), ctypes.c_longlong()
+        assert L.stabilizer_nullity(_fake_ptr(0x1000), 10, ctypes.c_double(eps), ctypes.byref(nu), ctypes.byref(cnt),
+                                    None) == sre.SRE_EINVAL
     g = (sre.Gate * 1)(sre.Gate(9, 0, 0))
     assert L.apply_clifford_tdoped_circuit(_fake_ptr(0x1000), 4, g, 1, None) == sre.SRE_EINVAL
     g = (sre.Gate * 1)(sre.Gate(3, 1, 1))

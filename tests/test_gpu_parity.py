@@ -247,6 +247,25 @@ def test_exact_clifford_invariance_multipass(sre):
     assert a["nullity"] == b["nullity"] <= 6
 
 
+@pytest.mark.parametrize("N", [6, 13, 16, 18])
+def test_nullity_wide_tolerance(sre, N):
+    """Qubit 0 with <Y> = 1 - 5e-4, the rest |0>: the Y family's largest
+    |c| is 1 - 5e-4 and it holds no exact stabilizer. At eps = 1e-3 its 2^(N-1)
+    strings count (nullity 0), at eps = 1e-6 they do not (nullity 1); both
+    readings of the nullity definition, with the oracle's count up to N = 8."""
+    phi = math.acos(1.0 - 5e-4)
+    q0 = (1 / math.sqrt(2), 1j * complex(math.cos(phi), math.sin(phi)) / math.sqrt(2))
+    psi = inputs.product_state([q0] + [inputs.ZERO_QUBIT] * (N - 1))
+    p = dev(psi)
+    assert sre.stabilizer_nullity(p, eps=1e-3) == (0, 1 << N)
+    assert sre.stabilizer_nullity(p, eps=1e-6) == (1, 1 << (N - 1))
+    r = sre.sre_exact(p, eps_null=1e-3)
+    assert r["nullity"] == 0 and r["stab_count"] == 1 << N
+    if N <= 8:
+        assert oracle.sre_exact(psi, eps=1e-3)["nullity"] == 0
+        assert oracle.sre_exact(psi, eps=1e-6)["nullity"] == 1
+
+
 def test_nullity_entry_point(sre):
     nu, cnt = sre.stabilizer_nullity(dev(inputs.t_product_state(12, 5)))
     assert nu == 5 and cnt == 1 << 7
