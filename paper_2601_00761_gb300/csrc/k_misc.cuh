@@ -28,7 +28,7 @@ cudaError_t launch_norm2(const float2 *psi, int N, double *scal, double *partial
 // DST_CANDLIST pass. counts[i] receives the family's stabilizer count, or 0
 // when it had no candidate or more than kdirect (<= cand_max, <=
 // NULL_CAND_MAX) of them; in the latter case F is appended to ovf (ovf_n).
-constexpr int NULL_CAND_MAX = 32;
+constexpr int NULL_CAND_MAX = 64;
 struct NullDirectArgs {
     const float2 *psi;
     const double *s_ptr;

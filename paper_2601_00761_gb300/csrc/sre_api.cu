@@ -204,7 +204,7 @@ struct Arena {
 // each family's candidate z' (NULL_CHUNK families at a time); families with
 // few candidates are recounted by direct FP64 sums at them, the rest by the
 // FP64 transform.
-constexpr long long NULL_CHUNK = 1LL << 12;
+constexpr long long NULL_CHUNK = 1LL << 11;
 
 struct NullWS {
     unsigned *cand_cnt, *cand_z;      // per chunk: counts, lists [slot][NULL_CAND_MAX]

@@ -266,6 +266,38 @@ def test_nullity_wide_tolerance(sre, N):
         assert oracle.sre_exact(psi, eps=1e-6)["nullity"] == 1
 
 
+@pytest.mark.parametrize("N", [8, 12, 16])
+def test_nullity_count_not_a_subgroup(sre, N):
+    """Every qubit with <Z> = 1 - 6e-4, eps = 1e-3: exactly the strings of
+    Z-weight <= 1 lie within eps of 1 (1 + N of them, not a power of two, so
+    the nullity is undefined); their packed z' span more than six dimensions,
+    so the recount sums at each listed z'. Oracle count up to N = 8."""
+    th = math.acos(1.0 - 6e-4) / 2
+    psi = inputs.product_state([(math.cos(th), math.sin(th))] * N)
+    r = sre.sre_exact(dev(psi), eps_null=1e-3, allow_nullity_error=True)
+    assert r["stab_count"] == 1 + N and r["nullity"] == -1
+    if N <= 8:
+        assert oracle.sre_exact(psi, eps=1e-3)["stab_count"] == 1 + N
+
+
+@pytest.mark.parametrize("k,seed", [(4, 1), (5, 2), (6, 3), (7, 4)])
+def test_nullity_coset_families(sre, k, seed):
+    """A random k-qubit stabilizer state next to |0>^(10-k): a family with a
+    stabilizer holds 2^(10-k) of them or more, their packed z' a coset of 3 to
+    6 dimensions (bin sums, in two and four chunks for 5 and 6), the x = 0
+    family's beyond the list (FP64 transform). Count, nullity and M_a against
+    the oracle."""
+    N = 10
+    top = oracle.circuit_state(k, inputs.random_clifford_gates(k, 12 * k, 950 + seed))
+    low = np.zeros(1 << (N - k), dtype=np.complex128)
+    low[0] = 1.0
+    psi = np.kron(top, low)
+    ref = oracle.sre_exact(psi)
+    r = sre.sre_exact(dev(psi))
+    assert r["stab_count"] == ref["stab_count"] == 1 << N and r["nullity"] == 0
+    assert np.max(np.abs(np.array(r["M"]) - ref["M"])) < TOL_M
+
+
 def test_nullity_entry_point(sre):
     nu, cnt = sre.stabilizer_nullity(dev(inputs.t_product_state(12, 5)))
     assert nu == 5 and cnt == 1 << 7
