@@ -31,7 +31,7 @@
  *  - workspace: device scratch of at least sre_workspace_bytes() bytes, owned
  *    by the caller, or NULL, in which case the library uses a buffer of its
  *    own (kept per device until sre_release_workspace()).
- *  - N is limited to 1..32 (sre_mc and sre_exact: 1..30, see each call).
+ *  - N is limited to 1..32 (sre_mc: 2..30, sre_exact: 1..26; see each call).
  *  - Errors: SRE_EINVAL (bad argument: N out of range, NULL or misaligned
  *    pointer, bad option), SRE_ENOMEM (allocation failed), SRE_ECUDA (a CUDA
  *    call failed; message says which), SRE_EZERO (psi has zero norm),
@@ -156,8 +156,10 @@ SRE_API sre_status sre_norm2(const void *psi_c64_dev, int N, double *norm2_host,
 /* Exact enumeration of all 4^N strings, Algorithm 1: M_1..M_3 and the
  * nullity in one sweep over the 2^N X-mask families (each family one
  * Walsh-Hadamard transform of f_x, Eq. Pxz-corr). Families whose FP32
- * spectrum has |c| > 1 - 1e-4 are re-evaluated in FP64 before the count
- * (n_flagged). N in 1..30. out: host. */
+ * spectrum has |c| > 1 - eps_null - 1e-4 (n_flagged of them) are recounted
+ * with every | |c| - 1 | < eps_null decision taken in FP64 (the listed
+ * candidates of each such family, by direct or coset sums, or its FP64
+ * transform). N in 1..26. out: host. */
 SRE_API sre_status sre_exact(const void *psi_c64_dev, int N, const sre_opts *opts,
                      void *workspace, size_t workspace_bytes, void *stream,
                      sre_result *out);
@@ -167,8 +169,8 @@ SRE_API sre_status sre_exact(const void *psi_c64_dev, int N, const sre_opts *opt
  * Ns_host[i] in 1..20). States are grouped by N; each launch covers every
  * (state, family) item of a chunk of same-N states, and the launch sequence
  * of the whole batch is captured once into a CUDA graph (cached for the same
- * batch shape) and replayed; the FP64 nullity recheck of candidate families
- * follows. Plans come from sre_autotune's table when opts leaves the tiling
+ * batch shape) and replayed; the FP64 nullity recount of candidate families
+ * follows, as in sre_exact. Plans come from sre_autotune's table when opts leaves the tiling
  * at 0. out: host array of `count` results (a state whose stabilizer count is
  * not a power of two gets nullity -1). workspace must be NULL (library
  * workspace). Returns SRE_EZERO if a state has zero norm. */
@@ -182,7 +184,8 @@ SRE_API sre_status sre_exact_batched(const void *const *psi_ptrs_host, const int
  * and the plan/workspace queries use whenever opts leaves those three fields
  * at 0 (so query workspace sizes after tuning). If the environment variable
  * SRE_TUNE_FILE names a file, the table is read from and written to it.
- * *best receives the choice (the defaults when N needs a single pass). */
+ * *best receives the choice (the defaults when N needs a single pass). N in
+ * 2..26. */
 SRE_API sre_status sre_autotune(const void *psi_c64_dev, int N, void *stream, sre_opts *best);
 
 /* Monte Carlo over X-mask families (N in 2..30).

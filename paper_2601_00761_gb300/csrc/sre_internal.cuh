@@ -76,12 +76,12 @@ __host__ __device__ __forceinline__ unsigned long long insert0(unsigned long lon
 }
 
 // Per-tile partial sums of the last pass (FP64): c^2, c^4, c^6, c^2 log2 c^2,
-// the two z-range weights the tile contributes to, and the count of FP32
-// nullity candidates (|c| > 1 - 1e-4).
+// the two z-range weights the tile contributes to, and the FP32 nullity
+// candidate flag (some |c| above PassArgs::cand_thr).
 struct TilePartial {
     double m[4];
     double w[2];
-    unsigned int cand;     // 1 if the tile holds a |c| > 1 - 1e-4
+    unsigned int cand;     // 1 if the tile holds a |c| > cand_thr
     unsigned int pad;
     double pad2;
 };
@@ -250,8 +250,5 @@ struct PassArgs {
     int cand_max;
 };
 
-// host launchers (k_passes*.cu)
-cudaError_t launch_pass(int precision_bits /*32|64*/, int M, int LO, int src, int dst,
-                        const PassArgs &a, int tiles_per_family, cudaStream_t st);
 
 } // namespace sre
