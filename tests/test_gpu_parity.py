@@ -187,7 +187,8 @@ def test_exact_vs_oracle(sre, N):
     _check_exact(sre.sre_exact(dev(h), allow_nullity_error=True), oracle.sre_exact(h), N)
 
 
-@pytest.mark.parametrize("N,k", [(1, 1), (2, 0), (5, 3), (9, 9), (14, 7), (15, 5), (16, 8), (17, 3), (18, 9)])
+@pytest.mark.parametrize("N,k", [(1, 1), (2, 0), (5, 3), (9, 9), (14, 7), (15, 5), (16, 8), (17, 3), (18, 9),
+                                 (20, 6)])
 def test_exact_t_product_closed_form(sre, N, k):
     r = sre.sre_exact(dev(inputs.t_product_state(N, k)))
     assert abs(r["M"][0] - k / 2) < TOL_M
@@ -221,9 +222,9 @@ def test_exact_n18_workload(sre):
             assert np.max(np.abs(c - oracle.family_spectrum(psi, x))) < TOL_C
 
 
-@pytest.mark.parametrize("NA,NB", [(8, 8), (9, 8), (9, 9)])
+@pytest.mark.parametrize("NA,NB", [(8, 8), (9, 8), (9, 9), (10, 10)])
 def test_exact_product_additivity(sre, NA, NB):
-    """N = 16..18, beyond the oracle's full sweep in test time: M_a, the
+    """N = 16..20, beyond the oracle's full sweep in test time: M_a, the
     nullity and the stabilizer count of a product state are the sums
     (product) of those of its factors, each factor's taken from the oracle."""
     a = inputs.haar_state(NA, 500 + NA)
@@ -358,6 +359,30 @@ def test_mc_marginal_vs_oracle(sre, N, n_x, zpx):
     assert np.max(np.abs(c - ref["c"])) < TOL_C
     assert np.max(np.abs(np.array(r["M"]) - ref["M"])) < TOL_M
     assert np.max(np.abs(np.array(r["M_rb"]) - ref["M_rb"])) < TOL_M
+
+
+@pytest.mark.parametrize("N", [12, 16])
+def test_mc_marginal_ragged_batches(sre, N):
+    """11 families in launches of 4 (4 + 4 + 3): draws, sampled expectations
+    and estimates equal the oracle's, as in one launch."""
+    psi = oracle.circuit_state(N, inputs.random_clifford_tdoped_gates(N, 8 * N, 3, 720 + N))
+    r = sre.sre_mc(dev(psi), sre.SRE_MC_MARGINAL, 11, 8, seed=31, counter0=5, return_samples=True, x_batch=4)
+    ref = oracle.mc_marginal(psi, 11, 8, 31, 5)
+    assert np.array_equal(r["xs"].cpu().numpy().astype(np.uint64), ref["xs"])
+    assert np.array_equal(r["zs"].cpu().numpy().astype(np.uint64), ref["zs"])
+    assert np.max(np.abs(r["c"].cpu().numpy() - ref["c"])) < TOL_C
+    assert np.max(np.abs(np.array(r["M"]) - ref["M"])) < TOL_M
+
+
+@pytest.mark.parametrize("N,xb", [(16, 1000), (18, 2999)])
+def test_exact_ragged_batches(sre, N, xb):
+    """Family batches that do not divide 2^N (a short last launch): the
+    per-family sums and their fixed-order totals do not depend on the batch
+    size, so M_a and the nullity equal the default plan's exactly."""
+    psi = dev(oracle.circuit_state(N, inputs.random_clifford_tdoped_gates(N, 0, 4, 730 + N, n_t=6, first_block=2 * N)))
+    a = sre.sre_exact(psi)
+    b = sre.sre_exact(psi, x_batch=xb)
+    assert a["M"] == b["M"] and a["nullity"] == b["nullity"] and a["stab_count"] == b["stab_count"]
 
 
 def test_mc_is_deterministic_run_to_run(sre):
