@@ -718,7 +718,21 @@ struct BatchGraph {
     unsigned long long kernels = 0;
     int prec = 0;
     double eps = 0.0;           // nullity tolerance (sets the candidate threshold)
+    std::vector<long long> plan;  // every bucket's tiling (plan_signature)
 };
+
+// The tiling a bucket's launch sequence was captured with: a cached graph is
+// replayed only for the same plans (options and the autotuner's table can
+// change them for the same batch shape).
+std::vector<long long> plan_signature(const std::vector<BucketPlan> &B) {
+    std::vector<long long> v;
+    for (const BucketPlan &b : B) {
+        v.insert(v.end(), {(long long)b.N, (long long)b.P.npass, (long long)b.P.M_last, b.P.B, b.P.tiles_last,
+                           (long long)b.states_per_chunk});
+        for (int i = 0; i < b.P.nstrided; ++i) v.insert(v.end(), {(long long)b.P.K[i], (long long)b.P.lo[i]});
+    }
+    return v;
+}
 std::mutex g_bgraph_mu;
 std::vector<BatchGraph> g_bgraph;
 
@@ -839,10 +853,11 @@ sre_status batched_impl(const void *const *psi_ptrs, const int *Ns, int count, c
     // main sequence: replay a cached graph of the same shape on the same workspace, else capture one
     cudaGraphExec_t exec = nullptr;
     unsigned long long kernels = 0;
+    const std::vector<long long> sig = plan_signature(B);
     {
         std::lock_guard<std::mutex> lk(g_bgraph_mu);
         for (auto &g : g_bgraph)
-            if (g.ws == base && g.shape == shape && g.prec == prec_code(o) && g.eps == o.eps_null) {
+            if (g.ws == base && g.shape == shape && g.prec == prec_code(o) && g.eps == o.eps_null && g.plan == sig) {
                 exec = g.exec;
                 kernels = g.kernels;
                 break;
@@ -873,6 +888,7 @@ sre_status batched_impl(const void *const *psi_ptrs, const int *Ns, int count, c
         g.kernels = kernels;
         g.prec = prec_code(o);
         g.eps = o.eps_null;
+        g.plan = sig;
         g_bgraph.push_back(g);
     }
     CK(cudaGraphLaunch(exec, st));

@@ -56,6 +56,21 @@ def test_batched_graph_replay_with_new_states(sre):
     _check(sre, b, rb)
 
 
+def test_batched_graph_follows_the_plan(sre):
+    """The same batch shape with another family batch size runs its own
+    launch sequence (a cached graph is keyed on the plan as well as the
+    shape): 4^16 families in launches of 1024, then of 4096."""
+    p = torch.from_numpy(inputs.haar_state(16, 16).astype(np.complex64)).cuda()
+    counts = []
+    for xb in (1024, 4096, 1024):
+        k0 = sre.sre_kernel_launches()
+        r = sre.sre_exact_batched([p], x_batch=xb)[0]
+        counts.append(sre.sre_kernel_launches() - k0)
+        ref = sre.sre_exact(p, x_batch=xb, allow_nullity_error=True)
+        assert np.max(np.abs(np.array(r["M"]) - np.array(ref["M"]))) < TOL_M
+    assert counts[0] == counts[2] and counts[0] > counts[1]
+
+
 def test_batched_small_vs_oracle(sre):
     specs = inputs.workload_batched_specs(count=6, seed0=77, n_min=3, n_max=8)
     states, refs = [], []
