@@ -84,6 +84,25 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def bf16_peak():
+    """Dense BF16 tensor rate (TFLOP/s): the measured burst figure, else the
+    fallback of an earlier GB300 measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def tc_mma_flop_per_family(pass_bits, N, nsplit=3):
+    """Tensor-core FLOPs a family issues in the split-BF16 form: every
+    4-bit group of a pass's transformed bits is one H_16 product, 16 MACs (32
+    FLOP) per packed point for each BF16 part of the real and of the
+    imaginary plane; leftover bits are FP32 butterflies."""
+    rounds = sum(b // 4 for b in pass_bits)
+    return 2.0 ** (N - 1) * rounds * 32.0 * nsplit * 2
+
+
 # ------------------------------------------------------------- clocks
 class Clocks:
     """nvidia-smi samples every 200 ms while the timed region runs."""
@@ -330,9 +349,14 @@ def run_cuda(a):
         tdom = int(np.argmax([tt["ms_sum"][p] for p in range(npass)]))
         tavg = tt["ms_sum"][tdom] / max(1, tt["launches"][tdom])
         tach = tt["bytes_per_launch"][tdom] / (tavg / 1e3) / 1e9
+        mma_tflops = (tc_mma_flop_per_family(sre.sre_make_plan(N, **kw)["pass_bits"], N) * n_x
+                      / (tms / tc_steps / 1e3) / 1e12)
+        bf16, bf16_kind = bf16_peak()
         tc = {"precision": "split-BF16 x3 (mma.sync m16n8k16, FP32 accumulate)",
               "value": world * tc_steps * n_x * float(2 ** N) / (tms / 1e3), "unit": UNIT,
               "ms_per_step": tms / tc_steps, "dominant_pass": tdom, "achieved_GBps": tach, "frac": tach / hbm,
+              "mma_tflops": mma_tflops, "mma_frac": mma_tflops / bf16,
+              "mma_peak": {"tflops": bf16, "kind": f"{bf16_kind} dense BF16 (MEASURED_PEAKS.json bf16_tflops)"},
               "pass_ms_share": [tt["ms_sum"][p] / sum(tt["ms_sum"][:npass]) for p in range(npass)],
               "M_rb": rtc["M_rb"], "err_rb": rtc["err_rb"]}
 
@@ -550,12 +574,7 @@ def run_mixed(a):
     dA, dB = 2 ** NA, 2 ** (N - NA)
     flop = 8.0 * dA * dA * dB           # the complex GEMM Psi Psi^H in FP32 arithmetic
     tflops = flop / (ms / 1e3) / 1e12
-    bf16 = 1876.6
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            bf16 = float(json.load(f)["bf16_tflops"])
-    except Exception:
-        pass
+    bf16, _ = bf16_peak()
     peak = bf16 / 9.0                   # FP32 emulated as 3 x 3 BF16 products
     line = {"metric": f"Pauli expectations/s on a subsystem: Tr(rho_A P) for all 4^{NA} P on the first {NA} of {N} qubits",
             "value": 4.0 ** NA / (ms / 1e3), "unit": "Pauli expectations/s", "n_gpus": 1, "steps": a.steps,
@@ -614,6 +633,8 @@ def run_exact18(a):
     ms, res, launches = timed(0)
     clk = clocks.stop()
     ms_tc, res_tc, _ = timed(2)
+    mma_tflops = (tc_mma_flop_per_family(sre.sre_make_plan(18)["pass_bits"], 18) * 2.0 ** 18 * len(states)
+                  / (ms_tc / 1e3) / 1e12)
     total_c = len(states) * 4.0 ** 18
     flop = total_c * 30.0        # 18 butterfly adds + ~12 FLOP of phase, squares and moment sums per string
     tflops = flop / (ms / 1e3) / 1e12
@@ -630,7 +651,8 @@ def run_exact18(a):
                          "flop_per_step": flop,
                          "peak_kind": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x max SM clock (MEASURED_PEAKS.json sm_max_mhz)"},
             "tensor_core_form": {"precision": "split-BF16 x3", "value": total_c / (ms_tc / 1e3), "ms_per_step": ms_tc,
-                                 "max_abs_dM_vs_fp32": dm},
+                                 "max_abs_dM_vs_fp32": dm, "mma_tflops": mma_tflops,
+                                 "mma_frac": mma_tflops / bf16_peak()[0]},
             "clocks": clk, "gpu_launches": int(launches),
             "states": [{"eta": sp["eta"], "n_t": sp["n_t"], "M": r["M"], "nullity": r["nullity"]}
                        for sp, r in zip(specs, res)]}
