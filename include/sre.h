@@ -296,6 +296,17 @@ SRE_API sre_status sre_philox_blocks(const unsigned long long *ctr_key_dev, unsi
  * (every entry point counts its launches). Host only. */
 SRE_API unsigned long long sre_kernel_launches(void);
 
+/* Self-test of the bounded device waits (no counterpart in the paper). The
+ * bulk-copy z sampler of sre_mc waits on mbarriers for its copies; every
+ * such wait gives up after about 2^31 SM cycles (about a second), records
+ * SRE_ERR_TIMEOUT in a device error word and lets the call return
+ * SRE_ETIMEOUT with the context intact. This call runs one warp whose
+ * mbarrier expects more bytes than the one copy issued to it, so its wait
+ * can only end by the bound: it returns SRE_ETIMEOUT when the bound works
+ * (about a second), SRE_OK if the wait completed (a broken barrier), or
+ * SRE_ECUDA. Synchronises the stream. */
+SRE_API sre_status sre_selftest_bounded_wait(void *stream);
+
 /* Pass timing inside sre_mc: enable = 1 clears the counters and starts
  * recording CUDA events around every full-batch family-transform pass launch
  * of subsequent sre_mc calls; enable = 0 stops. Either call first copies the

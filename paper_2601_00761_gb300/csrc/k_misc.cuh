@@ -71,6 +71,9 @@ cudaError_t launch_philox_test(const unsigned long long *ctr_key, unsigned long 
 // z sampler (k_sample.cu): recompute the c of each draw's range and pick z by
 // the exact fixed-point scan of c^2 over the range. fine: ranges of 2^ZR_FINE z
 // recomputed from the folded last-pass tile; else a range is a tile half.
+// one warp whose mbarrier wait can only end by its bound (k_sample.cu);
+// src16: 16 readable, 16-byte aligned device bytes; err: device word
+cudaError_t launch_wait_selftest(const void *src16, int *err, cudaStream_t st);
 cudaError_t launch_zsample(int single, int fine, int M, const PassArgs &a, const DrawInfo *draws, int z_per_x,
                            unsigned long long *zs, float *cz, cudaStream_t st);
 

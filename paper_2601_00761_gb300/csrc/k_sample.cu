@@ -172,7 +172,58 @@ cudaError_t launch_zs(const PassArgs &a, const DrawInfo *draws, int z_per_x, uns
 // input summed over its M - ZR_FINE top bits with signs (-1)^{F.h}, F the
 // block's top bits: the warp reads the tile once, folds it, and transforms
 // 2^ZR_FINE points instead of 2^M.
-constexpr int FOLD_WARPS = 4;   // 152 registers a thread: three CTAs per SM
+constexpr int FOLD_WARPS = 4;   // three CTAs per SM
+
+// shared-memory points per warp: the two-stage ring of 2^RL-point blocks
+// (the transpose and the fixed-point range reuse it afterwards)
+constexpr int FOLD_WSTRIDE = 2 * (1 << ZR_FINE);
+constexpr size_t FOLD_SMEM = sizeof(float2) * (size_t)FOLD_WARPS * FOLD_WSTRIDE + sizeof(uint64_t) * 2 * FOLD_WARPS;
+__device__ __forceinline__ uint64_t *fold_bars(unsigned char *smraw) {
+    return reinterpret_cast<uint64_t *>(smraw + sizeof(float2) * (size_t)FOLD_WARPS * FOLD_WSTRIDE);
+}
+
+// mbarrier and bulk-copy primitives (PTX ISA: mbarrier, cp.async.bulk)
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// make the initialised barriers visible to the asynchronous proxy
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// bytes (a multiple of 16) from global src to shared dst (both 16-byte
+// aligned), completing on bar
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// warp-uniform wait for the completion of phase `parity` of bar; false after
+// about 2^31 cycles (about a second) without it
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    const long long t0 = clock64();
+    for (;;) {
+        if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+        if (clock64() - t0 > (1LL << 31)) return false;
+    }
+}
 
 template <int M>
 __global__ void __launch_bounds__(32 * FOLD_WARPS) zsample_fold_kernel(const PassArgs a, const DrawInfo *draws,
@@ -180,9 +231,10 @@ __global__ void __launch_bounds__(32 * FOLD_WARPS) zsample_fold_kernel(const Pas
                                                                       float *cz) {
     constexpr int RL = ZR_FINE, NB = 1 << RL, H = 1 << (M - RL), SW = NB + NB / 32;
     static_assert(M > RL && RL == 10, "a warp holds 32 x 32 folded points");
+    static_assert(FOLD_WSTRIDE >= SW, "the transpose and the range fit the warp's region");
     extern __shared__ __align__(16) unsigned char smraw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2 *sm = reinterpret_cast<float2 *>(smraw) + warp * SW;
+    float2 *sm = reinterpret_cast<float2 *>(smraw) + warp * FOLD_WSTRIDE;
     const long long idx = (long long)blockIdx.x * FOLD_WARPS + warp;
     if (idx >= a.n_fam * (long long)z_per_x) return;      // uniform over the warp
     const long long slot = idx / z_per_x;
@@ -205,19 +257,53 @@ __global__ void __launch_bounds__(32 * FOLD_WARPS) zsample_fold_kernel(const Pas
     float2 f[32];
 #pragma unroll
     for (int k = 0; k < 32; ++k) f[k] = make_float2(0.f, 0.f);
-#pragma unroll 1
-    for (int h = 0; h < H; ++h) {
-        const float sg = (__popc(F & (uint32_t)h) & 1) ? -1.f : 1.f;
-        const float2 sg2 = make_float2(sg, sg);
-        const float2 *sb = src + (size_t)h * NB;
+    // The tile's 2^(M-RL) blocks of 2^RL points (8 KB each) arrive by bulk
+    // asynchronous copies into a two-stage ring of the warp's shared memory,
+    // each stage completing on its own mbarrier; lane 0 issues block h + 2
+    // into a stage once the warp has folded block h out of it. Every wait is
+    // bounded: past the bound the warp records a timeout in the error word,
+    // waits (bounded again) for its copies still in flight and returns.
+    {
+        float2 *ring = sm;                                   // 2 x 2^RL points
+        uint64_t *bar = fold_bars(smraw) + 2 * warp;
+        const float2 *tsrc = src - lane;
+        if (lane == 0) {
+            mbar_init(bar, 1);
+            mbar_init(bar + 1, 1);
+            fence_mbar_init();
 #pragma unroll
-        for (int k0 = 0; k0 < 32; k0 += 16) {
-            float2 y[16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) y[q] = __ldg(sb + 32 * (k0 + q));
-#pragma unroll
-            for (int q = 0; q < 16; ++q) f[k0 + q] = fma2(sg2, y[q], f[k0 + q]);
+            for (int h = 0; h < 2 && h < H; ++h) {
+                mbar_expect_tx(bar + h, NB * 8u);
+                bulk_g2s(ring + h * NB, tsrc + (size_t)h * NB, NB * 8u, bar + h);
+            }
         }
+        __syncwarp();
+        bool ok = true;
+#pragma unroll 1
+        for (int h = 0; h < H; ++h) {
+            const int st = h & 1;
+            if (!mbar_wait_bounded(bar + st, (uint32_t)((h >> 1) & 1))) {
+                ok = false;
+                // the copies still in flight: this stage's and, if issued, the other's
+                for (int q = h; q < H && q < h + 2; ++q) mbar_wait_bounded(bar + (q & 1), (uint32_t)((q >> 1) & 1));
+                break;
+            }
+            const float sg = (__popc(F & (uint32_t)h) & 1) ? -1.f : 1.f;
+            const float2 sg2 = make_float2(sg, sg);
+            const float2 *sb = ring + st * NB + lane;
+#pragma unroll
+            for (int k = 0; k < 32; ++k) f[k] = fma2(sg2, sb[32 * k], f[k]);
+            __syncwarp();
+            if (lane == 0 && h + 2 < H) {
+                mbar_expect_tx(bar + st, NB * 8u);
+                bulk_g2s(ring + st * NB, tsrc + (size_t)(h + 2) * NB, NB * 8u, bar + st);
+            }
+        }
+        if (!ok) {
+            if (lane == 0 && a.err_flag) atomicOr(a.err_flag, SRE_ERR_TIMEOUT);
+            return;
+        }
+        __syncwarp();
     }
     // ZR_FINE-bit transform: bits 5..9 in registers, then bits 0..4 after a
     // transpose through shared memory (padded: conflict-free both ways)
@@ -321,10 +407,31 @@ __global__ void __launch_bounds__(32 * FOLD_WARPS) zsample_fold_kernel(const Pas
     }
 }
 
+// One warp waits on an mbarrier whose expected bytes exceed the one 16-byte
+// copy issued to it, so the phase never completes: the bounded wait must give
+// up and record SRE_ERR_TIMEOUT (the copy itself has landed by then).
+__global__ void __launch_bounds__(32) wait_selftest_kernel(const float4 *src, int *err) {
+    __shared__ __align__(16) float4 buf[2];
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        mbar_expect_tx(&bar, 32u);
+        bulk_g2s(buf, src, 16u, &bar);
+    }
+    __syncwarp();
+    if (!mbar_wait_bounded(&bar, 0u) && threadIdx.x == 0) atomicOr(err, SRE_ERR_TIMEOUT);
+}
+
+cudaError_t launch_wait_selftest(const void *src16, int *err, cudaStream_t st) {
+    wait_selftest_kernel<<<1, 32, 0, st>>>(reinterpret_cast<const float4 *>(src16), err);
+    return cudaGetLastError();
+}
+
 template <int M>
 cudaError_t launch_fold(const PassArgs &a, const DrawInfo *draws, int z_per_x, unsigned long long *zs, float *cz,
                         cudaStream_t st) {
-    constexpr size_t smem = sizeof(float2) * (size_t)FOLD_WARPS * ((1 << ZR_FINE) + (1 << ZR_FINE) / 32);
+    constexpr size_t smem = FOLD_SMEM;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(zsample_fold_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,

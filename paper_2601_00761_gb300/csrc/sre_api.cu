@@ -267,6 +267,7 @@ struct McWS {
     unsigned long long *zs;
     float *cz;
     double *y, *out;
+    int *err;        // device error word (SRE_ERR_* bits)
 };
 
 void layout_mc(Arena &A, const Plan &P, int mode, long long n_x, int zpx, McWS &w) {
@@ -291,6 +292,7 @@ void layout_mc(Arena &A, const Plan &P, int mode, long long n_x, int zpx, McWS &
     w.cz = A.take<float>(nd);
     w.y = A.take<double>(6 * (size_t)n_x);
     w.out = A.take<double>(24);
+    w.err = A.take<int>(1);
 }
 
 // ------------------------------------------------ library-owned workspace
@@ -1378,6 +1380,7 @@ sre_status sre_mc(const void *psi, int N, int mode, long long n_x, int z_per_x, 
     const bool marg = mode == SRE_MC_MARGINAL;
     const unsigned long long d = 1ULL << N;
 
+    CK(cudaMemsetAsync(w.err, 0, sizeof(int), st));
     CK(launch_norm2((const float2 *)psi, N, w.scal, w.npart, st));
     count_launches(2);
     if (marg) {
@@ -1394,6 +1397,7 @@ sre_status sre_mc(const void *psi, int N, int mode, long long n_x, int z_per_x, 
     a.tile_out = w.tiles;
     a.want_ranges = marg ? 1 : 0;
     a.want_cand = 0;                 // the estimators need no nullity candidates
+    a.err_flag = w.err;
     a.rw_out = w.Wf;
     a.rw_stride = 1LL << (N - P.RL);
     const long long step = P.B < n_x ? P.B : n_x;
@@ -1430,6 +1434,8 @@ sre_status sre_mc(const void *psi, int N, int mode, long long n_x, int z_per_x, 
     double h[24];
     CK(cudaMemcpyAsync(h, w.out, 19 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(h + 20, w.scal + SCAL_NORM2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     h[21] = 0.0;
     if (marg) CK(cudaMemcpyAsync(h + 21, w.p, sizeof(double), cudaMemcpyDeviceToHost, st));   // p(0) = CDF(0)
     if (xs_dev) CK(cudaMemcpyAsync(xs_dev, w.xs, n_x * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
@@ -1439,6 +1445,7 @@ sre_status sre_mc(const void *psi, int N, int mode, long long n_x, int z_per_x, 
         CK(cudaMemcpyAsync(c_dev, w.cz, (size_t)n_x * z_per_x * sizeof(float), cudaMemcpyDeviceToDevice, st));
     CK(cudaStreamSynchronize(st));
     if (timing) CS(timer_fold(T));
+    if (herr & SRE_ERR_TIMEOUT) return fail(SRE_ETIMEOUT, "a bounded device wait of the z sampler expired");
     if (!(h[20] > 0.0)) return fail(SRE_EZERO, "psi has zero norm");
 
     init_result(out);
@@ -1646,6 +1653,24 @@ sre_status sre_mixed(const void *psi, int N, int N_A, void *workspace, size_t wo
 }
 
 unsigned long long sre_kernel_launches(void) { return g_launches.load(); }
+
+// 16 source bytes and the error word of the bounded-wait self-test
+__device__ __align__(16) int g_selftest_words[8];
+
+sre_status sre_selftest_bounded_wait(void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    void *base = nullptr;
+    CK(cudaGetSymbolAddress(&base, g_selftest_words));
+    int *words = reinterpret_cast<int *>(base);
+    CK(cudaMemsetAsync(words, 0, sizeof(int) * 8, st));
+    CK(launch_wait_selftest(words, words + 4, st));
+    count_launches(1);
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, words + 4, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (err & SRE_ERR_TIMEOUT) return fail(SRE_ETIMEOUT, "bounded wait expired (self-test: expected)");
+    return SRE_OK;
+}
 
 sre_status sre_pass_timing(int enable, double *ms_sum_host, long long *launches_host, double *bytes_host) {
     std::lock_guard<std::mutex> lk(g_timing_mu);

@@ -75,6 +75,9 @@ __host__ __device__ __forceinline__ unsigned long long insert0(unsigned long lon
     return ((v >> j) << (j + 1)) | lo;
 }
 
+// bits of the device error word
+constexpr int SRE_ERR_TIMEOUT = 1;      // a bounded wait ran out
+
 // Per-tile partial sums of the last pass (FP64): c^2, c^4, c^6, c^2 log2 c^2,
 // the two z-range weights the tile contributes to, and the FP32 nullity
 // candidate flag (some |c| above PassArgs::cand_thr).
@@ -237,7 +240,7 @@ struct PassArgs {
     const float2 *const *psi_list;
     const double *s_list;
     int precision;                     // 0: FP32 butterflies; 2, 3: split-BF16 tensor cores (FP32 tiles)
-    int *err_flag;                     // device error word (bounds checks)
+    int *err_flag;                     // device error word (SRE_ERR_* bits), or NULL
     // CTA order: 0 = tile-major (blockIdx.x = tile, y/z = family); 1 = one
     // linear grid with the family fastest, so that the families in flight
     // work on the same tile at once and share its psi lines in L2.
