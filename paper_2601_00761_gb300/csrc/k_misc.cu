@@ -326,15 +326,23 @@ cudaError_t launch_draw_x(const double *cdf, int N, long long n_x, int mode, uns
 // z-range selection: the FP32 range weights Wf[f][.] -> their inclusive FP64
 // scan W[f][.] (fixed order), then each draw k picks range r and the
 // remainder t' within it.
-__global__ void __launch_bounds__(256) zrange_select_kernel(const float *Wf, double *W, long long nr,
-                                                            long long n_fam, long long fam_base, int z_per_x,
-                                                            unsigned long long seed, unsigned long long ctr0,
-                                                            DrawInfo *draws) {
-    __shared__ double seg[257];
+// First level of the z draw for one family per CTA: the inclusive FP64
+// running sum W of the family's range weights (in range order) defines the
+// CDF; draw k picks the smallest range r with W[r] > u_k * W[nr - 1] (if
+// none, the last range with a positive step), and records the remainder of
+// the target inside it and the range's weight. W is kept implicit: thread t
+// owns the contiguous ranges [t per, (t + 1) per), the CTA scans the 256
+// chunk sums, and each chunk's end value E[t] = W[(t + 1) per - 1] is
+// formed by the same sequential additions that define W. A draw then
+// searches E in shared memory and re-forms W inside one chunk only.
+__global__ void __launch_bounds__(256) zrange_select_kernel(const float *Wf, long long nr, long long n_fam,
+                                                            long long fam_base, int z_per_x, unsigned long long seed,
+                                                            unsigned long long ctr0, DrawInfo *draws) {
+    __shared__ double seg[257];     // seg[t]: W just before chunk t
+    __shared__ double E[256];       // E[t]: W at the end of chunk t (W[-1] = 0 for empty chunks)
     const long long f = blockIdx.x;
     if (f >= n_fam) return;
     const float *wf = Wf + (size_t)f * nr;
-    double *w = W + (size_t)f * nr;
     const long long per = (nr + 255) / 256;
     const long long lo = threadIdx.x * per, hi = lo + per < nr ? lo + per : nr;
     double s = 0.0;
@@ -347,30 +355,72 @@ __global__ void __launch_bounds__(256) zrange_select_kernel(const float *Wf, dou
     }
     __syncthreads();
     double run = seg[threadIdx.x];
-    for (long long i = lo; i < hi; ++i) {
-        run += (double)wf[i];
-        w[i] = run;
-    }
+    for (long long i = lo; i < hi; ++i) run += (double)wf[i];
+    E[threadIdx.x] = run;
     __syncthreads();
-    const double total = w[nr - 1];
+    // the last chunk that holds ranges
+    const int tlast = (int)((nr - 1) / per);
+    const double total = E[tlast];
     for (int k = threadIdx.x; k < z_per_x; k += 256) {
         const double u = mc_uniform(seed, ctr0, (unsigned long long)(fam_base + f), 1ULL + (unsigned long long)k);
         const double t = u * total;
-        const unsigned long long r = cdf_search(w, (unsigned long long)nr, t);
+        unsigned long long r;
+        double wlo, wr_end;
+        if (total > t) {
+            // smallest chunk c with E[c] > t, then the smallest range in it
+            int a = 0, b = tlast;
+            while (a < b) {
+                const int mid = (a + b) >> 1;
+                if (E[mid] > t) b = mid; else a = mid + 1;
+            }
+            const long long c0 = (long long)a * per, c1 = c0 + per < nr ? c0 + per : nr;
+            double w = seg[a], prev = a > 0 ? E[a - 1] : 0.0;
+            long long i = c0;
+            for (; i < c1; ++i) {
+                const double nw = (i == c0 ? seg[a] : w) + (double)wf[i];
+                if (nw > t) { w = nw; break; }
+                prev = nw;
+                w = nw;
+            }
+            if (i == c1) i = c1 - 1;         // not reached: E[a] > t
+            r = (unsigned long long)i;
+            wlo = (i == c0) ? (a > 0 ? E[a - 1] : 0.0) : prev;
+            wr_end = w;
+        } else {
+            // target at or past the total: the last range whose running sum
+            // steps up (W[i] > W[i - 1]), else range 0
+            r = 0;
+            wlo = 0.0;
+            wr_end = 0.0;
+            bool found = false;
+            for (int c = tlast; c >= 0 && !found; --c) {
+                const long long c0 = (long long)c * per, c1 = c0 + per < nr ? c0 + per : nr;
+                double w = seg[c];
+                double before = c > 0 ? E[c - 1] : 0.0;
+                long long best = -1;
+                double bl = 0.0, bw = 0.0;
+                for (long long i = c0; i < c1; ++i) {
+                    const double pw = (i == c0) ? before : w;
+                    w = ((i == c0) ? seg[c] : w) + (double)wf[i];
+                    if (w > pw && (i > 0)) { best = i; bl = pw; bw = w; }
+                    else if (i == 0 && w > 0.0) { best = 0; bl = 0.0; bw = w; }
+                }
+                if (best >= 0) { r = (unsigned long long)best; wlo = bl; wr_end = bw; found = true; }
+            }
+            if (!found) { r = 0; wlo = 0.0; wr_end = seg[0] + (double)wf[0]; }
+        }
         DrawInfo di;
         di.range = r;
-        const double lo = r > 0 ? w[r - 1] : 0.0;
-        di.t = t - lo;
-        di.wr = w[r] - lo;
+        di.t = t - wlo;
+        di.wr = wr_end - wlo;
         di.pad = 0.0;
         draws[(size_t)(fam_base + f) * z_per_x + k] = di;
     }
 }
 
-cudaError_t launch_zrange_select(const float *Wf, double *W, long long nr, long long n_fam, long long fam_base,
-                                 int z_per_x, unsigned long long seed, unsigned long long ctr0, DrawInfo *draws,
-                                 cudaStream_t st) {
-    zrange_select_kernel<<<(unsigned)n_fam, 256, 0, st>>>(Wf, W, nr, n_fam, fam_base, z_per_x, seed, ctr0, draws);
+cudaError_t launch_zrange_select(const float *Wf, long long nr, long long n_fam, long long fam_base, int z_per_x,
+                                 unsigned long long seed, unsigned long long ctr0, DrawInfo *draws, cudaStream_t st) {
+    zrange_select_kernel<<<(unsigned)n_fam, 256, 0, st>>>(Wf, nr, n_fam, fam_base, z_per_x, seed, ctr0, draws);
     return cudaGetLastError();
 }
 

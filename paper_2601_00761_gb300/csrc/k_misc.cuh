@@ -54,9 +54,8 @@ cudaError_t launch_sum_u64(const unsigned long long *v, long long n, unsigned lo
 cudaError_t launch_scan(const double *p, unsigned long long n, double *cdf, double *bsum, cudaStream_t st);
 cudaError_t launch_draw_x(const double *cdf, int N, long long n_x, int mode, unsigned long long seed,
                           unsigned long long ctr0, unsigned long long *xs, cudaStream_t st);
-cudaError_t launch_zrange_select(const float *Wf, double *W, long long nr, long long n_fam, long long fam_base,
-                                 int z_per_x, unsigned long long seed, unsigned long long ctr0, DrawInfo *draws,
-                                 cudaStream_t st);
+cudaError_t launch_zrange_select(const float *Wf, long long nr, long long n_fam, long long fam_base, int z_per_x,
+                                 unsigned long long seed, unsigned long long ctr0, DrawInfo *draws, cudaStream_t st);
 cudaError_t launch_mc_stats(const FamMoments *fm, const float *cz, long long n_x, int z_per_x, int N, int mode,
                             double *y, double *out, cudaStream_t st);
 cudaError_t launch_norm2_multi(const float2 *const *psi_list, int n_states, int N, double *partial, int nb,

@@ -262,7 +262,6 @@ struct McWS {
     TilePartial *tiles;
     FamMoments *fm;
     float *Wf;       // range weights (FP32, one row per family of the batch)
-    double *W;       // their inclusive FP64 scan
     DrawInfo *draws;
     unsigned long long *zs;
     float *cz;
@@ -285,7 +284,6 @@ void layout_mc(Arena &A, const Plan &P, int mode, long long n_x, int zpx, McWS &
     w.fm = A.take<FamMoments>(n_x);
     const long long nr = 1LL << (P.N - P.RL);
     w.Wf = marg ? A.take<float>((size_t)B * (size_t)nr) : nullptr;
-    w.W = marg ? A.take<double>((size_t)B * (size_t)nr) : nullptr;
     const size_t nd = marg ? (size_t)n_x * (size_t)zpx : 1;
     w.draws = marg ? A.take<DrawInfo>(nd) : nullptr;
     w.zs = marg ? A.take<unsigned long long>(nd) : nullptr;
@@ -1420,7 +1418,7 @@ sre_status sre_mc(const void *psi, int N, int mode, long long n_x, int z_per_x, 
                              (marg && !fine) ? w.Wf : nullptr, nr, st));
         count_launches(1);
         if (marg) {
-            CK(launch_zrange_select(w.Wf, w.W, nr, nf, fb, z_per_x, seed, counter0, w.draws, st));
+            CK(launch_zrange_select(w.Wf, nr, nf, fb, z_per_x, seed, counter0, w.draws, st));
             count_launches(1);
             PassArgs c = b;
             c.src = w.inter;
