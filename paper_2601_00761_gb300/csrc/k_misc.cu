@@ -91,7 +91,8 @@ cudaError_t launch_norm2(const float2 *psi, int N, double *scal, double *partial
 __global__ void __launch_bounds__(256) fam_reduce_kernel(const TilePartial *tp, long long n_fam, int tiles,
                                                          const unsigned long long *xs, long long fam_base,
                                                          int N, int M_last, int RL, FamMoments *fm,
-                                                         long long fm_base, float *W, long long nr) {
+                                                         long long fm_base, float *W, long long nr,
+                                                         const unsigned long long *perm) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long f = (long long)blockIdx.x * 8 + warp;
     if (f >= n_fam) return;
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(256) fam_reduce_kernel(const TilePartial *tp, 
         c += __shfl_xor_sync(0xffffffffu, c, o);
     }
     if (lane == 0) {
-        FamMoments &o = fm[fm_base + f];
+        FamMoments &o = fm[perm ? (long long)perm[fam_base + f] : fm_base + f];
         o.m[0] = m0; o.m[1] = m1; o.m[2] = m2; o.m[3] = m3;
         o.cand = (unsigned long long)c;
     }
@@ -128,9 +129,9 @@ __global__ void __launch_bounds__(256) fam_reduce_kernel(const TilePartial *tp, 
 
 cudaError_t launch_fam_reduce(const TilePartial *tp, long long n_fam, int tiles, const unsigned long long *xs,
                               long long fam_base, int N, int M_last, int RL, FamMoments *fm, long long fm_base,
-                              float *W, long long nr, cudaStream_t st) {
+                              float *W, long long nr, cudaStream_t st, const unsigned long long *perm) {
     fam_reduce_kernel<<<(unsigned)((n_fam + 7) / 8), 256, 0, st>>>(tp, n_fam, tiles, xs, fam_base, N, M_last, RL,
-                                                                  fm, fm_base, W, nr);
+                                                                  fm, fm_base, W, nr, perm);
     return cudaGetLastError();
 }
 
@@ -337,11 +338,14 @@ cudaError_t launch_draw_x(const double *cdf, int N, long long n_x, int mode, uns
 // searches E in shared memory and re-forms W inside one chunk only.
 __global__ void __launch_bounds__(256) zrange_select_kernel(const float *Wf, long long nr, long long n_fam,
                                                             long long fam_base, int z_per_x, unsigned long long seed,
-                                                            unsigned long long ctr0, DrawInfo *draws) {
+                                                            unsigned long long ctr0, DrawInfo *draws,
+                                                            const unsigned long long *perm) {
     __shared__ double seg[257];     // seg[t]: W just before chunk t
     __shared__ double E[256];       // E[t]: W at the end of chunk t (W[-1] = 0 for empty chunks)
     const long long f = blockIdx.x;
     if (f >= n_fam) return;
+    // the family's own index: its draw stream and its draw records
+    const unsigned long long fam = perm ? perm[fam_base + f] : (unsigned long long)(fam_base + f);
     const float *wf = Wf + (size_t)f * nr;
     const long long per = (nr + 255) / 256;
     const long long lo = threadIdx.x * per, hi = lo + per < nr ? lo + per : nr;
@@ -362,7 +366,7 @@ __global__ void __launch_bounds__(256) zrange_select_kernel(const float *Wf, lon
     const int tlast = (int)((nr - 1) / per);
     const double total = E[tlast];
     for (int k = threadIdx.x; k < z_per_x; k += 256) {
-        const double u = mc_uniform(seed, ctr0, (unsigned long long)(fam_base + f), 1ULL + (unsigned long long)k);
+        const double u = mc_uniform(seed, ctr0, fam, 1ULL + (unsigned long long)k);
         const double t = u * total;
         unsigned long long r;
         double wlo, wr_end;
@@ -414,13 +418,14 @@ __global__ void __launch_bounds__(256) zrange_select_kernel(const float *Wf, lon
         di.t = t - wlo;
         di.wr = wr_end - wlo;
         di.pad = 0.0;
-        draws[(size_t)(fam_base + f) * z_per_x + k] = di;
+        draws[(size_t)fam * z_per_x + k] = di;
     }
 }
 
 cudaError_t launch_zrange_select(const float *Wf, long long nr, long long n_fam, long long fam_base, int z_per_x,
-                                 unsigned long long seed, unsigned long long ctr0, DrawInfo *draws, cudaStream_t st) {
-    zrange_select_kernel<<<(unsigned)n_fam, 256, 0, st>>>(Wf, nr, n_fam, fam_base, z_per_x, seed, ctr0, draws);
+                                 unsigned long long seed, unsigned long long ctr0, DrawInfo *draws,
+                                 const unsigned long long *perm, cudaStream_t st) {
+    zrange_select_kernel<<<(unsigned)n_fam, 256, 0, st>>>(Wf, nr, n_fam, fam_base, z_per_x, seed, ctr0, draws, perm);
     return cudaGetLastError();
 }
 

@@ -44,9 +44,11 @@ struct NullDirectArgs {
     unsigned long long *counts, *ovf, *ovf_n;
 };
 cudaError_t launch_null_direct(const NullDirectArgs &a, long long n_fam, cudaStream_t st);
+// per-family sums of a launch's tile partials into fm[fm_base + slot], or,
+// with perm (processing order -> family index), into fm[perm[fam_base + slot]]
 cudaError_t launch_fam_reduce(const TilePartial *tp, long long n_fam, int tiles, const unsigned long long *xs,
                               long long fam_base, int N, int M_last, int RL, FamMoments *fm, long long fm_base,
-                              float *W, long long nr, cudaStream_t st);
+                              float *W, long long nr, cudaStream_t st, const unsigned long long *perm = nullptr);
 cudaError_t launch_exact_totals(const FamMoments *fm, long long n_fam, double *partial, int n_part,
                                 double *out, unsigned long long *flag_list, unsigned long long *n_flag,
                                 cudaStream_t st);
@@ -55,7 +57,8 @@ cudaError_t launch_scan(const double *p, unsigned long long n, double *cdf, doub
 cudaError_t launch_draw_x(const double *cdf, int N, long long n_x, int mode, unsigned long long seed,
                           unsigned long long ctr0, unsigned long long *xs, cudaStream_t st);
 cudaError_t launch_zrange_select(const float *Wf, long long nr, long long n_fam, long long fam_base, int z_per_x,
-                                 unsigned long long seed, unsigned long long ctr0, DrawInfo *draws, cudaStream_t st);
+                                 unsigned long long seed, unsigned long long ctr0, DrawInfo *draws,
+                                 const unsigned long long *perm, cudaStream_t st);
 cudaError_t launch_mc_stats(const FamMoments *fm, const float *cz, long long n_x, int z_per_x, int N, int mode,
                             double *y, double *out, cudaStream_t st);
 cudaError_t launch_norm2_multi(const float2 *const *psi_list, int n_states, int N, double *partial, int nb,
@@ -73,8 +76,9 @@ cudaError_t launch_philox_test(const unsigned long long *ctr_key, unsigned long 
 // one warp whose mbarrier wait can only end by its bound (k_sample.cu);
 // src16: 16 readable, 16-byte aligned device bytes; err: device word
 cudaError_t launch_wait_selftest(const void *src16, int *err, cudaStream_t st);
+// z draws of a launch's families (k_sample.cu); perm as for launch_fam_reduce
 cudaError_t launch_zsample(int single, int fine, int M, const PassArgs &a, const DrawInfo *draws, int z_per_x,
-                           unsigned long long *zs, float *cz, cudaStream_t st);
+                           unsigned long long *zs, float *cz, const unsigned long long *perm, cudaStream_t st);
 
 // gates (k_gates.cu)
 struct GateRow { unsigned char op, q0, q1; };

@@ -15,7 +15,8 @@ namespace sre {
 
 template <class Cfg, int SRC, int PREC>
 __global__ void __launch_bounds__(Cfg::NT) zsample_kernel(const PassArgs a, const DrawInfo *draws, int z_per_x,
-                                                          unsigned long long *zs, float *cz) {
+                                                          unsigned long long *zs, float *cz,
+                                                          const unsigned long long *perm) {
     typedef float R;
     typedef float2 C2;
     static_assert(Cfg::G == 1, "one tile per CTA");
@@ -27,14 +28,15 @@ __global__ void __launch_bounds__(Cfg::NT) zsample_kernel(const PassArgs a, cons
     if (idx >= a.n_fam * (long long)z_per_x) return;   // uniform over the CTA
     const long long slot = idx / z_per_x;
     const int kdraw = (int)(idx - slot * z_per_x);
-    const long long gf = a.fam_base + slot;
+    const long long gf = a.fam_base + slot;                          // processing order
+    const long long of = perm ? (long long)perm[gf] : gf;           // the family's own index
     const uint32_t t = threadIdx.x;
 
     const int N = a.N, n = a.n;
     const unsigned long long x = a.xs[gf] & ((1ULL << N) - 1ULL);
     const int j = x ? 63 - __clzll((long long)x) : n;
     const unsigned long long half = 1ULL << n;
-    const DrawInfo dr = draws[(size_t)gf * z_per_x + kdraw];
+    const DrawInfo dr = draws[(size_t)of * z_per_x + kdraw];
     const int RL = Cfg::M;
     const unsigned long long zstart = dr.range << RL;
     const unsigned long long zp0 = ((zstart >> (j + 1)) << j) | (zstart & ((1ULL << j) - 1ULL));
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(Cfg::NT) zsample_kernel(const PassArgs a, cons
     __syncthreads();
     const unsigned long long before = wsum[wid] + incl - own;
     const unsigned long long total = wsum[NW];
-    const size_t out = (size_t)gf * z_per_x + kdraw;
+    const size_t out = (size_t)of * z_per_x + kdraw;
     if (T < total && before <= T && T < before + own) {
         unsigned long long run = before;
         int pick = lo + PER - 1;
@@ -138,7 +140,7 @@ __global__ void __launch_bounds__(Cfg::NT) zsample_kernel(const PassArgs a, cons
 
 template <class Cfg, int SRC, int PREC>
 cudaError_t launch_zs1(const PassArgs &a, const DrawInfo *draws, int z_per_x, unsigned long long *zs, float *cz,
-                       cudaStream_t st) {
+                       const unsigned long long *perm, cudaStream_t st) {
     const size_t smem = sizeof(float2) * (size_t)Cfg::PSIZE + sizeof(double) * ((Cfg::NT + 31) / 32 + 4);
     static bool attr = false;
     if (!attr) {
@@ -149,17 +151,17 @@ cudaError_t launch_zs1(const PassArgs &a, const DrawInfo *draws, int z_per_x, un
     }
     const long long nd = a.n_fam * (long long)z_per_x;
     dim3 grid((unsigned)(nd < 65535 ? nd : 65535), (unsigned)((nd + 65534) / 65535));
-    zsample_kernel<Cfg, SRC, PREC><<<grid, Cfg::NT, smem, st>>>(a, draws, z_per_x, zs, cz);
+    zsample_kernel<Cfg, SRC, PREC><<<grid, Cfg::NT, smem, st>>>(a, draws, z_per_x, zs, cz, perm);
     return cudaGetLastError();
 }
 
 template <class Cfg, int SRC>
 cudaError_t launch_zs(const PassArgs &a, const DrawInfo *draws, int z_per_x, unsigned long long *zs, float *cz,
-                      cudaStream_t st) {
-    if (a.precision == 0 || Cfg::T < 32) return launch_zs1<Cfg, SRC, 0>(a, draws, z_per_x, zs, cz, st);
+                      const unsigned long long *perm, cudaStream_t st) {
+    if (a.precision == 0 || Cfg::T < 32) return launch_zs1<Cfg, SRC, 0>(a, draws, z_per_x, zs, cz, perm, st);
     if constexpr (Cfg::T >= 32) {
-        if (a.precision == 2) return launch_zs1<Cfg, SRC, 2>(a, draws, z_per_x, zs, cz, st);
-        if (a.precision == 3) return launch_zs1<Cfg, SRC, 3>(a, draws, z_per_x, zs, cz, st);
+        if (a.precision == 2) return launch_zs1<Cfg, SRC, 2>(a, draws, z_per_x, zs, cz, perm, st);
+        if (a.precision == 3) return launch_zs1<Cfg, SRC, 3>(a, draws, z_per_x, zs, cz, perm, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -228,7 +230,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 template <int M>
 __global__ void __launch_bounds__(32 * FOLD_WARPS) zsample_fold_kernel(const PassArgs a, const DrawInfo *draws,
                                                                       int z_per_x, unsigned long long *zs,
-                                                                      float *cz) {
+                                                                      float *cz, const unsigned long long *perm) {
     constexpr int RL = ZR_FINE, NB = 1 << RL, H = 1 << (M - RL), SW = NB + NB / 32;
     static_assert(M > RL && RL == 10, "a warp holds 32 x 32 folded points");
     static_assert(FOLD_WSTRIDE >= SW, "the transpose and the range fit the warp's region");
@@ -239,11 +241,12 @@ __global__ void __launch_bounds__(32 * FOLD_WARPS) zsample_fold_kernel(const Pas
     if (idx >= a.n_fam * (long long)z_per_x) return;      // uniform over the warp
     const long long slot = idx / z_per_x;
     const int kdraw = (int)(idx - slot * z_per_x);
-    const long long gf = a.fam_base + slot;
+    const long long gf = a.fam_base + slot;                          // processing order
+    const long long of = perm ? (long long)perm[gf] : gf;           // the family's own index
     const int N = a.N, n = a.n;
     const unsigned long long x = a.xs[gf] & ((1ULL << N) - 1ULL);
     const int j = x ? 63 - __clzll((long long)x) : n;
-    const size_t out = (size_t)gf * z_per_x + kdraw;
+    const size_t out = (size_t)of * z_per_x + kdraw;
     const DrawInfo dr = draws[out];
     const unsigned long long zstart = dr.range << RL;
     const unsigned long long zp0 = ((zstart >> (j + 1)) << j) | (zstart & ((1ULL << j) - 1ULL));
@@ -430,7 +433,7 @@ cudaError_t launch_wait_selftest(const void *src16, int *err, cudaStream_t st) {
 
 template <int M>
 cudaError_t launch_fold(const PassArgs &a, const DrawInfo *draws, int z_per_x, unsigned long long *zs, float *cz,
-                        cudaStream_t st) {
+                        const unsigned long long *perm, cudaStream_t st) {
     constexpr size_t smem = FOLD_SMEM;
     static bool attr = false;
     if (!attr) {
@@ -442,33 +445,33 @@ cudaError_t launch_fold(const PassArgs &a, const DrawInfo *draws, int z_per_x, u
     const long long nd = a.n_fam * (long long)z_per_x;
     const long long nb = (nd + FOLD_WARPS - 1) / FOLD_WARPS;
     if (nb > 0x7fffffffLL) return cudaErrorInvalidValue;
-    zsample_fold_kernel<M><<<(unsigned)nb, 32 * FOLD_WARPS, smem, st>>>(a, draws, z_per_x, zs, cz);
+    zsample_fold_kernel<M><<<(unsigned)nb, 32 * FOLD_WARPS, smem, st>>>(a, draws, z_per_x, zs, cz, perm);
     return cudaGetLastError();
 }
 
 template <int M> using SampleSingle = TileCfg<float, M, 0, (M < 5 ? M : 5), 1>;
 
 cudaError_t launch_zsample(int single, int fine, int M, const PassArgs &a, const DrawInfo *draws, int z_per_x,
-                           unsigned long long *zs, float *cz, cudaStream_t st) {
+                           unsigned long long *zs, float *cz, const unsigned long long *perm, cudaStream_t st) {
     if (fine) {
         switch (M) {
-        case 11: return launch_fold<11>(a, draws, z_per_x, zs, cz, st);
-        case 12: return launch_fold<12>(a, draws, z_per_x, zs, cz, st);
-        case 13: return launch_fold<13>(a, draws, z_per_x, zs, cz, st);
-        case 14: return launch_fold<14>(a, draws, z_per_x, zs, cz, st);
+        case 11: return launch_fold<11>(a, draws, z_per_x, zs, cz, perm, st);
+        case 12: return launch_fold<12>(a, draws, z_per_x, zs, cz, perm, st);
+        case 13: return launch_fold<13>(a, draws, z_per_x, zs, cz, perm, st);
+        case 14: return launch_fold<14>(a, draws, z_per_x, zs, cz, perm, st);
         default: return cudaErrorInvalidValue;
         }
     }
     if (single) {
         switch (M) {
-#define C(m) case m: return launch_zs<SampleSingle<m>, SRC_PSI_FAMILY>(a, draws, z_per_x, zs, cz, st);
+#define C(m) case m: return launch_zs<SampleSingle<m>, SRC_PSI_FAMILY>(a, draws, z_per_x, zs, cz, perm, st);
         C(0) C(1) C(2) C(3) C(4) C(5) C(6) C(7) C(8) C(9) C(10) C(11) C(12) C(13) C(14)
 #undef C
         default: return cudaErrorInvalidValue;
         }
     }
     switch (M) {
-#define C(m) case m: return launch_zs<TileCfg<float, m, 0, 5, 1>, SRC_BUF>(a, draws, z_per_x, zs, cz, st);
+#define C(m) case m: return launch_zs<TileCfg<float, m, 0, 5, 1>, SRC_BUF>(a, draws, z_per_x, zs, cz, perm, st);
     C(10) C(11) C(12) C(13) C(14)
 #undef C
     default: return cudaErrorInvalidValue;

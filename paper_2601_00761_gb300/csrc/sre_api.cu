@@ -258,6 +258,7 @@ struct McWS {
     double *scal, *npart;
     double *p, *mwork, *bsum;
     unsigned long long *xs;
+    unsigned long long *xs_ord, *perm;   // the families in processing order, and their own indices
     void *inter;
     TilePartial *tiles;
     FamMoments *fm;
@@ -278,6 +279,8 @@ void layout_mc(Arena &A, const Plan &P, int mode, long long n_x, int zpx, McWS &
     w.mwork = marg ? A.take<double>(d) : nullptr;
     w.bsum = marg ? A.take<double>(d / SCAN_CHUNK + 1) : nullptr;
     w.xs = A.take<unsigned long long>(n_x);
+    w.xs_ord = P.npass > 1 ? A.take<unsigned long long>(n_x) : nullptr;
+    w.perm = P.npass > 1 ? A.take<unsigned long long>(n_x) : nullptr;
     const long long B = P.npass > 1 ? P.B : (n_x < P.B ? n_x : P.B);
     w.inter = P.npass > 1 ? (void *)A.take<char>(P.slot_bytes * (size_t)P.B) : nullptr;
     w.tiles = A.take<TilePartial>((size_t)B * (size_t)P.tiles_last);
@@ -1388,10 +1391,40 @@ sre_status sre_mc(const void *psi, int N, int mode, long long n_x, int z_per_x, 
     }
     CK(launch_draw_x(w.p, N, n_x, marg ? 1 : 0, seed, counter0, w.xs, st));
     count_launches(1);
+    // Multi-pass plans process the families in an order that lets the
+    // families of one launch share psi in L2: by the top bit j of x (the same
+    // rows b for every family with that j), then by x's bits over the first
+    // strided pass's tile index (partner tile = tile ^ those bits, so the
+    // partner tiles of a launch span a few aligned blocks), then by index.
+    // Each family keeps its own index for its moments, draw stream and
+    // outputs, so no result depends on the order.
+    const unsigned long long *xs_run = w.xs, *perm = nullptr;
+    if (P.npass > 1) {
+        std::vector<unsigned long long> hx((size_t)n_x), order((size_t)n_x), hxo((size_t)n_x);
+        CK(cudaMemcpyAsync(hx.data(), w.xs, sizeof(unsigned long long) * (size_t)n_x, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const int cb = P.ms[0] - P.K[0], tb = P.lo[0] - cb;
+        auto key = [&](unsigned long long x) {
+            const unsigned long long j = x ? (unsigned long long)(63 - __builtin_clzll(x)) : 0ULL;
+            return (j << 40) | ((x >> cb) & ((1ULL << tb) - 1ULL));
+        };
+        for (long long i = 0; i < n_x; ++i) order[(size_t)i] = (unsigned long long)i;
+        std::sort(order.begin(), order.end(), [&](unsigned long long p, unsigned long long q) {
+            const unsigned long long kp = key(hx[p]), kq = key(hx[q]);
+            return kp != kq ? kp < kq : p < q;
+        });
+        for (long long i = 0; i < n_x; ++i) hxo[(size_t)i] = hx[order[(size_t)i]];
+        CK(cudaMemcpyAsync(w.xs_ord, hxo.data(), sizeof(unsigned long long) * (size_t)n_x, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(w.perm, order.data(), sizeof(unsigned long long) * (size_t)n_x, cudaMemcpyHostToDevice,
+                           st));
+        CK(cudaStreamSynchronize(st));   // the host vectors go out of scope
+        xs_run = w.xs_ord;
+        perm = w.perm;
+    }
 
     PassArgs a = base_args(P, psi, w.scal);
     a.precision = prec_code(o);
-    a.xs = w.xs;
+    a.xs = xs_run;
     a.tile_out = w.tiles;
     a.want_ranges = marg ? 1 : 0;
     a.want_cand = 0;                 // the estimators need no nullity candidates
@@ -1414,16 +1447,16 @@ sre_status sre_mc(const void *psi, int N, int mode, long long n_x, int z_per_x, 
         b.fam_base = fb;
         b.n_fam = nf;
         CS(run_transform(P, b, SRC_PSI_FAMILY, DST_MOMENTS, w.inter, st, (timing && nf == step) ? &T : nullptr));
-        CK(launch_fam_reduce(w.tiles, nf, (int)P.tiles_last, w.xs, fb, N, P.M_last, P.RL, w.fm, fb,
-                             (marg && !fine) ? w.Wf : nullptr, nr, st));
+        CK(launch_fam_reduce(w.tiles, nf, (int)P.tiles_last, xs_run, fb, N, P.M_last, P.RL, w.fm, fb,
+                             (marg && !fine) ? w.Wf : nullptr, nr, st, perm));
         count_launches(1);
         if (marg) {
-            CK(launch_zrange_select(w.Wf, nr, nf, fb, z_per_x, seed, counter0, w.draws, st));
+            CK(launch_zrange_select(w.Wf, nr, nf, fb, z_per_x, seed, counter0, w.draws, perm, st));
             count_launches(1);
             PassArgs c = b;
             c.src = w.inter;
             c.lo_g = 0;
-            CK(launch_zsample(P.npass == 1, fine ? 1 : 0, P.M_last, c, w.draws, z_per_x, w.zs, w.cz, st));
+            CK(launch_zsample(P.npass == 1, fine ? 1 : 0, P.M_last, c, w.draws, z_per_x, w.zs, w.cz, perm, st));
             count_launches(1);
         }
     }
