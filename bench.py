@@ -314,7 +314,8 @@ def run_cuda(a):
     traffic = tpf * fam_per_launch if (tpf is not None and fam_per_launch) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic,
-                "traffic_note": "ncu dram read+write of a 32-family capture scaled to the launch's families "
+                "traffic_note": "ncu dram read+write per family, mean over the 32 strided launches of a full-size "
+                                "step (one-pass capture), times the launch's families "
                                 "(profiles/strided_pass_n24.md)" if traffic else None, "kernel": ["strided pass 0 (reads psi, writes the packed intermediate)",
                                             "row pass (reads the intermediate, fused moments)"][min(dom, 1)]
                 if npass == 2 else f"pass {dom}",
