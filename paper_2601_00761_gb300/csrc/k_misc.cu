@@ -327,96 +327,119 @@ cudaError_t launch_draw_x(const double *cdf, int N, long long n_x, int mode, uns
 // z-range selection: the FP32 range weights Wf[f][.] -> their inclusive FP64
 // scan W[f][.] (fixed order), then each draw k picks range r and the
 // remainder t' within it.
-// First level of the z draw for one family per CTA: the inclusive FP64
-// running sum W of the family's range weights (in range order) defines the
-// CDF; draw k picks the smallest range r with W[r] > u_k * W[nr - 1] (if
-// none, the last range with a positive step), and records the remainder of
-// the target inside it and the range's weight. W is kept implicit: thread t
-// owns the contiguous ranges [t per, (t + 1) per), the CTA scans the 256
-// chunk sums, and each chunk's end value E[t] = W[(t + 1) per - 1] is
-// formed by the same sequential additions that define W. A draw then
-// searches E in shared memory and re-forms W inside one chunk only.
+// First level of the z draw for one family per CTA. Thread t owns the
+// contiguous ranges [t per, (t + 1) per) ("chunk" t). The FP64 CDF is
+// C(i) = S_t + (w_lo + ... + w_i) for i in chunk t, summed in range order from
+// the chunk's start S_t, where S_t is the inclusive scan of the chunk sums
+// (each chunk summed as four interleaved partial sums, the scan by warp
+// shuffles: short FP64 dependency chains on a narrow FP64 pipe). Draw k picks
+// the chunk a with S_a <= t < S_{a+1}, t = u_k S_256, then the smallest range
+// r of it with C(r) > t; if rounding leaves C below t at the chunk's end (or t
+// reaches the total), the last range of positive weight is taken and its
+// remainder is clamped by the sampler. It records t - C(r - 1) and the
+// range's weight C(r) - C(r - 1). Rows of at most ZSEL_STAGE_MAX ranges (a
+// power of two) are first staged in shared memory by coalesced loads, with
+// one padding word per chunk so the chunk-wise reads are free of bank
+// conflicts.
+constexpr long long ZSEL_STAGE_MAX = 16384;
+template <bool STAGED>
 __global__ void __launch_bounds__(256) zrange_select_kernel(const float *Wf, long long nr, long long n_fam,
                                                             long long fam_base, int z_per_x, unsigned long long seed,
                                                             unsigned long long ctr0, DrawInfo *draws,
                                                             const unsigned long long *perm) {
-    __shared__ double seg[257];     // seg[t]: W just before chunk t
-    __shared__ double E[256];       // E[t]: W at the end of chunk t (W[-1] = 0 for empty chunks)
+    __shared__ double seg[257];     // seg[t] = S_t, seg[256] = the total
+    __shared__ double wsum[8];
+    extern __shared__ float swf[];
     const long long f = blockIdx.x;
     if (f >= n_fam) return;
     // the family's own index: its draw stream and its draw records
     const unsigned long long fam = perm ? perm[fam_base + f] : (unsigned long long)(fam_base + f);
-    const float *wf = Wf + (size_t)f * nr;
     const long long per = (nr + 255) / 256;
-    const long long lo = threadIdx.x * per, hi = lo + per < nr ? lo + per : nr;
-    double s = 0.0;
-    for (long long i = lo; i < hi; ++i) s += (double)wf[i];
-    seg[threadIdx.x + 1] = s;
+    const float *wrow = Wf + (size_t)f * nr;
+    const int lp = STAGED ? 31 - __clz((int)per) : 0;
+    if constexpr (STAGED) {
+        for (uint32_t i = threadIdx.x; i < (uint32_t)nr; i += 256) swf[i + (i >> lp)] = wrow[i];
+        __syncthreads();
+    }
+    auto wf = [&](long long i) -> double {
+        if constexpr (STAGED) return (double)swf[(uint32_t)i + ((uint32_t)i >> lp)];
+        else return (double)wrow[i];
+    };
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long lo = tid * per, hi = lo + per < nr ? lo + per : nr;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    long long i = lo;
+    for (; i + 3 < hi; i += 4) {
+        a0 += wf(i);
+        a1 += wf(i + 1);
+        a2 += wf(i + 2);
+        a3 += wf(i + 3);
+    }
+    for (; i < hi; ++i) a0 += wf(i);
+    double v = (a0 + a1) + (a2 + a3);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    if (lane == 31) wsum[warp] = v;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        seg[0] = 0.0;
-        for (int t = 1; t <= 256; ++t) seg[t] += seg[t - 1];
+    if (warp == 0) {
+        double w = lane < 8 ? wsum[lane] : 0.0;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const double u = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += u;
+        }
+        if (lane < 8) wsum[lane] = w;
     }
     __syncthreads();
-    double run = seg[threadIdx.x];
-    for (long long i = lo; i < hi; ++i) run += (double)wf[i];
-    E[threadIdx.x] = run;
+    seg[tid + 1] = v + (warp > 0 ? wsum[warp - 1] : 0.0);
+    if (tid == 0) seg[0] = 0.0;
     __syncthreads();
-    // the last chunk that holds ranges
-    const int tlast = (int)((nr - 1) / per);
-    const double total = E[tlast];
-    for (int k = threadIdx.x; k < z_per_x; k += 256) {
+    const int tlast = (int)((nr - 1) / per);     // the last chunk that holds ranges
+    const double total = seg[256];
+    for (int k = tid; k < z_per_x; k += 256) {
         const double u = mc_uniform(seed, ctr0, fam, 1ULL + (unsigned long long)k);
         const double t = u * total;
-        unsigned long long r;
-        double wlo, wr_end;
+        long long r = -1;
+        double clo = 0.0, chi = 0.0;
         if (total > t) {
-            // smallest chunk c with E[c] > t, then the smallest range in it
-            int a = 0, b = tlast;
+            int a = 0, b = tlast;                  // smallest a with S_{a+1} > t
             while (a < b) {
                 const int mid = (a + b) >> 1;
-                if (E[mid] > t) b = mid; else a = mid + 1;
+                if (seg[mid + 1] > t) b = mid; else a = mid + 1;
             }
             const long long c0 = (long long)a * per, c1 = c0 + per < nr ? c0 + per : nr;
-            double w = seg[a], prev = a > 0 ? E[a - 1] : 0.0;
-            long long i = c0;
-            for (; i < c1; ++i) {
-                const double nw = (i == c0 ? seg[a] : w) + (double)wf[i];
-                if (nw > t) { w = nw; break; }
-                prev = nw;
-                w = nw;
+            double run = seg[a], lastp_lo = 0.0, lastp_hi = 0.0;
+            long long lastp = -1;
+            for (long long q = c0; q < c1; ++q) {
+                const double w = wf(q), nrun = run + w;
+                if (w > 0.0) { lastp = q; lastp_lo = run; lastp_hi = nrun; }
+                if (nrun > t) { r = q; clo = run; chi = nrun; break; }
+                run = nrun;
             }
-            if (i == c1) i = c1 - 1;         // not reached: E[a] > t
-            r = (unsigned long long)i;
-            wlo = (i == c0) ? (a > 0 ? E[a - 1] : 0.0) : prev;
-            wr_end = w;
-        } else {
-            // target at or past the total: the last range whose running sum
-            // steps up (W[i] > W[i - 1]), else range 0
-            r = 0;
-            wlo = 0.0;
-            wr_end = 0.0;
-            bool found = false;
-            for (int c = tlast; c >= 0 && !found; --c) {
+            if (r < 0 && lastp >= 0) { r = lastp; clo = lastp_lo; chi = lastp_hi; }
+        }
+        if (r < 0) {
+            // t at or past the total (or a chunk without weight): the last
+            // range of positive weight
+            for (int c = tlast; c >= 0 && r < 0; --c) {
+                if (!(seg[c + 1] > seg[c])) continue;
                 const long long c0 = (long long)c * per, c1 = c0 + per < nr ? c0 + per : nr;
-                double w = seg[c];
-                double before = c > 0 ? E[c - 1] : 0.0;
-                long long best = -1;
-                double bl = 0.0, bw = 0.0;
-                for (long long i = c0; i < c1; ++i) {
-                    const double pw = (i == c0) ? before : w;
-                    w = ((i == c0) ? seg[c] : w) + (double)wf[i];
-                    if (w > pw && (i > 0)) { best = i; bl = pw; bw = w; }
-                    else if (i == 0 && w > 0.0) { best = 0; bl = 0.0; bw = w; }
+                double run = seg[c];
+                for (long long q = c0; q < c1; ++q) {
+                    const double w = wf(q), nrun = run + w;
+                    if (w > 0.0) { r = q; clo = run; chi = nrun; }
+                    run = nrun;
                 }
-                if (best >= 0) { r = (unsigned long long)best; wlo = bl; wr_end = bw; found = true; }
             }
-            if (!found) { r = 0; wlo = 0.0; wr_end = seg[0] + (double)wf[0]; }
+            if (r < 0) { r = 0; clo = 0.0; chi = wf(0); }
         }
         DrawInfo di;
-        di.range = r;
-        di.t = t - wlo;
-        di.wr = wr_end - wlo;
+        di.range = (unsigned long long)r;
+        di.t = t - clo;
+        di.wr = chi - clo;
         di.pad = 0.0;
         draws[(size_t)fam * z_per_x + k] = di;
     }
@@ -425,7 +448,21 @@ __global__ void __launch_bounds__(256) zrange_select_kernel(const float *Wf, lon
 cudaError_t launch_zrange_select(const float *Wf, long long nr, long long n_fam, long long fam_base, int z_per_x,
                                  unsigned long long seed, unsigned long long ctr0, DrawInfo *draws,
                                  const unsigned long long *perm, cudaStream_t st) {
-    zrange_select_kernel<<<(unsigned)n_fam, 256, 0, st>>>(Wf, nr, n_fam, fam_base, z_per_x, seed, ctr0, draws, perm);
+    if (nr <= ZSEL_STAGE_MAX && (nr & (nr - 1)) == 0) {
+        const size_t smem = sizeof(float) * (size_t)(nr + 256 + 1);
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(zrange_select_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)(sizeof(float) * (ZSEL_STAGE_MAX + 257)));
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        zrange_select_kernel<true><<<(unsigned)n_fam, 256, smem, st>>>(Wf, nr, n_fam, fam_base, z_per_x, seed, ctr0,
+                                                                       draws, perm);
+    } else {
+        zrange_select_kernel<false><<<(unsigned)n_fam, 256, 0, st>>>(Wf, nr, n_fam, fam_base, z_per_x, seed, ctr0,
+                                                                     draws, perm);
+    }
     return cudaGetLastError();
 }
 
