@@ -331,8 +331,21 @@ __device__ __forceinline__ void fine_range_weights(float2 s2, unsigned long long
     }
 }
 
-template <class Cfg, int SRC, int DST, int PREC = 0>
-__global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const PassArgs a) {
+// Families a CTA of a psi-reading strided pass transforms in turn, on the
+// same tile. Neighbouring families in the sorted order share their own-half
+// rows, so the later ones find them in L1 (N = 24: 2.79 ms per 128-family
+// launch with 4, 2.83 with 2, 2.97 with 1; 8 gains nothing over 4).
+#ifndef SRE_STRIDED_FPC
+#define SRE_STRIDED_FPC 4
+#endif
+template <class Cfg, int SRC> struct FamPerCta {
+    static constexpr int v = (SRC == SRC_PSI_FAMILY && Cfg::G == 1 && Cfg::LO > 0) ? SRE_STRIDED_FPC : 1;
+};
+
+// One tile of one family (the rep-th family of the CTA); false when the CTA
+// has no rep-th family.
+template <class Cfg, int SRC, int DST, int PREC>
+__device__ __forceinline__ bool fwht_pass_body(const PassArgs &a, int rep) {
     typedef typename Cfg::Real R;
     typedef typename Cfg::C2 C2;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -350,9 +363,12 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const Pas
         slot = (long long)blockIdx.x * Cfg::G + grp;
         tile = 0;
     } else if (a.fam_fast) {
+        constexpr int FPC = FamPerCta<Cfg, SRC>::v;
         const unsigned long long L = blockIdx.x;
-        slot = (long long)(L % (unsigned long long)a.n_fam);
-        tile = L / (unsigned long long)a.n_fam;
+        const unsigned long long np = ((unsigned long long)a.n_fam + FPC - 1) / FPC;
+        slot = (long long)(L % np) * FPC + rep;
+        tile = L / np;
+        if (rep > 0 && slot >= a.n_fam) return false;
     } else {
         slot = (long long)blockIdx.y + 65535LL * (long long)blockIdx.z;
         tile = blockIdx.x;
@@ -560,7 +576,27 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const Pas
             tp.cand = (cand && omx > a.cand_thr * a.cand_thr) ? 1u : 0u;
         }
     }
+    return true;
 }
+
+template <class Cfg, int SRC, int DST, int PREC = 0>
+__global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const PassArgs a) {
+    constexpr int FPC = FamPerCta<Cfg, SRC>::v;
+    if constexpr (FPC == 1) {
+        fwht_pass_body<Cfg, SRC, DST, PREC>(a, 0);
+    } else {
+        if (!a.fam_fast) {
+            fwht_pass_body<Cfg, SRC, DST, PREC>(a, 0);
+            return;
+        }
+#pragma unroll 1
+        for (int r = 0; r < FPC; ++r) {
+            if (r) __syncthreads();                 // the tile buffer is reused
+            if (!fwht_pass_body<Cfg, SRC, DST, PREC>(a, r)) break;
+        }
+    }
+}
+
 
 template <class Cfg, int SRC, int DST, int PREC = 0>
 cudaError_t launch_cfg(const PassArgs &a, int tiles, cudaStream_t st) {
@@ -583,8 +619,9 @@ cudaError_t launch_cfg(const PassArgs &a, int tiles, cudaStream_t st) {
         const long long total = nf * (long long)tiles;
         if ((SRC == SRC_PSI_FAMILY || SRC == SRC_PSI_Q) && nf > 1 && tiles > 1 &&
             total < 0x7fffffffLL) {
+            constexpr int FPC = FamPerCta<Cfg, SRC>::v;
             b.fam_fast = 1;
-            grid = dim3((unsigned)total, 1, 1);
+            grid = dim3((unsigned)(((nf + FPC - 1) / FPC) * (long long)tiles), 1, 1);
         } else {
             grid = dim3((unsigned)tiles, (unsigned)(nf < 65535 ? nf : 65535), (unsigned)((nf + 65534) / 65535));
         }
