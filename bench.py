@@ -518,6 +518,16 @@ def run_precondition(a):
     sre.apply_two_qubit_gates(after_state, mats, pairs)
     after = sre.sre_mc(after_state, sre.SRE_MC_UNIFORM, n_x, 1, seed=N)
     m2 = (N // 2) * math.log2(4 / 3)
+    # r_2 against the preconditioner's depth N_C (prefixes of the same circuit)
+    sweep = []
+    n_sweep = min(n_x, 8192)
+    for depth in (0, 2, 4, 8, 16, 24, 32, 2 * N):
+        st_ = psi.clone()
+        if depth:
+            mk, pk = inputs.brickwall_circuit(N, depth, "clifford", 30 + N)
+            sre.apply_two_qubit_gates(st_, mk, pk)
+        r = sre.sre_mc(st_, sre.SRE_MC_UNIFORM, n_sweep, 1, seed=N + 1)
+        sweep.append({"layers": depth, "r2": r["r2"], "M2": r["M"][1], "err_M2": r["err_M"][1]})
     line = {"metric": f"brick-wall Clifford preconditioner (depth 2N) on psi at N={N}, two-qubit gates applied per second",
             "value": len(pairs) / (ms / 1e3), "unit": "gates/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": ms,
@@ -537,7 +547,8 @@ def run_precondition(a):
             "study": {"M2_closed_form": m2,
                       "before": {"r2": before["r2"], "M2": before["M"][1], "err_M2": before["err_M"][1]},
                       "after": {"r2": after["r2"], "M2": after["M"][1], "err_M2": after["err_M"][1]},
-                      "r2_closed_form_before": r2_psi_m(N)}}
+                      "r2_closed_form_before": r2_psi_m(N),
+                      "r2_vs_layers": {"n_x": n_sweep, "points": sweep}}}
     print(json.dumps(line), flush=True)
     return 0
 
