@@ -4,16 +4,24 @@
 // in FP64. A family flagged by the FP32 sweep (some |c| near 1) is recounted
 // at the packed z' an FP32 candidate pass listed for it: every other z' holds
 // only |c| below the candidate threshold, which lies more than 1e-4 (far
-// beyond the FP32 error) under 1 - eps. For the listed z',
+// beyond the FP32 error) under 1 - eps. For a packed z',
 //   H(z') = sum_g h(g) (-1)^{popc(g & z')},   g < 2^(N-1),
 // with h(g) = conj psi(b ^ x) psi(b), b = g with 0 inserted at bit j (the top
 // bit of x), or h(g) = (|psi(g)|^2, |psi(g + 2^(N-1))|^2) for x = 0: the same
-// packed transform the sweep evaluates, here one output at a time. The pair
+// packed transform the sweep evaluates, here at chosen outputs. The pair
 // (c(z0), c(z1)) follows from H(z') as in the transform (up to signs, which
-// the count ignores). Each family costs 2^(N-1) (4 + 2k) FP64 operations for k
-// listed z', against about 2^(N-1) (2N + 8) for a full FP64 transform, so
-// families with more than kdirect candidates are appended to an overflow list
-// and recounted by the transform instead.
+// the count ignores). Routes, per family (one CTA each):
+//  - coset: the listed z' lie in z'_0 + span(v_1..v_m), m <= 6 (stabilizer
+//    structure). One sweep over g accumulates h(g) (-1)^{g.z'_0} into 2^m bins
+//    keyed by the parities g.v_i, and an m-bit WHT of the bins gives H on the
+//    whole coset: 6 FP64 operations per point for any number of candidates.
+//  - direct: wider spans with at most kdirect candidates: H at each listed z'
+//    by its own signed sum, 4 + 2k operations per point for k candidates.
+//  - overflow: the rest (or more than cand_max candidates, the list then being
+//    incomplete) is appended to a list for the FP64 transform, about 2N + 12
+//    operations per point.
+// Points of a coset that were not listed lie below the threshold and count
+// nothing, so every route counts exactly the FP64 decisions.
 #include "k_misc.cuh"
 
 namespace sre {

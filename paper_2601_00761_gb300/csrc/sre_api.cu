@@ -493,8 +493,8 @@ sre_status run_marginal(const void *psi, int N, const double *scal, double *p, d
 }
 
 // Recount of the n flagged families xs (F, with the state in the high bits
-// when a32.psi_list is set): counts[i] per family from the direct FP64 sums;
-// the families with more than null_kdirect(N) candidates land in ovf
+// when a32.psi_list is set): counts[i] per family from the coset or direct
+// FP64 sums (k_null.cu); the families that neither route takes land in ovf
 // (*n_ovf of them) with their FP64-transform counts in counts2.
 sre_status null_recount(const Plan &P, const Plan &P64, const PassArgs &a32, const PassArgs &a64,
                         const unsigned long long *xs, long long n, double eps, const NullWS &w, cudaStream_t st,
