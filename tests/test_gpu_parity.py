@@ -484,6 +484,38 @@ def test_mc_marginal_fine_ranges(sre, k_low):
     assert n_exact >= 0.9 * n_total
 
 
+@pytest.mark.parametrize("radix", [11, 12, 14])
+def test_mc_marginal_fold_widths(sre, radix):
+    """Last-pass tiles of 2^11, 2^12 and 2^14 points: each draw folds 2, 4
+    or 16 blocks of 2^10 outputs through the sampler's bulk-copy ring. Draws
+    against the oracle's inverse CDF within the propagated bound, sampled c
+    against brute force."""
+    N = 16
+    plan = sre.sre_make_plan(N, radix_log2=radix)
+    assert plan["pass_bits"][-1] == radix and plan["range_log2"] == 10
+    psi = inputs.haar_state(N, 950 + radix)
+    n_x, zpx = 12, 16
+    r = sre.sre_mc(dev(psi), sre.SRE_MC_MARGINAL, n_x, zpx, seed=7, return_samples=True, radix_log2=radix)
+    xs = r["xs"].cpu().numpy().astype(np.uint64)
+    zs = r["zs"].cpu().numpy().astype(np.uint64).reshape(n_x, zpx)
+    c = r["c"].cpu().numpy().reshape(n_x, zpx)
+    ref = oracle.mc_marginal(psi, n_x, zpx, 7, 0)
+    assert np.array_equal(xs, ref["xs"])
+    ref_zs = ref["zs"].reshape(n_x, zpx)
+    n_exact = n_total = 0
+    for i in range(n_x):
+        cf = oracle.family_spectrum(psi, int(xs[i]))
+        cg = sre.sre_family_spectrum(dev(psi), int(xs[i]), radix_log2=radix).cpu().numpy().astype(np.float64)
+        for k in range(zpx):
+            u = oracle.mc_draw(7, 0, i, 1 + k)
+            ok, exact = draw_within_bound(int(zs[i, k]), int(ref_zs[i, k]), cf * cf, cg * cg, u, 10)
+            assert ok, (i, k, int(zs[i, k]), int(ref_zs[i, k]))
+            n_exact += exact
+            n_total += 1
+            assert abs(c[i, k] - cf[int(zs[i, k])]) < TOL_C
+    assert n_exact >= 0.9 * n_total
+
+
 # ----------------------------------------------------------------- gates
 @pytest.mark.parametrize("N,n", [(1, 20), (3, 40), (5, 60), (8, 120), (12, 200), (14, 200), (17, 300)])
 def test_gates_vs_oracle(sre, N, n):
