@@ -367,16 +367,34 @@ def run_cuda(a):
         xs_h = torch.empty(n_x, dtype=torch.int64).pin_memory()
         zs_h = torch.empty(n_x * zpx, dtype=torch.int64).pin_memory()
         cs_h = torch.empty(n_x * zpx, dtype=torch.float32).pin_memory()
-        psi_dev2 = torch.empty_like(psi)
+        # Every step uploads its state from pinned host memory and reads its
+        # samples back. The upload of step i + 1 runs on a copy stream into the
+        # other of two device buffers while step i computes; all of them lie
+        # inside the timed region.
+        bufs = [torch.empty_like(psi), torch.empty_like(psi)]
+        cstream = torch.cuda.Stream()
+        copied = [torch.cuda.Event(), torch.cuda.Event()]
+        used = [torch.cuda.Event(), torch.cuda.Event()]
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
+        cstream.wait_event(e0)
+        with torch.cuda.stream(cstream):
+            bufs[0].copy_(psi_host, non_blocking=True)
+            copied[0].record(cstream)
         for i in range(a.steps):
-            psi_dev2.copy_(psi_host, non_blocking=True)
-            sre.sre_mc(psi_dev2, sre.SRE_MC_MARGINAL, n_x, zpx, seed=24,
+            b = i % 2
+            stream.wait_event(copied[b])
+            if i + 1 < a.steps:
+                cstream.wait_event(used[1 - b])
+                with torch.cuda.stream(cstream):
+                    bufs[1 - b].copy_(psi_host, non_blocking=True)
+                    copied[1 - b].record(cstream)
+            sre.sre_mc(bufs[b], sre.SRE_MC_MARGINAL, n_x, zpx, seed=24,
                        counter0=base_ctr + (1 << 30) + i * n_x, workspace=ws, outputs=(xs, zs, cs), **kw)
+            used[b].record(stream)
             xs_h.copy_(xs, non_blocking=True)
             zs_h.copy_(zs, non_blocking=True)
             cs_h.copy_(cs, non_blocking=True)
