@@ -55,24 +55,44 @@ def parse():
     return ap.parse_args()
 
 
-def profiled_traffic(N, dom_pass):
-    """DRAM bytes per family of the dominant kernel from the committed ncu
-    summary (profiles/strided_pass_n24.md), or None when that summary is for
-    another kernel or the kernel's sources changed since it was captured."""
+TRAFFIC_SOURCES = ("k_pass.cuh", "sre_internal.cuh", "k_pass_f32_multi.cu", "k_pass_dispatch.cuh")
+
+
+def kernel_source_hash():
+    """First 16 hex digits of the SHA-256 over the pass kernel's sources: the
+    key under which profiles/traffic.json records a capture."""
     import hashlib
-    if N != 24 or dom_pass != 0:
-        return None
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2601_00761_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(N, dom_pass):
+    """ncu DRAM bytes (read + write) per family of pass `dom_pass` at N, from
+    profiles/traffic.json (a small-case capture, scaled per family), or None
+    when no capture exists for that pass or the kernel's sources changed since
+    it was taken."""
     try:
-        txt = open(os.path.join(ROOT, "profiles", "strided_pass_n24.md")).read()
-        vals = dict(l.split(": ", 1) for l in txt.splitlines() if l.startswith(("traffic_bytes", "source_sha")))
-        h = hashlib.sha256()
-        for f in ("k_pass.cuh", "sre_internal.cuh", "k_pass_f32_multi.cu", "k_pass_dispatch.cuh"):
-            h.update(open(os.path.join(ROOT, "paper_2601_00761_gb300", "csrc", f), "rb").read())
-        if h.hexdigest()[:16] != vals["source_sha256_16"].strip():
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)
+        e = rec["captures"][f"N{N}_pass{dom_pass}"]
+        if e["source_sha256_16"] != kernel_source_hash():
             return None
-        return float(vals["traffic_bytes_per_family"])
+        return float(e["dram_bytes_per_family"]), e
     except Exception:
         return None
+
+
+def dram_min_bytes(N, dom_pass, npass, fam):
+    """Bytes pass `dom_pass` must move through DRAM per launch of `fam`
+    families: pass 0 reads psi once per launch (the families of a launch share
+    its lines in L2) and writes the 4 B-per-string packed intermediate; a later
+    pass reads the intermediate (and writes it again unless it is the last)."""
+    d = float(2 ** N)
+    if dom_pass == 0:
+        return 8.0 * d + 4.0 * d * fam
+    return 4.0 * d * fam * (1 if dom_pass == npass - 1 else 2)
 
 
 def peaks():
@@ -114,12 +134,13 @@ class Clocks:
     def __init__(self, gpu_index: int):
         self.p = None
         self.idx = gpu_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = None
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
+            import tempfile
+            fd, self.path = tempfile.mkstemp(prefix="sre_clocks_", suffix=".csv")
+            self.f = os.fdopen(fd, "w")
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
                                        "--format=csv,noheader,nounits", "-lms", "200"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
@@ -136,8 +157,13 @@ class Clocks:
             self.p.kill()
         self.f.close()
         sm, mx, reasons = [], 0.0, set()
+        lines = open(self.path).read().splitlines()
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in lines:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -307,22 +333,38 @@ def run_cuda(a):
     shares = [timing["ms_sum"][p] for p in range(npass)]
     dom = int(np.argmax(shares))
     avg_ms = timing["ms_sum"][dom] / max(1, timing["launches"][dom])
-    achieved = timing["bytes_per_launch"][dom] / (avg_ms / 1e3) / 1e9
+    survey_bytes = timing["bytes_per_launch"][dom]          # 8 B psi per string per family (+ 4 B out)
+    fam_launch = max(1, round(n_x / max(1, timing["launches"][dom] / a.steps)))
+    min_bytes = dram_min_bytes(N, dom, npass, fam_launch)
     step_bytes = sum(timing["bytes_per_launch"][p] * timing["launches"][p] for p in range(npass)) / a.steps
-    fam_per_launch = timing["bytes_per_launch"][dom] / (12.0 * 2 ** N) if dom == 0 else None
-    tpf = profiled_traffic(N, dom) if not (a.radix or a.tile or a.x_batch) else None
-    traffic = tpf * fam_per_launch if (tpf is not None and fam_per_launch) else None
+    tp = profiled_traffic(N, dom) if not (a.radix or a.tile or a.x_batch) else None
+    traffic = tp[0] * fam_launch if tp else None
+    # achieved: the bytes DRAM moved per launch (ncu, small-case capture scaled
+    # to the launch's families) over the live CUDA-event launch time; without a
+    # capture for the current kernel, the DRAM-minimal bytes of the launch
+    basis = traffic if traffic is not None else min_bytes
+    achieved = basis / (avg_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic,
-                "traffic_note": "ncu dram read+write per family, mean over the 32 strided launches of a full-size "
-                                "step (one-pass capture), times the launch's families "
-                                "(profiles/strided_pass_n24.md)" if traffic else None, "kernel": ["strided pass 0 (reads psi, writes the packed intermediate)",
-                                            "row pass (reads the intermediate, fused moments)"][min(dom, 1)]
+                "achieved_basis": ("ncu dram__bytes_read+write per family (small-case capture, "
+                                   "profiles/traffic.json) x families per launch") if traffic is not None else
+                                  "DRAM-minimal bytes per launch (no ncu capture for the current kernel sources)",
+                "dram_min_bytes_per_launch": min_bytes,
+                "frac_dram_min": min_bytes / (avg_ms / 1e3) / 1e9 / hbm,
+                "survey_bytes_per_launch": survey_bytes,
+                "frac_algorithmic": survey_bytes / (avg_ms / 1e3) / 1e9 / hbm,
+                "frac_algorithmic_note": "16 B per string counted with psi read from DRAM by every family; "
+                                         "the families of a launch share psi in L2, so this exceeds 1",
+                "traffic_capture": tp[1].get("capture") if tp else None,
+                "kernel": ["strided pass 0 (reads psi, writes the packed intermediate)",
+                           "row pass (reads the intermediate, fused moments)"][min(dom, 1)]
                 if npass == 2 else f"pass {dom}",
+                "families_per_launch": fam_launch,
                 "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                "avg_launch_ms": avg_ms, "bytes_per_launch": timing["bytes_per_launch"][dom],
-                "pass_ms_share": [s / sum(shares) for s in shares],
-                "step_algorithmic_GBps": step_bytes / (ms / a.steps / 1e3) / 1e9 / world * world}
+                "avg_launch_ms": avg_ms,
+                "pass_avg_launch_ms": [timing["ms_sum"][p] / max(1, timing["launches"][p]) for p in range(npass)],
+                "pass_ms_share": [s_ / sum(shares) for s_ in shares],
+                "step_algorithmic_GBps": step_bytes / (ms / a.steps / 1e3) / 1e9}
 
     # the split-BF16 tensor-core form on the same workload (BF16X3: FP32-level accuracy)
     tc = None

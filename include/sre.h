@@ -296,6 +296,12 @@ SRE_API sre_status sre_philox_blocks(const unsigned long long *ctr_key_dev, unsi
  * (every entry point counts its launches). Host only. */
 SRE_API unsigned long long sre_kernel_launches(void);
 
+/* Number of device allocations (cudaMalloc) this library has made since it
+ * was loaded: its own per-device workspace and gate buffers, each time one is
+ * created or grown. Calls given a caller workspace, and sre_exact_noalloc,
+ * leave it unchanged. Host only. */
+SRE_API unsigned long long sre_device_allocations(void);
+
 /* Self-test of the bounded device waits (no counterpart in the paper). The
  * bulk-copy z sampler of sre_mc waits on mbarriers for its copies; every
  * such wait gives up after about 2^31 SM cycles (about a second), records

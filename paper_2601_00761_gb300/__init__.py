@@ -19,7 +19,7 @@ import numpy as np
 __all__ = ["sre_version", "sre_last_error", "sre_default_opts", "sre_make_plan", "sre_workspace_bytes",
            "sre_release_workspace", "sre_norm2", "sre_exact", "sre_exact_batched", "sre_mc",
            "pauli_x_marginal", "stabilizer_nullity", "apply_clifford_tdoped_circuit",
-           "sre_family_spectrum", "sre_family_spectrum_f64", "sre_philox_blocks", "sre_kernel_launches",
+           "sre_family_spectrum", "sre_family_spectrum_f64", "sre_philox_blocks", "sre_kernel_launches", "sre_device_allocations",
            "sre_selftest_bounded_wait",
            "sre_profile_passes", "sre_pass_timing", "sre_exact_noalloc", "sre_autotune", "SreError",
            "SRE_FP32_SIMT", "SRE_BF16X2_TC", "SRE_BF16X3_TC", "SRE_MC_UNIFORM", "SRE_MC_MARGINAL",
@@ -121,6 +121,7 @@ def load():
         "sre_family_spectrum_f64": ([_vp, ctypes.c_int, ctypes.c_ulonglong, _vp, _vp], st),
         "sre_philox_blocks": ([_vp, _vp, ctypes.c_int, _vp], st),
         "sre_kernel_launches": ([], ctypes.c_ulonglong),
+        "sre_device_allocations": ([], ctypes.c_ulonglong),
         "sre_selftest_bounded_wait": ([_vp], st),
         "sre_autotune": ([_vp, ctypes.c_int, _vp, ctypes.POINTER(Opts)], st),
         "sre_exact_noalloc": ([_vp, ctypes.c_int, ctypes.POINTER(Opts), _vp, ctypes.POINTER(Result)], st),
@@ -381,6 +382,11 @@ def sre_selftest_bounded_wait() -> int:
 def sre_kernel_launches() -> int:
     """Kernels the library has launched since it was loaded."""
     return int(load().sre_kernel_launches())
+
+
+def sre_device_allocations() -> int:
+    """Device allocations (cudaMalloc) the library has made since it was loaded."""
+    return int(load().sre_device_allocations())
 
 
 def sre_profile_passes(psi, n_x: int, **kw) -> dict:

@@ -217,13 +217,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return done != 0;
 }
-// warp-uniform wait for the completion of phase `parity` of bar; false after
-// about 2^31 cycles (about a second) without it
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    const long long t0 = clock64();
+// Waiting budget of a warp: about 2^31 SM cycles (about a second) for all of
+// its waits together, and one more such budget for draining its copies after a
+// timeout, so a warp that meets a stuck copy returns within about two seconds.
+constexpr long long WAIT_BUDGET = 1LL << 31;
+
+// warp-uniform wait for the completion of phase `parity` of bar; false once
+// the SM clock has passed `deadline` without it
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long deadline) {
     for (;;) {
         if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
-        if (clock64() - t0 > (1LL << 31)) return false;
+        if (clock64() > deadline) return false;
     }
 }
 
@@ -282,13 +286,18 @@ __global__ void __launch_bounds__(32 * FOLD_WARPS) zsample_fold_kernel(const Pas
         }
         __syncwarp();
         bool ok = true;
+        const long long deadline = clock64() + WAIT_BUDGET;     // one budget for every wait of the warp
 #pragma unroll 1
         for (int h = 0; h < H; ++h) {
             const int st = h & 1;
-            if (!mbar_wait_bounded(bar + st, (uint32_t)((h >> 1) & 1))) {
+            if (!mbar_wait_bounded(bar + st, (uint32_t)((h >> 1) & 1), deadline)) {
                 ok = false;
-                // the copies still in flight: this stage's and, if issued, the other's
-                for (int q = h; q < H && q < h + 2; ++q) mbar_wait_bounded(bar + (q & 1), (uint32_t)((q >> 1) & 1));
+                // the copies still in flight (this stage's and, if issued, the
+                // other's) share one more budget; a copy that has not landed
+                // by then may still be writing the warp's shared memory when
+                // the kernel returns, and the error word reports it
+                const long long drain = clock64() + WAIT_BUDGET;
+                for (int q = h; q < H && q < h + 2; ++q) mbar_wait_bounded(bar + (q & 1), (uint32_t)((q >> 1) & 1), drain);
                 break;
             }
             const float sg = (__popc(F & (uint32_t)h) & 1) ? -1.f : 1.f;
@@ -423,7 +432,7 @@ __global__ void __launch_bounds__(32) wait_selftest_kernel(const float4 *src, in
         bulk_g2s(buf, src, 16u, &bar);
     }
     __syncwarp();
-    if (!mbar_wait_bounded(&bar, 0u) && threadIdx.x == 0) atomicOr(err, SRE_ERR_TIMEOUT);
+    if (!mbar_wait_bounded(&bar, 0u, clock64() + WAIT_BUDGET) && threadIdx.x == 0) atomicOr(err, SRE_ERR_TIMEOUT);
 }
 
 cudaError_t launch_wait_selftest(const void *src16, int *err, cudaStream_t st) {

@@ -51,6 +51,9 @@ constexpr size_t BATCH_BYTES = 8ULL << 30;   // intermediate budget per launch s
 // kernels issued by this library since load (all entry points)
 std::atomic<unsigned long long> g_launches{0};
 void count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+// device allocations this library made since load (cudaMalloc of its own
+// workspace and gate buffers)
+std::atomic<unsigned long long> g_allocs{0};
 constexpr int EXACT_PARTS = 1024;
 
 // --------------------------------------------------------------- plans
@@ -314,6 +317,7 @@ sre_status own_workspace(size_t need, void **out) {
         w.p = nullptr;
         w.n = 0;
         cudaError_t e = cudaMalloc(&w.p, need);
+        g_allocs.fetch_add(1, std::memory_order_relaxed);
         if (e != cudaSuccess) {
             w.p = nullptr;
             return fail(SRE_ENOMEM, "cudaMalloc(%zu) failed: %s", need, cudaGetErrorString(e));
@@ -1107,6 +1111,7 @@ sre_status run_gate_list(void *psi, int N, const std::vector<GateRow> &in_rows, 
             b.p = nullptr;
             b.n = 0;
             cudaError_t e = cudaMalloc(&b.p, need);
+            g_allocs.fetch_add(1, std::memory_order_relaxed);
             if (e != cudaSuccess) return fail(SRE_ENOMEM, "gate buffer: %s", cudaGetErrorString(e));
             b.n = need;
         }
@@ -1684,6 +1689,8 @@ sre_status sre_mixed(const void *psi, int N, int N_A, void *workspace, size_t wo
 }
 
 unsigned long long sre_kernel_launches(void) { return g_launches.load(); }
+
+unsigned long long sre_device_allocations(void) { return g_allocs.load(); }
 
 // 16 source bytes and the error word of the bounded-wait self-test
 __device__ __align__(16) int g_selftest_words[8];

@@ -76,3 +76,19 @@ def test_noalloc_rejects_sizes_beyond_the_scratch(sre):
     st, _ = _call_abi(sre, psi)
     assert st == sre.SRE_EINVAL
     assert "scratch" in sre.sre_last_error()
+
+
+def test_noalloc_makes_no_device_allocation(sre):
+    """The defining property: with the library's own workspace released, two
+    calls of sre_exact_noalloc leave the library's allocation counter where it
+    was (sre_exact without a workspace, by contrast, allocates again)."""
+    psi = torch.from_numpy(inputs.haar_state(12, 7)).cuda()
+    torch.cuda.synchronize()
+    sre.sre_release_workspace()
+    a0 = sre.sre_device_allocations()
+    for _ in range(2):
+        st, r = _call_abi(sre, psi)
+        assert st == sre.SRE_OK
+    assert sre.sre_device_allocations() == a0
+    sre.sre_exact(psi)
+    assert sre.sre_device_allocations() >= a0 + 1
