@@ -43,7 +43,12 @@
 
 typedef double complex cplx;
 
-/* Test hook: a nonzero value plants one known mistake (see or_set_mutation). */
+/* Test hook: a nonzero value plants one known mistake, so that tests can show
+ * a pin catches it: 1 phase i^{x.z} dropped, 2 conjugation order swapped,
+ * 3 wrong output index, 4 "- N" dropped from M_2, 5 ln 2 dropped from the
+ * standard errors of M_2 and M_3, 6 the (1 - p(0)) factor dropped from the
+ * marginal estimator's standard error, 7 the standard errors divided by the
+ * square root of the number of drawn x plus one instead of that number. */
 static int g_mutation = 0;
 void or_set_mutation(int m) { g_mutation = m; }
 
@@ -520,11 +525,11 @@ int or_mc_uniform(const float *psi, int N, long long n_x, uint64_t seed, uint64_
         double r = sqrt(var) / Ex;
         if (a == 0) {
             M[0] = Shat - N;
-            err[0] = (dd - 1.0) * sqrt(var) / sqrt(nm);   /* sigma of H_hat, bits */
+            err[0] = (dd - 1.0) * sqrt(var) / sqrt(g_mutation == 7 ? nm + 1.0 : nm);   /* sigma of H_hat, bits */
         } else {
             double alpha = (double)(a + 1);
             M[a] = log2(Shat) / (1.0 - alpha) - N;
-            err[a] = r / (fabs(1.0 - alpha) * log(2.0) * sqrt((double)n_x));
+            err[a] = r / (fabs(1.0 - alpha) * (g_mutation == 5 ? 1.0 : log(2.0)) * sqrt((double)n_x));
         }
     }
     free(c); free(w);
@@ -609,13 +614,13 @@ int or_mc_marginal(const float *psi, int N, long long n_x, int z_per_x, uint64_t
             double var = kval(sq) / n - mean * mean;
             if (var < 0) var = 0;
             double S = p0 * g0[a] + (1.0 - p0) * mean;
-            double se = (1.0 - p0) * sqrt(var / n);
+            double se = (g_mutation == 6 ? 1.0 : 1.0 - p0) * sqrt(var / (g_mutation == 7 ? n + 1.0 : n));
             double Mv, ev;
             if (a == 0) { Mv = S; ev = se; }
             else {
                 double alpha = (double)(a + 1);
                 Mv = log2(S) / (1.0 - alpha);
-                ev = se / (S * fabs(1.0 - alpha) * log(2.0));
+                ev = se / (S * fabs(1.0 - alpha) * (g_mutation == 5 ? 1.0 : log(2.0)));
             }
             if (which) { M_rb[a] = Mv; err_rb[a] = ev; }
             else { M[a] = Mv; err[a] = ev; }

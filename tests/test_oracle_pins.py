@@ -417,6 +417,100 @@ def test_mc_all_families_is_exact_at_large_sample():
     assert np.all(np.abs(mc["M"] - ex) < 5 * mc["err"] + 1e-9)
 
 
+# ------------------------------------------- MC standard errors (Eq. stdM)
+# The error bars of both MC estimators are pinned against the spread of the
+# estimates themselves over many seeds, which no formula in the oracle enters.
+#
+# alpha = 1 is exact at any sample size: M_1 is linear in the per-family
+# values (uniform: M_1 = m_0 + (d-1) mean h_x - N; marginal: M_1 = p(0) G_0 +
+# (1 - p(0)) mean g_x), and the oracle's error bar is the population standard
+# deviation of the nm drawn families over sqrt(nm) (times (d-1), resp.
+# (1 - p(0))), so E[err^2] = ((nm-1)/nm) Var(M_1) exactly. At nm = 2 that
+# separates sqrt(nm) from sqrt(nm+1) (a factor 2/3 in the variance) and, on a
+# state with p(0) = 1/4, a dropped (1 - p(0)) (a factor 16/9).
+#
+# alpha = 2, 3 use the delta method (Eq. stdM: 1/(|1-alpha| ln 2 sqrt(N_x))
+# times the relative spread), valid once the relative error of S is small:
+# checked at 400-800 families, where the mean error bar must match the
+# standard deviation of M_hat within 15% (500 seeds: about 3% sampling noise
+# on that standard deviation); a dropped ln 2 is off by 1/ln 2 = 1.44.
+def _sigma_states():
+    N = 8
+    mixed = oracle.circuit_state(N, inputs.random_clifford_tdoped_gates(N, 80, 4, 11))   # p(0) ~ 0.01
+    local = inputs.t_product_state(N, 2)                                                 # p(0) = 1/4
+    return mixed, local
+
+
+def _spread(psi, mode, n_x, seeds, zpx=4):
+    """(estimates, error bars) over seeds, per estimator: {name: (M[K,3], err[K,3])}."""
+    acc = {}
+    for s in seeds:
+        if mode == "uniform":
+            r = oracle.mc_uniform(psi, n_x, seed=s)
+            acc.setdefault("uniform", ([], []))
+            acc["uniform"][0].append(r["M"]); acc["uniform"][1].append(r["err"])
+        else:
+            r = oracle.mc_marginal(psi, n_x, zpx, seed=s)
+            for nm_, mk, ek in (("z-sample", "M", "err"), ("per-family", "M_rb", "err_rb")):
+                acc.setdefault(nm_, ([], []))
+                acc[nm_][0].append(r[mk]); acc[nm_][1].append(r[ek])
+    return {k: (np.array(v[0]), np.array(v[1])) for k, v in acc.items()}
+
+
+def _sigma_small_n_ratios():
+    """Var-ratio E[err_1^2] nm/(nm-1) / Var(M_1) at n_x = 3 (nm = 2 drawn
+    families), 6000 seeds, for every estimator and both states."""
+    out = {}
+    mixed, local = _sigma_states()
+    nm = 2
+    for sname, psi in (("mixed", mixed), ("local", local)):
+        for mode in ("uniform", "marginal"):
+            for est, (M, e) in _spread(psi, mode, nm + 1, range(5000, 11000), zpx=2).items():
+                out[(sname, est)] = np.mean(e[:, 0] ** 2) * nm / (nm - 1) / np.var(M[:, 0], ddof=1)
+    return out
+
+
+def _sigma_large_n_ratios():
+    """mean err / std M for alpha = 1, 2, 3 at 800 (uniform) and 400
+    (marginal) families, 500 seeds, on the mixed-support state."""
+    mixed, _ = _sigma_states()
+    out = {}
+    for mode, n_x in (("uniform", 800), ("marginal", 400)):
+        for est, (M, e) in _spread(mixed, mode, n_x, range(2000, 2500)).items():
+            out[est] = e.mean(axis=0) / M.std(axis=0, ddof=1)
+    return out
+
+
+def _sigma_pins_pass():
+    small = _sigma_small_n_ratios()
+    if any(abs(v - 1.0) > 0.12 for v in small.values()):
+        return False
+    large = _sigma_large_n_ratios()
+    return all(abs(r - 1.0) < 0.15 for v in large.values() for r in v)
+
+
+def test_mc_standard_error_exact_at_small_n():
+    for key, v in _sigma_small_n_ratios().items():
+        assert abs(v - 1.0) < 0.12, (key, v)
+
+
+def test_mc_standard_error_matches_spread():
+    for est, v in _sigma_large_n_ratios().items():
+        for a in range(3):
+            assert abs(v[a] - 1.0) < 0.15, (est, a + 1, v[a])
+
+
+@pytest.mark.parametrize("m", [5, 6, 7])
+def test_sigma_mutations(m):
+    """5: ln 2 dropped; 6: (1 - p(0)) dropped; 7: sqrt(n) -> sqrt(n + 1).
+    Each must fail the standard-error pins."""
+    oracle.set_mutation(m)
+    try:
+        assert not _sigma_pins_pass()
+    finally:
+        oracle.set_mutation(0)
+
+
 # ------------------------------------------------------------- mutations
 def _pins_pass():
     """A compact subset of the pins above; False if any fails."""
