@@ -85,6 +85,11 @@ def lib():
             L.or_apply_gates.argtypes = [_c_dp, ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong]
             L.or_apply_gates.restype = ctypes.c_int
             L.or_set_mutation.argtypes = [ctypes.c_int]
+            L.or_exact_families.argtypes = [_c_fp, ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
+                                            ctypes.c_uint64, _c_dp, ctypes.c_void_p]
+            L.or_exact_finalize.argtypes = [_c_dp, ctypes.c_void_p, ctypes.c_int, _c_dp, _c_dp,
+                                            ctypes.c_void_p, ctypes.c_void_p]
+            L.or_exact_finalize.restype = None
             L.or_fluctuation_ratio.argtypes = [_c_fp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
             L.or_apply_two_qubit.argtypes = [_c_dp, ctypes.c_int, _c_dp, ctypes.c_void_p, ctypes.c_longlong]
             L.or_apply_two_qubit.restype = ctypes.c_int
@@ -210,6 +215,35 @@ def sre_exact(psi, eps: float = 1e-6, per_family: bool = False) -> dict:
     if fam is not None:
         out["family"] = fam
     return out
+
+
+def exact_families(psi, x0: int, x1: int, eps: float = 1e-6):
+    """Algorithm 1's loop body for x0 <= x < x1: per-family sums
+    [sum c^2, sum c^4, sum c^6, sum c^2 log2 c^2] (shape (x1-x0, 4)) and counts
+    of | |c| - 1 | < eps. Families are independent; exact_finalize sums them."""
+    a = _psi(psi)
+    N = _nq(a)
+    fam = np.zeros((x1 - x0, 4))
+    cnt = np.zeros(x1 - x0, dtype=np.int64)
+    rc = lib().or_exact_families(_fp(a), N, eps, x0, x1, _dp(fam),
+                                 cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)))
+    if rc != 0:
+        raise ValueError("or_exact_families failed")
+    return fam, cnt
+
+
+def exact_finalize(fam, cnt, N: int) -> dict:
+    """M_1..M_3, S, stabilizer count and nullity from all d families' sums (x order)."""
+    fam = np.ascontiguousarray(fam, dtype=np.float64)
+    cnt = np.ascontiguousarray(cnt, dtype=np.int64)
+    assert fam.shape == (1 << N, 4) and cnt.shape == (1 << N,)
+    M = np.zeros(3)
+    S = np.zeros(3)
+    sc = ctypes.c_longlong(0)
+    nul = ctypes.c_int(0)
+    lib().or_exact_finalize(_dp(fam), cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), N, _dp(M), _dp(S),
+                            ctypes.byref(sc), ctypes.byref(nul))
+    return {"M": M, "S": S, "stab_count": sc.value, "nullity": nul.value}
 
 
 def apply_two_qubit(psi, mats, pairs) -> np.ndarray:

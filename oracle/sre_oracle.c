@@ -231,6 +231,46 @@ static void finalize_moments(const double T[4], int N, double M[3], double S[3])
     if (g_mutation == 4) M[1] = -log2(S[1]);   /* dropped "- N" */
 }
 
+/* Algorithm 1, the loop over x restricted to x0 <= x < x1: fam[4 (x - x0) ..]
+ * receives the per-family partial sums of family_moments and cnt[x - x0] the
+ * family's count of | |c| - 1 | < eps. Families are independent, so a sweep
+ * may be split into ranges; or_exact_finalize then sums them in x order.
+ * Returns 0, or -1 on allocation failure or a bad range. */
+int or_exact_families(const float *psi, int N, double eps, uint64_t x0, uint64_t x1, double *fam,
+                      long long *cnt) {
+    uint64_t d = 1ULL << N;
+    if (x0 > x1 || x1 > d) return -1;
+    double s = 1.0 / or_norm2(psi, N);
+    double *c = (double *)malloc(d * sizeof(double));
+    cplx *w = (cplx *)malloc(d * sizeof(cplx));
+    if (!c || !w) { free(c); free(w); return -1; }
+    for (uint64_t x = x0; x < x1; ++x) {
+        or_family_spectrum(psi, N, x, s, c, NULL, w);
+        family_moments(c, d, eps, fam + 4 * (x - x0), cnt + (x - x0));
+    }
+    free(c); free(w);
+    return 0;
+}
+
+/* The end of Algorithm 1 from the per-family sums of all d families (in x
+ * order): Neumaier totals, Eq. SRE-def (finalize_moments), the stabilizer
+ * count and nullity = N - log2(count) (-1 if the count is not a power of two). */
+void or_exact_finalize(const double *fam, const long long *cnt, int N, double *M, double *S,
+                       long long *stab_count, int *nullity) {
+    uint64_t d = 1ULL << N;
+    ksum tot[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    long long count = 0;
+    for (uint64_t x = 0; x < d; ++x) {
+        for (int a = 0; a < 4; ++a) kadd(&tot[a], fam[4 * x + a]);
+        count += cnt[x];
+    }
+    double T[4] = {kval(&tot[0]), kval(&tot[1]), kval(&tot[2]), kval(&tot[3])};
+    finalize_moments(T, N, M, S);
+    *stab_count = count;
+    *nullity = -1;
+    if (count > 0 && (count & (count - 1)) == 0) *nullity = N - (63 - __builtin_clzll((uint64_t)count));
+}
+
 /* Algorithm 1: exact sweep over all x.
  * out: M[3], S[3]; stab_count = #{P : ||c|-1| < eps}; nullity = N - log2(count)
  * (-1 if the count is not a power of two). fam (optional, d x 4) receives the
@@ -239,28 +279,13 @@ static void finalize_moments(const double T[4], int N, double M[3], double S[3])
 int or_sre_exact(const float *psi, int N, double eps, double *M, double *S,
                  long long *stab_count, int *nullity, double *fam) {
     uint64_t d = 1ULL << N;
-    double s = 1.0 / or_norm2(psi, N);
-    double *c = (double *)malloc(d * sizeof(double));
-    cplx *w = (cplx *)malloc(d * sizeof(cplx));
-    if (!c || !w) { free(c); free(w); return -1; }
-    ksum tot[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    long long count = 0;
-    for (uint64_t x = 0; x < d; ++x) {
-        or_family_spectrum(psi, N, x, s, c, NULL, w);
-        double m[4];
-        long long cnt;
-        family_moments(c, d, eps, m, &cnt);
-        for (int a = 0; a < 4; ++a) kadd(&tot[a], m[a]);
-        count += cnt;
-        if (fam) memcpy(fam + 4 * x, m, sizeof m);
-    }
-    double T[4] = {kval(&tot[0]), kval(&tot[1]), kval(&tot[2]), kval(&tot[3])};
-    finalize_moments(T, N, M, S);
-    *stab_count = count;
-    *nullity = -1;
-    if (count > 0 && (count & (count - 1)) == 0) *nullity = N - (63 - __builtin_clzll((uint64_t)count));
-    free(c); free(w);
-    return 0;
+    double *f = fam ? fam : (double *)malloc(4 * d * sizeof(double));
+    long long *cnt = (long long *)malloc(d * sizeof(long long));
+    int rc = (f && cnt) ? or_exact_families(psi, N, eps, 0, d, f, cnt) : -1;
+    if (rc == 0) or_exact_finalize(f, cnt, N, M, S, stab_count, nullity);
+    if (!fam) free(f);
+    free(cnt);
+    return rc;
 }
 
 /* Two-qubit gates (SM, brick-wall circuits): gate k is the 4x4 complex
