@@ -292,6 +292,18 @@ SRE_API sre_status sre_family_spectrum_f64(const void *psi_c64_dev, int N, unsig
 SRE_API sre_status sre_philox_blocks(const unsigned long long *ctr_key_dev, unsigned long long *out_dev,
                              int n, void *stream);
 
+/* Self-test of the fifth-generation tensor-core path (no counterpart in the
+ * paper; it checks the conventions the tensor-core kernels rely on):
+ * D = A B^T in FP32 from BF16 operands, A: M x K and B: N x K row-major
+ * (K contiguous) device arrays of BF16 bit patterns, 16-byte aligned;
+ * D: M x N row-major FP32. M and N multiples of 128, K of 64. swizzle: 128
+ * or 64, the bytes per operand row of the shared-memory tiles (K blocks of
+ * 64 or 32). err_dev: a caller-owned device int the call clears and the
+ * kernel sets when a bounded wait runs out (then SRE_ETIMEOUT). Synchronises
+ * the stream. */
+SRE_API sre_status sre_tc_gemm_selftest(const void *A_bf16_dev, const void *B_bf16_dev, float *D_dev, int M,
+                                        int N, int K, int swizzle, int *err_dev, void *stream);
+
 /* Number of CUDA kernels this library has launched since it was loaded
  * (every entry point counts its launches). Host only. */
 SRE_API unsigned long long sre_kernel_launches(void);

@@ -19,7 +19,7 @@ import numpy as np
 __all__ = ["sre_version", "sre_last_error", "sre_default_opts", "sre_make_plan", "sre_workspace_bytes",
            "sre_release_workspace", "sre_norm2", "sre_exact", "sre_exact_batched", "sre_mc",
            "pauli_x_marginal", "stabilizer_nullity", "apply_clifford_tdoped_circuit",
-           "sre_family_spectrum", "sre_family_spectrum_f64", "sre_philox_blocks", "sre_kernel_launches", "sre_device_allocations",
+           "sre_family_spectrum", "sre_family_spectrum_f64", "sre_philox_blocks", "sre_kernel_launches", "sre_device_allocations", "sre_tc_gemm_selftest",
            "sre_selftest_bounded_wait",
            "sre_profile_passes", "sre_pass_timing", "sre_exact_noalloc", "sre_autotune", "SreError",
            "SRE_FP32_SIMT", "SRE_BF16X2_TC", "SRE_BF16X3_TC", "SRE_MC_UNIFORM", "SRE_MC_MARGINAL",
@@ -122,6 +122,8 @@ def load():
         "sre_philox_blocks": ([_vp, _vp, ctypes.c_int, _vp], st),
         "sre_kernel_launches": ([], ctypes.c_ulonglong),
         "sre_device_allocations": ([], ctypes.c_ulonglong),
+        "sre_tc_gemm_selftest": ([_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp],
+                                 st),
         "sre_selftest_bounded_wait": ([_vp], st),
         "sre_autotune": ([_vp, ctypes.c_int, _vp, ctypes.POINTER(Opts)], st),
         "sre_exact_noalloc": ([_vp, ctypes.c_int, ctypes.POINTER(Opts), _vp, ctypes.POINTER(Result)], st),
@@ -382,6 +384,20 @@ def sre_selftest_bounded_wait() -> int:
 def sre_kernel_launches() -> int:
     """Kernels the library has launched since it was loaded."""
     return int(load().sre_kernel_launches())
+
+
+def sre_tc_gemm_selftest(A, B, swizzle: int = 128):
+    """D = A B^T (FP32) from BF16 device matrices A (M x K) and B (N x K)
+    through the library's tcgen05 self-test kernel."""
+    import torch
+    assert A.dtype == torch.bfloat16 and B.dtype == torch.bfloat16 and A.is_contiguous() and B.is_contiguous()
+    M, K = A.shape
+    N = B.shape[0]
+    D = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check(load().sre_tc_gemm_selftest(_vp(A.data_ptr()), _vp(B.data_ptr()), _vp(D.data_ptr()), M, N, K, swizzle,
+                                       _vp(err.data_ptr()), _stream()))
+    return D
 
 
 def sre_device_allocations() -> int:

@@ -90,4 +90,8 @@ cudaError_t launch_gate_blocks(float2 *psi, int N, const GateRow *gates_dev, con
 constexpr int GATE_BLOCK_Q = 13;   // qubits per fused gate block (2^13 amplitudes, 64 KB of shared memory)
 constexpr int GATE_BLOCK_LOW = 5;  // qubits 0..4 always in the block (256-byte contiguous runs)
 
+// tcgen05 self-test GEMM (k_tc05.cu): D = A B^T, BF16 in, FP32 out
+cudaError_t launch_tc05_gemm_selftest(const void *A, const void *B, float *D, int M, int N, int K, int swizzle,
+                                      int *err, cudaStream_t st);
+
 } // namespace sre

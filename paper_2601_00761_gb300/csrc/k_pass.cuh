@@ -15,8 +15,6 @@
 // pass's global bit offset and the family come from PassArgs / the grid.
 #pragma once
 
-#include <type_traits>
-
 #include "sre_internal.cuh"
 #include "k_tc.cuh"
 
@@ -425,18 +423,6 @@ __device__ __forceinline__ bool fwht_pass_body(const PassArgs &a, int rep) {
     // ---------------------------------------------------------- prologue
     pass_prologue<Cfg, SRC>(v, a, psi, slot, x, j, half, gbase, t);
 
-    // The moments epilogue scales the tile's c^2 log2 c^2 sum by log2 of
-    // sig = (2s)^2 (x != 0) or s^2 (x = 0). Its FP64 log runs in the writing
-    // thread here, while the tile's loads are in flight, not after the
-    // reduction at the end of the tile.
-    double lg_sig = 0.0;
-    if constexpr (DST == DST_MOMENTS) {
-        if (t == 0) {
-            const double sd = *s_ptr;
-            lg_sig = log2(x ? 4.0 * sd * sd : sd * sd);
-        }
-        asm volatile("" : "+d"(lg_sig));   // keep it ahead of the transform's barriers
-    }
 
     // --------------------------------------------------------- transform
     if constexpr (PREC == 0) tile_transform<Cfg>(v, sm, t, grp);
@@ -592,6 +578,13 @@ __device__ __forceinline__ bool fwht_pass_body(const PassArgs &a, int rep) {
         if (active && t == 0) {
             const double sd = *s_ptr;
             const double g1 = x ? 4.0 * sd * sd : sd * sd, g2 = g1 * g1, g3 = g2 * g1;
+            // log2 g1 = e + log2 m, g1 = m 2^e, m in [1/2, 1): the FP32 log of
+            // the mantissa is good to about 1e-7 absolute, far below the FP32
+            // rounding of the tile sums, and keeps FP64 work off the tile's
+            // critical path (a full FP64 log is tens of FP64 instructions)
+            int ex;
+            const double mt = frexp(g1, &ex);
+            const double lg_sig = (double)ex + (double)log2f((float)mt);
             const long long tiles = (long long)(half >> Cfg::M) > 0 ? (long long)(half >> Cfg::M) : 1;
             TilePartial &tp = a.tile_out[(size_t)slot * (size_t)tiles + tile];
             tp.m[0] = g1 * out[0];
@@ -623,152 +616,6 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const Pas
     }
 }
 
-
-// ---------------------------------------------------------------------------
-// Strided psi-reading pass with the tile's own half shared in shared memory.
-//
-// Every family of a launch with the same top X bit j reads the same own
-// amplitudes psi[b], b = g with 0 inserted at bit j, for the g of a tile;
-// only the partner psi[b ^ x] differs. The CTA therefore holds two tile
-// groups of 2^(M-5) threads, each transforming one family at a time, and
-// FPC families of the same tile in turn (FPC / 2 rounds). In the first round
-// both groups read psi from global memory and group 0 also keeps its own
-// amplitudes in a dense shared copy of the tile (its family's j is j0); in
-// later rounds a family with j = j0 takes its own amplitudes from that copy,
-// so the tile's own rows cross the L2-to-SM fabric once per FPC families
-// instead of once per family. The groups synchronise their transform rounds
-// on named barriers of their own, so after the first round they run out of
-// step, one group loading while the other transforms.
-template <class Cfg, int OWN>    // OWN: 0 global, 1 global and kept in `own`, 2 from `own`
-__device__ __forceinline__ void psi_family_prologue(float2 (&v)[Cfg::E], const float2 *psi, float2 *own,
-                                                    uint32_t base, uint32_t rs, unsigned long long x, int j,
-                                                    unsigned long long half, uint32_t t) {
-    constexpr int A0 = Maps<Cfg>::first;
-    constexpr int LB = Cfg::E < 8 ? Cfg::E : 8;
-    const uint32_t e0 = Cfg::elem(t, 0, A0);
-    if (x != 0) {
-        const uint32_t hm = ~((1u << j) - 1u), x32 = (uint32_t)x;
-#pragma unroll
-        for (int k0 = 0; k0 < Cfg::E; k0 += LB) {
-            float2 u[LB], w[LB];
-#pragma unroll
-            for (int q = 0; q < LB; ++q) {
-                const uint32_t g = slot_gidx<Cfg, A0>(base, rs, k0 + q);
-                const uint32_t b = g + (g & hm);
-                if constexpr (OWN == 2) u[q] = own[e0 + ((uint32_t)(k0 + q) << A0)];
-                else u[q] = __ldg(psi + b);
-                w[q] = __ldg(psi + (b ^ x32));
-            }
-#pragma unroll
-            for (int q = 0; q < LB; ++q) {
-                if constexpr (OWN == 1) own[e0 + ((uint32_t)(k0 + q) << A0)] = u[q];
-                const float ux = u[q].x, uy = u[q].y, wx = w[q].x, wy = w[q].y;
-                v[k0 + q].x = fmaf(wx, ux, wy * uy);     // conj(w) * u, contraction fixed
-                v[k0 + q].y = fmaf(wx, uy, -(wy * ux));
-            }
-        }
-    } else {
-        const uint32_t h32 = (uint32_t)half;
-#pragma unroll
-        for (int k0 = 0; k0 < Cfg::E; k0 += LB) {
-            float2 u[LB], w[LB];
-#pragma unroll
-            for (int q = 0; q < LB; ++q) {
-                const uint32_t g = slot_gidx<Cfg, A0>(base, rs, k0 + q);
-                if constexpr (OWN == 2) u[q] = own[e0 + ((uint32_t)(k0 + q) << A0)];
-                else u[q] = __ldg(psi + g);
-                w[q] = __ldg(psi + (g | h32));
-            }
-#pragma unroll
-            for (int q = 0; q < LB; ++q) {
-                if constexpr (OWN == 1) own[e0 + ((uint32_t)(k0 + q) << A0)] = u[q];
-                const float ux = u[q].x, uy = u[q].y, wx = w[q].x, wy = w[q].y;
-                v[k0 + q].x = fmaf(ux, ux, uy * uy);
-                v[k0 + q].y = fmaf(wx, wx, wy * wy);
-            }
-        }
-    }
-}
-
-template <class Cfg, int FPC>
-__global__ void __launch_bounds__(Cfg::NT, 1) strided_psi_shared_kernel(const PassArgs a) {
-    static_assert(Cfg::G == 2 && Cfg::LO > 0 && std::is_same<typename Cfg::Real, float>::value, "two FP32 strided groups");
-    static_assert(FPC % 2 == 0, "families come in pairs");
-    extern __shared__ __align__(16) unsigned char smraw[];
-    float2 *sm = reinterpret_cast<float2 *>(smraw);                 // the groups' padded exchange tiles
-    float2 *own = sm + 2 * Cfg::PSIZE;                              // dense own tile (2^M points)
-    const uint32_t tid = threadIdx.x;
-    const uint32_t grp = tid >> Cfg::TB;
-    const uint32_t t = tid & (Cfg::T - 1);
-    const unsigned long long np = ((unsigned long long)a.n_fam + FPC - 1) / FPC;
-    const unsigned long long L = blockIdx.x;
-    const long long slot0 = (long long)(L % np) * FPC;
-    const unsigned long long tile = L / np;
-    const int N = a.N, n = a.n;
-    const unsigned long long dmask = (1ULL << N) - 1ULL;
-    const unsigned long long half = 1ULL << n;
-    const int cb_bits = a.lo_g - Cfg::LO;
-    const unsigned long long gbase = ((tile >> cb_bits) << (a.lo_g + Cfg::K)) | ((tile & ((1ULL << cb_bits) - 1ULL)) << Cfg::LO);
-    const uint32_t rs = 1u << a.lo_g;
-    constexpr int A0 = Maps<Cfg>::first, AL = Maps<Cfg>::last;
-    const uint32_t base0 = thread_gidx<Cfg>(gbase, a.lo_g, Cfg::elem(t, 0, A0));
-    const uint32_t baseL = thread_gidx<Cfg>(gbase, a.lo_g, Cfg::elem(t, 0, AL));
-    auto fam_x = [&](long long slot) -> unsigned long long {
-        return (a.xs ? a.xs[a.fam_base + slot] : (unsigned long long)(a.fam_base + slot)) & dmask;
-    };
-    const unsigned long long x0 = fam_x(slot0);
-    const int j0 = x0 ? 63 - __clzll((long long)x0) : n;
-    float2 v[Cfg::E];
-#pragma unroll 1
-    for (int r = 0; r < FPC / 2; ++r) {
-        long long slot = slot0 + 2 * r + grp;
-        if (2 * r > 0 && slot0 + 2 * r >= a.n_fam) break;          // uniform over the CTA
-        const bool active = slot < a.n_fam;
-        if (!active) slot = a.n_fam - 1;                           // run on valid data, write nothing
-        const unsigned long long x = fam_x(slot);
-        const int j = x ? 63 - __clzll((long long)x) : n;
-        if (r == 0) {
-            if (grp == 0) psi_family_prologue<Cfg, 1>(v, a.psi, own, base0, rs, x, j, half, t);
-            else psi_family_prologue<Cfg, 0>(v, a.psi, own, base0, rs, x, j, half, t);
-        } else {
-            round_barrier<Cfg, true>(grp);                          // the exchange tile is reused
-            if (j == j0) psi_family_prologue<Cfg, 2>(v, a.psi, own, base0, rs, x, j, half, t);
-            else psi_family_prologue<Cfg, 0>(v, a.psi, own, base0, rs, x, j, half, t);
-        }
-        tile_transform<Cfg, true>(v, sm, t, grp);
-        if (active) {
-            float2 *dst = reinterpret_cast<float2 *>(a.dst) + (size_t)slot * (size_t)a.slot_elems;
-#pragma unroll
-            for (int k = 0; k < Cfg::E; ++k) dst[slot_gidx<Cfg, AL>(baseL, rs, k)] = v[k];
-        }
-        if (r == 0) __syncthreads();                               // the own tile is complete
-    }
-}
-
-// Shared memory of strided_psi_shared_kernel: two padded exchange tiles and
-// the dense own tile.
-template <class Cfg>
-constexpr size_t strided_psi_shared_smem() {
-    return sizeof(float2) * (2 * (size_t)Cfg::PSIZE + (size_t)Cfg::SIZE);
-}
-
-// Launch over `tiles` tiles x n_fam families, FPC families per CTA, the
-// family fastest (the families in flight share the tile's lines in L2).
-template <class Cfg, int FPC>
-cudaError_t launch_strided_psi_shared(const PassArgs &a, int tiles, cudaStream_t st) {
-    constexpr size_t smem = strided_psi_shared_smem<Cfg>();
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(strided_psi_shared_kernel<Cfg, FPC>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_done = true;
-    }
-    const long long groups = (a.n_fam + FPC - 1) / FPC;
-    if (groups * (long long)tiles >= 0x7fffffffLL) return cudaErrorInvalidValue;
-    strided_psi_shared_kernel<Cfg, FPC><<<(unsigned)(groups * tiles), Cfg::NT, smem, st>>>(a);
-    return cudaGetLastError();
-}
 
 template <class Cfg, int SRC, int DST, int PREC = 0>
 cudaError_t launch_cfg(const PassArgs &a, int tiles, cudaStream_t st) {

@@ -1,24 +1,8 @@
 // Instantiations: FP32 strided passes (2^K rows x 2^(MS-K) columns) and row passes.
 #include "k_pass_dispatch.cuh"
 namespace sre {
-// Families of one tile per CTA of the shared-own strided pass.
-#ifndef SRE_SHARED_FPC
-#define SRE_SHARED_FPC 8
-#endif
-
 cudaError_t launch_f32_strided(int MS, int K, int src, int dst, const PassArgs &a, int tiles, cudaStream_t st) {
     if (MS != f32_strided_ms(K)) return cudaErrorInvalidValue;
-    // psi-reading passes of one state over several families and tiles: the
-    // tile's own amplitudes are shared by the families of a CTA
-    if (SRE_SHARED_FPC > 0 && src == SRC_PSI_FAMILY && dst == DST_BUF && a.precision == 0 && !a.psi_list &&
-        a.n_fam > 1 && tiles > 1) {
-        switch (K) {
-#define C(k) case k: return launch_strided_psi_shared<TileCfg<float, f32_strided_ms(k), f32_strided_ms(k) - k, 5, 2>, SRE_SHARED_FPC>(a, tiles, st);
-        C(1) C(2) C(3) C(4) C(5) C(6) C(7) C(8) C(9) C(10)
-#undef C
-        default: return cudaErrorInvalidValue;
-        }
-    }
     switch (K) {
 #define C(k) case k: return launch_sd<KIND_STRIDED, TileCfg<float, f32_strided_ms(k), f32_strided_ms(k) - k, 5, 1>>(src, dst, a, tiles, st);
     C(1) C(2) C(3) C(4) C(5) C(6) C(7) C(8) C(9) C(10)

@@ -1798,4 +1798,22 @@ sre_status sre_philox_blocks(const unsigned long long *ctr_key_dev, unsigned lon
     return SRE_OK;
 }
 
+sre_status sre_tc_gemm_selftest(const void *A_bf16_dev, const void *B_bf16_dev, float *D_dev, int M, int N, int K,
+                                int swizzle, int *err_dev, void *stream) {
+    if (!A_bf16_dev || !B_bf16_dev || !D_dev || !err_dev) return fail(SRE_EINVAL, "tc gemm self-test: NULL pointer");
+    if (M <= 0 || N <= 0 || K <= 0 || M % 128 || N % 128 || K % 64)
+        return fail(SRE_EINVAL, "tc gemm self-test: M, N must be multiples of 128 and K of 64 (got %d, %d, %d)", M, N, K);
+    if (((uintptr_t)A_bf16_dev | (uintptr_t)B_bf16_dev) & 15) return fail(SRE_EINVAL, "tc gemm self-test: operands must be 16-byte aligned");
+    if (swizzle != 128 && swizzle != 64) return fail(SRE_EINVAL, "tc gemm self-test: swizzle must be 128 or 64");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(err_dev, 0, sizeof(int), st));
+    CK(launch_tc05_gemm_selftest(A_bf16_dev, B_bf16_dev, D_dev, M, N, K, swizzle, err_dev, st));
+    count_launches(1);
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h & SRE_ERR_TIMEOUT) return fail(SRE_ETIMEOUT, "tc gemm self-test: a bounded wait ran out");
+    return SRE_OK;
+}
+
 } // extern "C"

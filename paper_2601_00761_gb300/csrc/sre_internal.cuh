@@ -153,16 +153,7 @@ __device__ __forceinline__ void butterflies(C2 (&v)[E]) {
     }
 }
 
-// Barrier between the rounds of a tile: the whole CTA (GB = false), or only
-// the 2^TB threads of the tile's group, on named barrier 1 + g (GB = true), so
-// that the groups of a CTA can run their tiles out of step.
-template <class Cfg, bool GB>
-__device__ __forceinline__ void round_barrier(uint32_t g) {
-    if constexpr (GB) asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(Cfg::T) : "memory");
-    else __syncthreads();
-}
-
-template <class Cfg, int r, bool GB = false>
+template <class Cfg, int r>
 struct Rounds {
     typedef typename Cfg::C2 C2;
     static constexpr int i = Cfg::NR - 1 - r;
@@ -170,7 +161,7 @@ struct Rounds {
     __device__ static __forceinline__ void run(C2 (&v)[Cfg::E], C2 *sm, uint32_t t, uint32_t g) {
         C2 *pb = sm + Cfg::phys(Cfg::elem(t, 0, a), g);
         if constexpr (r > 0) {
-            round_barrier<Cfg, GB>(g);
+            __syncthreads();
 #pragma unroll
             for (int k = 0; k < Cfg::E; ++k) v[k] = pb[Cfg::pad((uint32_t)k << a)];
         }
@@ -178,7 +169,7 @@ struct Rounds {
         if constexpr (r < Cfg::NR - 1) {
 #pragma unroll
             for (int k = 0; k < Cfg::E; ++k) pb[Cfg::pad((uint32_t)k << a)] = v[k];
-            Rounds<Cfg, r + 1, GB>::run(v, sm, t, g);
+            Rounds<Cfg, r + 1>::run(v, sm, t, g);
         }
     }
 };
@@ -190,10 +181,10 @@ template <class Cfg> struct Maps {
     static constexpr int last = Cfg::NR > 0 ? Cfg::slot_base(0) : first;
 };
 
-template <class Cfg, bool GB = false>
+template <class Cfg>
 __device__ __forceinline__ void tile_transform(typename Cfg::C2 (&v)[Cfg::E], typename Cfg::C2 *sm,
                                                uint32_t t, uint32_t g) {
-    if constexpr (Cfg::NR > 0) Rounds<Cfg, 0, GB>::run(v, sm, t, g);
+    if constexpr (Cfg::NR > 0) Rounds<Cfg, 0>::run(v, sm, t, g);
 }
 
 // z-ranges of the two-level sampler: 2^ZR_FINE consecutive z per range when
