@@ -69,10 +69,7 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
                     print("compiled", os.path.basename(s), flush=True)
     if todo or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        # cuBLAS (the Gram matrix of the mixed-state entry point), found through
-        # the toolkit next to this nvcc at run time as well
-        libdir = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(cc))), "lib64")
-        cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-L", libdir, "-lcublas", "-Xlinker", "-rpath=" + libdir]
+        cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr[-6000:]}")

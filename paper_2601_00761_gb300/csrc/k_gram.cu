@@ -1,0 +1,270 @@
+// k_gram.cu -- the Gram matrix C = Psi Psi^H of a bipartite state on the
+// tensor cores (SM, mixed states: the reduced state of the first N_A qubits
+// is rho_A = C, C[a][a'] = sum_e psi(a, e) conj psi(a', e), and the partial
+// transform reads h_{x_A}(a) = C[a][a ^ x_A]).
+//
+// Psi is the complex64 state viewed as d_A x d_B (row a = the low N_A bits,
+// column e = the rest; element (a, e) at psi[a + d_A e]). With X = Re Psi and
+// Y = Im Psi, C = (X X^T + Y Y^T) + i (Y X^T - X Y^T): four real products
+// with K = d_B. Every FP32 value is split into three BF16 parts (x = x0 + x1 +
+// x2 exactly up to the last bits of x2) and a product x y is taken as the six
+// part products x_p y_q with p + q <= 2, which leaves an error of about
+// 2^-24 |x y|, the FP32 rounding level.
+//
+// 1. gram_split_kernel transposes Psi into six K-major BF16 planes
+//    P[c * 3 + p][a][e] (c = 0: X, 1: Y; p the part).
+// 2. gram_tc_kernel: one 128 x 128 tile (I, J) of C per CTA, I <= J only;
+//    K in blocks of 32 (64-byte rows, TMA with the 64-byte swizzle), a
+//    two-stage ring of 12 boxes per block (X_I, Y_I, X_J, Y_J, three parts
+//    each, 96 KB per stage); one thread issues the TMA loads and the 48 MMAs
+//    per block (D_re, D_im: 128 TMEM columns each); the four warps write the
+//    tile and, off the diagonal, its conjugate transpose. With several chunks
+//    of K the tile is added to C.
+// 3. gram_simt_kernel: small shapes (d_A < 128 or d_B < 32), FP32 products
+//    summed in FP64 per entry.
+#include "k_tc05.cuh"
+#include "sre_internal.cuh"
+
+#include <cuda_bf16.h>
+
+namespace sre {
+
+// ------------------------------------------------------------ split
+// planes: 6 x dA x dBc BF16 (K-major); this chunk covers columns e0 .. e0 + dBc
+__global__ void __launch_bounds__(256) gram_split_kernel(const float2 *psi, int NA, long long e0, int dBc_log2,
+                                                         __nv_bfloat16 *planes) {
+    __shared__ float2 t[32][33];
+    const unsigned long long dA = 1ULL << NA, dBc = 1ULL << dBc_log2;
+    const unsigned long long a0 = (unsigned long long)blockIdx.x * 32, c0 = (unsigned long long)blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    // read 32 rows a (contiguous) x 32 columns e
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int col = ty + 8 * k;
+        t[col][tx] = psi[(a0 + tx) + dA * (unsigned long long)(e0 + (long long)(c0 + col))];
+    }
+    __syncthreads();
+    const size_t plane = (size_t)dA * dBc;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int row = ty + 8 * k;                    // a = a0 + row, e = c0 + tx
+        const float2 v = t[tx][row];
+        const size_t o = (size_t)(a0 + row) * dBc + c0 + tx;
+        const float xs[2] = {v.x, v.y};
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const float x = xs[c];
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            const float r1 = x - __bfloat162float(h);
+            const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+            const float r2 = r1 - __bfloat162float(m);
+            const __nv_bfloat16 l = __float2bfloat16_rn(r2);
+            planes[(size_t)(3 * c + 0) * plane + o] = h;
+            planes[(size_t)(3 * c + 1) * plane + o] = m;
+            planes[(size_t)(3 * c + 2) * plane + o] = l;
+        }
+    }
+}
+
+// ------------------------------------------------------------ tensor cores
+constexpr int GRAM_T = 128;                    // tile rows / columns
+constexpr int GRAM_KB = 32;                    // K per block (64-byte rows)
+constexpr uint32_t GRAM_BOX = GRAM_T * 64;     // bytes of one 128 x 32 BF16 box
+constexpr uint32_t GRAM_STAGE = 12 * GRAM_BOX; // X_I, Y_I, X_J, Y_J x 3 parts
+constexpr size_t GRAM_SMEM = 1024 + 2 * (size_t)GRAM_STAGE + 128;
+
+// tile index -> (I, J) with I <= J over nt x nt tiles (row-major upper triangle)
+__device__ __forceinline__ void tri_tile(int idx, int nt, int &I, int &J) {
+    int i = 0, rem = idx;
+    while (rem >= nt - i) { rem -= nt - i; ++i; }
+    I = i;
+    J = i + rem;
+}
+
+__global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__ CUtensorMap tp, float2 *C, int NA,
+                                                         int dBc_log2, int accumulate_c, int *err) {
+    using namespace tc05;
+    extern __shared__ unsigned char smraw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = reinterpret_cast<uint64_t *>(base + 2 * GRAM_STAGE);
+    uint64_t *done = full + 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 2);
+    int *last = reinterpret_cast<int *>(tslot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned long long dA = 1ULL << NA;
+    const int nt = (int)(dA / GRAM_T);
+    int I, J;
+    tri_tile((int)blockIdx.x, nt, I, J);
+    const int r0I = I * GRAM_T, r0J = J * GRAM_T;
+    if (warp == 0) {
+        tmem_alloc(tslot, 256);
+        tmem_relinquish();
+    }
+    if (threadIdx.x == 32) {
+        mbar_init(full, 1);
+        mbar_init(full + 1, 1);
+        mbar_init(done, 1);
+        mbar_init(done + 1, 1);
+        fence_barrier_init();
+        prefetch_tmap(&tp);
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tslot;            // D_re: columns 0..127, D_im: 128..255
+    const int nk = (1 << dBc_log2) / GRAM_KB;
+    if (threadIdx.x == 0) {
+        const long long deadline = clock64() + (1LL << 32);
+        const uint32_t id_pos = idesc_bf16_f32(GRAM_T, GRAM_T, false);
+        const uint32_t id_neg = idesc_bf16_f32(GRAM_T, GRAM_T, true);
+        auto load_stage = [&](int kb, int s) {
+            unsigned char *st = base + s * GRAM_STAGE;
+            mbar_expect_tx(full + s, GRAM_STAGE);
+            // slot (m, p): m = 0 X_I, 1 Y_I, 2 X_J, 3 Y_J; plane = 3 (m & 1) + p
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+#pragma unroll
+                for (int p = 0; p < 3; ++p)
+                    tma_load_3d(st + (m * 3 + p) * GRAM_BOX, &tp, kb * GRAM_KB, m < 2 ? r0I : r0J, 3 * (m & 1) + p,
+                                full + s);
+        };
+        int committed = -1;
+        bool ok = true;
+        load_stage(0, 0);
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb & 1;
+            if (!mbar_wait(full + s, (uint32_t)((kb >> 1) & 1), deadline)) { ok = false; break; }
+            fence_after_sync();
+            const uint32_t sb = smem_u32(base + s * GRAM_STAGE);
+            auto slot = [&](int m, int p, int ks) { return smem_desc<64>(sb + (m * 3 + p) * GRAM_BOX + 32 * ks); };
+#pragma unroll
+            for (int ks = 0; ks < GRAM_KB / 16; ++ks) {
+                // part pairs (p, q) with p + q <= 2
+                const int PP[6] = {0, 0, 1, 0, 2, 1}, QQ[6] = {0, 1, 0, 2, 0, 1};
+#pragma unroll
+                for (int u = 0; u < 6; ++u) {
+                    const int p = PP[u], q = QQ[u];
+                    const uint32_t acc = (kb > 0 || ks > 0 || u > 0) ? 1u : 0u;
+                    mma_bf16(tmem, slot(0, p, ks), slot(2, q, ks), id_pos, acc);          // X_I X_J^T
+                    mma_bf16(tmem, slot(1, p, ks), slot(3, q, ks), id_pos, 1u);           // + Y_I Y_J^T
+                    mma_bf16(tmem + 128, slot(1, p, ks), slot(2, q, ks), id_pos, acc);    // Y_I X_J^T
+                    mma_bf16(tmem + 128, slot(0, p, ks), slot(3, q, ks), id_neg, 1u);     // - X_I Y_J^T
+                }
+            }
+            mma_commit(done + s);
+            committed = kb;
+            if (kb + 1 < nk) {
+                const int s1 = (kb + 1) & 1;
+                if (kb >= 1 && !mbar_wait(done + s1, (uint32_t)(((kb - 1) >> 1) & 1), deadline)) { ok = false; break; }
+                load_stage(kb + 1, s1);
+            }
+        }
+        if (!ok) atomicOr(err, SRE_ERR_TIMEOUT);
+        *last = committed;
+    }
+    __syncthreads();
+    const int lk = *last;
+    bool have = false;
+    if (lk >= 0) have = mbar_wait(done + (lk & 1), (uint32_t)((lk >> 1) & 1), clock64() + (1LL << 32));
+    if (lk >= 0 && !have && lane == 0) atomicOr(err, SRE_ERR_TIMEOUT);
+    fence_after_sync();
+    if (lk == nk - 1 && have) {
+        const unsigned long long i = (unsigned long long)r0I + 32 * warp + lane;
+        const uint32_t lrow = (uint32_t)(32 * warp) << 16;
+#pragma unroll 1
+        for (int c = 0; c < GRAM_T; c += 32) {
+            float re[32], im[32];
+            tmem_ld32(tmem + lrow + (uint32_t)c, re);
+            tmem_ld32(tmem + lrow + 128u + (uint32_t)c, im);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                const unsigned long long jj = (unsigned long long)r0J + c + k;
+                float2 v = make_float2(re[k], im[k]);
+                float2 *pc = C + i + dA * jj;
+                if (accumulate_c) { const float2 o = *pc; v.x += o.x; v.y += o.y; }
+                *pc = v;
+            }
+            if (I != J) {
+                // C[j][i] = conj C[i][j]: 32 consecutive j of this thread's row i
+                float2 *row = C + (unsigned long long)r0J + c + dA * i;
+#pragma unroll
+                for (int k = 0; k < 32; k += 2) {
+                    float4 w = make_float4(re[k], -im[k], re[k + 1], -im[k + 1]);
+                    float4 *pr = reinterpret_cast<float4 *>(row + k);
+                    if (accumulate_c) {
+                        const float4 o = *pr;
+                        w.x += o.x; w.y += o.y; w.z += o.z; w.w += o.w;
+                    }
+                    *pr = w;
+                }
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
+// ------------------------------------------------------------ small shapes
+__global__ void __launch_bounds__(256) gram_simt_kernel(const float2 *psi, int NA, int NB, float2 *C) {
+    const unsigned long long dA = 1ULL << NA, dB = 1ULL << NB;
+    const unsigned long long idx = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= dA * dA) return;
+    const unsigned long long i = idx % dA, j = idx / dA;     // C[i][j] at i + dA j
+    double re = 0.0, im = 0.0;
+    for (unsigned long long e = 0; e < dB; ++e) {
+        const float2 a = psi[i + dA * e], b = psi[j + dA * e];
+        // a conj(b)
+        re += (double)(a.x * b.x + a.y * b.y);
+        im += (double)(a.y * b.x - a.x * b.y);
+    }
+    C[i + dA * j] = make_float2((float)re, (float)im);
+}
+
+// K chunk (columns of Psi per split) bounded so the planes stay within 2^27 elements each
+int gram_chunk_log2(int N, int NA) {
+    const int nb = N - NA;
+    const int cap = 27 - NA;
+    return nb < cap ? nb : (cap < 5 ? 5 : cap);
+}
+
+size_t gram_plane_bytes(int N, int NA) {
+    if (NA < 7 || N - NA < 5) return 0;
+    return (size_t)6 * ((size_t)1 << NA) * ((size_t)1 << gram_chunk_log2(N, NA)) * sizeof(__nv_bfloat16);
+}
+
+cudaError_t launch_gram(const float2 *psi, int N, int NA, float2 *C, void *planes, int *err, int *launches,
+                        cudaStream_t st) {
+    const int NB = N - NA;
+    *launches = 0;
+    if (NA < 7 || NB < 5) {
+        const unsigned long long n = 1ULL << (2 * NA);
+        gram_simt_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(psi, NA, NB, C);
+        *launches = 1;
+        return cudaGetLastError();
+    }
+    const int cl = gram_chunk_log2(N, NA);
+    const unsigned long long dA = 1ULL << NA, dBc = 1ULL << cl;
+    const int nt = (int)(dA / GRAM_T);
+    const int ntiles = nt * (nt + 1) / 2;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GRAM_SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    CUtensorMap tp;
+    cudaError_t e = tc05_make_map_bf16(&tp, planes, dA, dBc, dBc, GRAM_T, 64, 6);
+    if (e != cudaSuccess) return e;
+    for (long long e0 = 0; e0 < (1LL << NB); e0 += (long long)dBc) {
+        gram_split_kernel<<<dim3((unsigned)(dA / 32), (unsigned)(dBc / 32)), 256, 0, st>>>(
+            psi, NA, e0, cl, reinterpret_cast<__nv_bfloat16 *>(planes));
+        gram_tc_kernel<<<ntiles, 128, GRAM_SMEM, st>>>(tp, C, NA, cl, e0 > 0 ? 1 : 0, err);
+        *launches += 2;
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+} // namespace sre

@@ -45,10 +45,12 @@ struct NullDirectArgs {
 };
 cudaError_t launch_null_direct(const NullDirectArgs &a, long long n_fam, cudaStream_t st);
 // per-family sums of a launch's tile partials into fm[fm_base + slot], or,
-// with perm (processing order -> family index), into fm[perm[fam_base + slot]]
+// with perm (processing order -> family index), into fm[perm[fam_base + slot]];
+// s = 1/|psi|^2 from *s_ptr, or from s_list[F >> N] in multi-state launches
 cudaError_t launch_fam_reduce(const TilePartial *tp, long long n_fam, int tiles, const unsigned long long *xs,
                               long long fam_base, int N, int M_last, int RL, FamMoments *fm, long long fm_base,
-                              float *W, long long nr, cudaStream_t st, const unsigned long long *perm = nullptr);
+                              float *W, long long nr, cudaStream_t st, const unsigned long long *perm,
+                              const double *s_ptr, const double *s_list);
 cudaError_t launch_exact_totals(const FamMoments *fm, long long n_fam, double *partial, int n_part,
                                 double *out, unsigned long long *flag_list, unsigned long long *n_flag,
                                 cudaStream_t st);
@@ -93,5 +95,12 @@ constexpr int GATE_BLOCK_LOW = 5;  // qubits 0..4 always in the block (256-byte 
 // tcgen05 self-test GEMM (k_tc05.cu): D = A B^T, BF16 in, FP32 out
 cudaError_t launch_tc05_gemm_selftest(const void *A, const void *B, float *D, int M, int N, int K, int swizzle,
                                       int *err, cudaStream_t st);
+
+// Gram matrix C = Psi Psi^H of the reduced state on the low N_A qubits
+// (k_gram.cu): column-major d_A x d_A complex C; `planes` holds
+// gram_plane_bytes(N, N_A) bytes; *launches receives the kernels issued.
+size_t gram_plane_bytes(int N, int NA);
+cudaError_t launch_gram(const float2 *psi, int N, int NA, float2 *C, void *planes, int *err, int *launches,
+                        cudaStream_t st);
 
 } // namespace sre

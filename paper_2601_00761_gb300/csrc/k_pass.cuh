@@ -515,9 +515,9 @@ __device__ __forceinline__ bool fwht_pass_body(const PassArgs &a, int rep) {
         // weights are read off the packed sum of q: a tile spans two ranges
         // of 2^M consecutive z (range A, then range B).
         // Sums run on the transform outputs h; c = sc h with sc = 2 s (x != 0)
-        // or s (x = 0, h = (Re + Im, Re - Im)), so each sum is scaled once
-        // per tile by a power of sig = sc^2 (FP32 for the range weights that
-        // go straight to the range rows, FP64 for the tile partials).
+        // or s (x = 0, h = (Re + Im, Re - Im)), so each sum is scaled by a
+        // power of sig = sc^2: here (FP32) for the range weights that go
+        // straight to the range rows, per family (FP64) for the tile partials.
         float s;
         if constexpr (S_SHARED) s = s_sh[grp];
         else s = (float)(*s_ptr);
@@ -576,23 +576,13 @@ __device__ __forceinline__ bool fwht_pass_body(const PassArgs &a, int rep) {
         float omx;
         group_reduce<Cfg::T, Cfg::NT, 6>(acc, qmax, out, omx, red);
         if (active && t == 0) {
-            const double sd = *s_ptr;
-            const double g1 = x ? 4.0 * sd * sd : sd * sd, g2 = g1 * g1, g3 = g2 * g1;
-            // log2 g1 = e + log2 m, g1 = m 2^e, m in [1/2, 1): the FP32 log of
-            // the mantissa is good to about 1e-7 absolute, far below the FP32
-            // rounding of the tile sums, and keeps FP64 work off the tile's
-            // critical path (a full FP64 log is tens of FP64 instructions)
-            int ex;
-            const double mt = frexp(g1, &ex);
-            const double lg_sig = (double)ex + (double)log2f((float)mt);
+            // sums in transform units; fam_reduce_kernel scales them to c units
+            // once per family (powers of sig = sc^2 and the log2 sig term)
             const long long tiles = (long long)(half >> Cfg::M) > 0 ? (long long)(half >> Cfg::M) : 1;
             TilePartial &tp = a.tile_out[(size_t)slot * (size_t)tiles + tile];
-            tp.m[0] = g1 * out[0];
-            tp.m[1] = g2 * out[1];
-            tp.m[2] = g3 * out[2];
-            tp.m[3] = g1 * (out[3] + lg_sig * out[0]);
-            tp.w[0] = g1 * out[4]; tp.w[1] = g1 * out[5];
-            tp.cand = (cand && (double)omx * g1 > (double)a.cand_thr * (double)a.cand_thr) ? 1u : 0u;
+            tp.m[0] = out[0]; tp.m[1] = out[1]; tp.m[2] = out[2]; tp.m[3] = out[3];
+            tp.w[0] = out[4]; tp.w[1] = out[5];
+            tp.cand = (cand && omx * sig > a.cand_thr * a.cand_thr) ? 1u : 0u;
         }
     }
     return true;

@@ -8,7 +8,6 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdlib>
-#include <cublas_v2.h>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -645,7 +644,7 @@ sre_status exact_impl(const void *psi, int N, const sre_opts &o, void *ws, size_
         b.n_fam = nf;
         CS(run_transform(P, b, SRC_PSI_FAMILY, DST_MOMENTS, w.inter, st));
         CK(launch_fam_reduce(w.tiles, nf, (int)P.tiles_last, nullptr, fb, N, P.M_last, P.M_last, w.fm, fb, nullptr,
-                             0, st));
+                             0, st, nullptr, a.s_ptr, nullptr));
         count_launches(1);
     }
     CK(cudaMemsetAsync(w.nflag, 0, sizeof(unsigned long long), st));
@@ -805,7 +804,7 @@ sre_status batch_main(const std::vector<BucketPlan> &B, const BatchWS &w, int co
                 c.n_fam = nf;
                 CS(run_transform(b.P, c, SRC_PSI_FAMILY, DST_MOMENTS, w.inter, st));
                 CK(launch_fam_reduce(w.tiles, nf, (int)b.P.tiles_last, nullptr, fb, b.N, b.P.M_last, b.P.M_last,
-                                     w.fm, fb - f0, nullptr, 0, st));
+                                     w.fm, fb - f0, nullptr, 0, st, nullptr, nullptr, w.s_list + b.off));
                 count_launches(1);
             }
             CK(launch_state_totals(w.fm, f0, b.N, c0, c1 - c0, w.totals + TOT_N * (size_t)b.off, b.flags,
@@ -1133,9 +1132,11 @@ struct MixedWS {
     float2 *C;
     TilePartial *tiles;
     FamMoments *fm;
+    void *planes;      // BF16 split planes of Psi for the tensor-core Gram kernel (one K chunk)
+    int *err;          // device error word
 };
 
-void layout_mixed(Arena &A, int NA, MixedWS &w) {
+void layout_mixed(Arena &A, int N, int NA, MixedWS &w) {
     const unsigned long long dA = 1ULL << NA;
     w.scal = A.take<double>(SCAL_N);
     w.npart = A.take<double>(NORM_BLOCKS);
@@ -1144,52 +1145,32 @@ void layout_mixed(Arena &A, int NA, MixedWS &w) {
     w.C = A.take<float2>(dA * dA);
     w.tiles = A.take<TilePartial>(dA);
     w.fm = A.take<FamMoments>(dA);
-}
-
-std::mutex g_blas_mu;
-std::vector<cublasHandle_t> g_blas;
-
-sre_status blas_handle(cublasHandle_t *h) {
-    int dev = 0;
-    CK(cudaGetDevice(&dev));
-    std::lock_guard<std::mutex> lk(g_blas_mu);
-    if ((int)g_blas.size() <= dev) g_blas.resize(dev + 1, nullptr);
-    if (!g_blas[dev]) {
-        cublasHandle_t nh = nullptr;
-        if (cublasCreate(&nh) != CUBLAS_STATUS_SUCCESS) return fail(SRE_ECUDA, "cublasCreate failed");
-        g_blas[dev] = nh;
-    }
-    *h = g_blas[dev];
-    return SRE_OK;
+    w.planes = A.take<unsigned char>(gram_plane_bytes(N, NA));
+    w.err = A.take<int>(1);
 }
 
 // SRE of the reduced state on the first N_A qubits (SM, mixed states):
-// C = Psi Psi^H by one cuBLAS GEMM (Psi = psi viewed column-major d_A x d_B), then
-// every family x_A of the N_A-qubit system through the single-pass transform
-// with the h(a) = C[a][a ^ x_A] prologue and the fused moments, then the
-// fixed-order FP64 totals; Eq. Msre-mixed on the host.
+// C = Psi Psi^H on the tensor cores (Psi = psi viewed column-major d_A x d_B;
+// k_gram.cu), then every family x_A of the N_A-qubit system through the
+// single-pass transform with the h(a) = C[a][a ^ x_A] prologue and the fused
+// moments, then the fixed-order FP64 totals; Eq. Msre-mixed on the host.
 sre_status mixed_impl(const void *psi, int N, int NA, void *ws, size_t ws_bytes, cudaStream_t st,
                       sre_mixed_result *out) {
     Arena dry(nullptr);
     MixedWS w;
-    layout_mixed(dry, NA, w);
+    layout_mixed(dry, N, NA, w);
     void *base = nullptr;
     CS(resolve_workspace(ws, ws_bytes, dry.off, &base));
     Arena A(base);
-    layout_mixed(A, NA, w);
-    const unsigned long long dA = 1ULL << NA, dB = 1ULL << (N - NA);
+    layout_mixed(A, N, NA, w);
+    const unsigned long long dA = 1ULL << NA;
     CK(launch_norm2((const float2 *)psi, N, w.scal, w.npart, st));
     count_launches(2);
-    cublasHandle_t h = nullptr;
-    CS(blas_handle(&h));
-    if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) return fail(SRE_ECUDA, "cublasSetStream failed");
-    // C = Psi Psi^H as one complex GEMM (both triangles), FP32 emulated on the
-    // BF16 tensor cores: cuBLAS splits each FP32 input into three BF16 parts
-    const cuComplex one = make_cuComplex(1.0f, 0.0f), zero = make_cuComplex(0.0f, 0.0f);
-    if (cublasGemmEx(h, CUBLAS_OP_N, CUBLAS_OP_C, (int)dA, (int)dA, (int)dB, &one, psi, CUDA_C_32F, (int)dA, psi,
-                     CUDA_C_32F, (int)dA, &zero, w.C, CUDA_C_32F, (int)dA, CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
-                     CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
-        return fail(SRE_ECUDA, "cublasGemmEx failed (N=%d, N_A=%d)", N, NA);
+    CK(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+    int gl = 0;
+    cudaError_t ge = launch_gram((const float2 *)psi, N, NA, w.C, w.planes, w.err, &gl, st);
+    count_launches(gl);
+    if (ge != cudaSuccess) return fail(SRE_ECUDA, "Gram matrix (N=%d, N_A=%d): %s", N, NA, cudaGetErrorString(ge));
     PassArgs a;
     memset(&a, 0, sizeof a);
     a.N = NA;
@@ -1206,7 +1187,8 @@ sre_status mixed_impl(const void *psi, int N, int NA, void *ws, size_t ws_bytes,
     cudaError_t e = launch_f32_single(NA - 1, SRC_GRAM, DST_MOMENTS, a, st);
     if (e != cudaSuccess) return fail(SRE_ECUDA, "mixed-state transform (N_A=%d): %s", NA, cudaGetErrorString(e));
     count_launches(1);
-    CK(launch_fam_reduce(w.tiles, (long long)dA, 1, nullptr, 0, NA, NA - 1, NA - 1, w.fm, 0, nullptr, 0, st));
+    CK(launch_fam_reduce(w.tiles, (long long)dA, 1, nullptr, 0, NA, NA - 1, NA - 1, w.fm, 0, nullptr, 0, st, nullptr,
+                         a.s_ptr, nullptr));
     count_launches(1);
     unsigned long long *no_flags = nullptr;
     CK(launch_exact_totals(w.fm, (long long)dA, w.epart, EXACT_PARTS, w.etot, no_flags, nullptr, st));
@@ -1214,7 +1196,10 @@ sre_status mixed_impl(const void *psi, int N, int NA, void *ws, size_t ws_bytes,
     double T[TOT_N + 1];
     CK(cudaMemcpyAsync(T, w.etot, TOT_N * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(T + TOT_N, w.scal + SCAL_NORM2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (herr & SRE_ERR_TIMEOUT) return fail(SRE_ETIMEOUT, "Gram matrix: a bounded wait ran out");
     if (!(T[TOT_N] > 0.0)) return fail(SRE_EZERO, "psi has zero norm");
     memset(out, 0, sizeof *out);
     const double da = (double)dA;
@@ -1453,7 +1438,7 @@ sre_status sre_mc(const void *psi, int N, int mode, long long n_x, int z_per_x, 
         b.n_fam = nf;
         CS(run_transform(P, b, SRC_PSI_FAMILY, DST_MOMENTS, w.inter, st, (timing && nf == step) ? &T : nullptr));
         CK(launch_fam_reduce(w.tiles, nf, (int)P.tiles_last, xs_run, fb, N, P.M_last, P.RL, w.fm, fb,
-                             (marg && !fine) ? w.Wf : nullptr, nr, st, perm));
+                             (marg && !fine) ? w.Wf : nullptr, nr, st, perm, a.s_ptr, nullptr));
         count_launches(1);
         if (marg) {
             CK(launch_zrange_select(w.Wf, nr, nf, fb, z_per_x, seed, counter0, w.draws, perm, st));
@@ -1670,7 +1655,7 @@ sre_status sre_mixed_workspace_bytes(int N, int N_A, size_t *bytes) {
     if (!bytes) return fail(SRE_EINVAL, "bytes is NULL");
     Arena dry(nullptr);
     MixedWS w;
-    layout_mixed(dry, N_A, w);
+    layout_mixed(dry, N, N_A, w);
     *bytes = dry.off;
     return SRE_OK;
 }

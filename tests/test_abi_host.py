@@ -139,9 +139,12 @@ def test_argument_errors_do_not_touch_the_gpu(L):
 
 
 def test_mixed_workspace_bytes(L):
-    # dominated by the d_A x d_A complex64 Gram matrix
-    assert sre.sre_mixed_workspace_bytes(20, 10) > 8 * 4 ** 10
-    assert sre.sre_mixed_workspace_bytes(20, 10) < 8 * 4 ** 10 + (1 << 20)
+    # the d_A x d_A complex64 Gram matrix and the six BF16 split planes of Psi
+    # (d_A x d_B each) that the tensor-core Gram kernel reads
+    want = 8 * 4 ** 10 + 6 * 2 * 2 ** 20
+    assert want < sre.sre_mixed_workspace_bytes(20, 10) < want + (1 << 20)
+    # small subsystems take the SIMT route and no planes
+    assert sre.sre_mixed_workspace_bytes(12, 6) < 8 * 4 ** 6 + (1 << 20)
 
 
 def test_structs_match_header_layout():

@@ -79,3 +79,35 @@ def test_mixed_n18_sampled_against_oracle(sre):
     r = sre.sre_mixed(dev(psi), NA)
     ref = oracle.sre_mixed(psi, NA)
     assert np.max(np.abs(np.array(r["M"][1:]) - ref["M"][1:])) < TOL_M and abs(r["S2"] - ref["S2"]) < TOL_M
+
+
+def test_mixed_gram_tiles_vs_oracle(sre):
+    """d_A = 1024: an 8 x 8 grid of 128 x 128 Gram tiles on the tensor cores
+    (36 computed, the rest written as conjugate transposes), 8 K blocks."""
+    N, NA = 18, 10
+    psi = inputs.unnormalised_gaussian_state(N, 1810)
+    r = sre.sre_mixed(dev(psi), NA)
+    ref = oracle.sre_mixed(psi, NA)
+    assert abs(r["S2"] - ref["S2"]) < TOL_M
+    assert np.max(np.abs(np.array(r["M"][1:]) - ref["M"][1:])) < TOL_M
+    assert np.allclose(r["W"][:3], ref["W"][:3], rtol=1e-5)
+
+
+def test_mixed_gram_chunked_k(sre):
+    """N = 28, N_A = 7: the split planes hold 2^20 of the 2^21 columns of
+    Psi, so the Gram matrix is accumulated over two chunks. A product state
+    |T>^7 (x) (Haar on 21 qubits) has rho_A pure (S_2 = 0) with M_2 =
+    7 log2(4/3), and the GHZ state has rho_A = (|0><0| + |1..1><1..1|)/2
+    (S_2 = 1, M_2 = 0)."""
+    N, NA = 28, 7
+    a = torch.from_numpy(inputs.t_product_state(NA, NA)).cuda()
+    b = torch.from_numpy(inputs.haar_state(N - NA, 28)).cuda()
+    psi = (b[:, None] * a[None, :]).reshape(-1).contiguous()      # index a + 2^NA e
+    r = sre.sre_mixed(psi, NA)
+    assert abs(r["S2"]) < 1e-5
+    assert abs(r["M"][1] - NA * math.log2(4 / 3)) < TOL_M
+    del psi, b
+    g = torch.zeros(1 << N, dtype=torch.complex64, device="cuda")
+    g[0] = g[-1] = 1.0
+    r = sre.sre_mixed(g, NA)
+    assert abs(r["S2"] - 1.0) < TOL_M and abs(r["M"][1]) < TOL_M
