@@ -20,7 +20,9 @@
 //    per block (D_re, D_im: 128 TMEM columns each); the four warps write the
 //    tile and, off the diagonal, its conjugate transpose. With several chunks
 //    of K the tile is added to C.
-// 3. gram_simt_kernel: small shapes (d_A < 128 or d_B < 32), FP32 products
+// 3. gram_diag_kernel: the diagonal (the trace of rho_A and the x_A = 0
+//    family) summed in FP64 and written over the tiles' diagonal.
+// 4. gram_simt_kernel: small shapes (d_A < 128 or d_B < 32), FP32 products
 //    summed in FP64 per entry.
 #include "k_tc05.cuh"
 #include "sre_internal.cuh"
@@ -221,6 +223,23 @@ __global__ void __launch_bounds__(256) gram_simt_kernel(const float2 *psi, int N
     C[i + dA * j] = make_float2((float)re, (float)im);
 }
 
+// Diagonal of C, sum_e |psi(a, e)|^2, in FP64 (written over the tensor-core
+// tile's diagonal). It holds the trace of rho_A and every c_{0,z}, which
+// dominate the moments of a strongly mixed rho_A; the tensor cores' FP32
+// accumulation leaves them about 1e-6 off, summed in FP64 they carry only
+// the final FP32 rounding.
+__global__ void __launch_bounds__(256) gram_diag_kernel(const float2 *psi, int NA, int NB, float2 *C) {
+    const unsigned long long dA = 1ULL << NA, dB = 1ULL << NB;
+    const unsigned long long a = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= dA) return;
+    double acc = 0.0;
+    for (unsigned long long e = 0; e < dB; ++e) {
+        const float2 v = psi[a + dA * e];
+        acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+    }
+    C[a + dA * a] = make_float2((float)acc, 0.0f);
+}
+
 // K chunk (columns of Psi per split) bounded so the planes stay within 2^27 elements each
 int gram_chunk_log2(int N, int NA) {
     const int nb = N - NA;
@@ -264,7 +283,9 @@ cudaError_t launch_gram(const float2 *psi, int N, int NA, float2 *C, void *plane
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    gram_diag_kernel<<<(unsigned)((dA + 255) / 256), 256, 0, st>>>(psi, NA, NB, C);
+    *launches += 1;
+    return cudaGetLastError();
 }
 
 } // namespace sre

@@ -87,27 +87,19 @@ cudaError_t launch_norm2(const float2 *psi, int N, double *scal, double *partial
     return cudaGetLastError();
 }
 
-// tile partials -> family sums in c units; z-range weights scattered to
-// W[fam][range]. The tiles hold sums of q = h^2 (transform units); with
-// sig = sc^2 (sc = 2 s for x != 0, s for x = 0; s from s_list[F >> N] when
-// several states share the launch, else *s_ptr):
-//   sum c^2 = sig Q1, sum c^4 = sig^2 Q2, sum c^6 = sig^3 Q3,
-//   sum c^2 log2 c^2 = sig (QL + log2(sig) Q1).
+// tile partials -> family sums; z-range weights scattered to W[fam][range]
 __global__ void __launch_bounds__(256) fam_reduce_kernel(const TilePartial *tp, long long n_fam, int tiles,
                                                          const unsigned long long *xs, long long fam_base,
                                                          int N, int M_last, int RL, FamMoments *fm,
                                                          long long fm_base, float *W, long long nr,
-                                                         const unsigned long long *perm, const double *s_ptr,
-                                                         const double *s_list) {
+                                                         const unsigned long long *perm) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long f = (long long)blockIdx.x * 8 + warp;
     if (f >= n_fam) return;
     const int n = N - 1;
-    const unsigned long long F = xs ? xs[fam_base + f] : (unsigned long long)(fam_base + f);
-    const unsigned long long x = F & ((1ULL << N) - 1ULL);
+    unsigned long long x = xs ? xs[fam_base + f] : (unsigned long long)(fam_base + f);
+    x &= (1ULL << N) - 1ULL;
     const int j = x ? 63 - __clzll((long long)x) : n;
-    const double s = s_list ? s_list[F >> N] : *s_ptr;
-    const double g1 = x ? 4.0 * s * s : s * s;
     double m0 = 0, m1 = 0, m2 = 0, m3 = 0, c = 0;
     for (int t = lane; t < tiles; t += 32) {
         const TilePartial &p = tp[(size_t)f * tiles + t];
@@ -116,8 +108,8 @@ __global__ void __launch_bounds__(256) fam_reduce_kernel(const TilePartial *tp, 
             const unsigned long long zt = (unsigned long long)t << M_last;
             const unsigned long long rA = insert0(zt, j) >> RL;
             const unsigned long long rB = (j < RL) ? rA + 1 : rA + (1ULL << (j - RL));
-            W[(size_t)f * nr + rA] = (float)(g1 * p.w[0]);
-            W[(size_t)f * nr + rB] = (float)(g1 * p.w[1]);
+            W[(size_t)f * nr + rA] = (float)p.w[0];
+            W[(size_t)f * nr + rB] = (float)p.w[1];
         }
     }
 #pragma unroll
@@ -130,21 +122,16 @@ __global__ void __launch_bounds__(256) fam_reduce_kernel(const TilePartial *tp, 
     }
     if (lane == 0) {
         FamMoments &o = fm[perm ? (long long)perm[fam_base + f] : fm_base + f];
-        const double g2 = g1 * g1;
-        o.m[0] = g1 * m0;
-        o.m[1] = g2 * m1;
-        o.m[2] = g2 * g1 * m2;
-        o.m[3] = g1 * (m3 + log2(g1) * m0);
+        o.m[0] = m0; o.m[1] = m1; o.m[2] = m2; o.m[3] = m3;
         o.cand = (unsigned long long)c;
     }
 }
 
 cudaError_t launch_fam_reduce(const TilePartial *tp, long long n_fam, int tiles, const unsigned long long *xs,
                               long long fam_base, int N, int M_last, int RL, FamMoments *fm, long long fm_base,
-                              float *W, long long nr, cudaStream_t st, const unsigned long long *perm,
-                              const double *s_ptr, const double *s_list) {
+                              float *W, long long nr, cudaStream_t st, const unsigned long long *perm) {
     fam_reduce_kernel<<<(unsigned)((n_fam + 7) / 8), 256, 0, st>>>(tp, n_fam, tiles, xs, fam_base, N, M_last, RL,
-                                                                  fm, fm_base, W, nr, perm, s_ptr, s_list);
+                                                                  fm, fm_base, W, nr, perm);
     return cudaGetLastError();
 }
 

@@ -45,12 +45,10 @@ struct NullDirectArgs {
 };
 cudaError_t launch_null_direct(const NullDirectArgs &a, long long n_fam, cudaStream_t st);
 // per-family sums of a launch's tile partials into fm[fm_base + slot], or,
-// with perm (processing order -> family index), into fm[perm[fam_base + slot]];
-// s = 1/|psi|^2 from *s_ptr, or from s_list[F >> N] in multi-state launches
+// with perm (processing order -> family index), into fm[perm[fam_base + slot]]
 cudaError_t launch_fam_reduce(const TilePartial *tp, long long n_fam, int tiles, const unsigned long long *xs,
                               long long fam_base, int N, int M_last, int RL, FamMoments *fm, long long fm_base,
-                              float *W, long long nr, cudaStream_t st, const unsigned long long *perm,
-                              const double *s_ptr, const double *s_list);
+                              float *W, long long nr, cudaStream_t st, const unsigned long long *perm = nullptr);
 cudaError_t launch_exact_totals(const FamMoments *fm, long long n_fam, double *partial, int n_part,
                                 double *out, unsigned long long *flag_list, unsigned long long *n_flag,
                                 cudaStream_t st);

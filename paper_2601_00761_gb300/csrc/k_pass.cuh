@@ -267,32 +267,28 @@ __device__ __forceinline__ float lg2_ftz(float x) {
     return r;
 }
 
-// Fused moment sums of Algorithm 1 over one thread's E transformed elements,
-// in units of the transform output: for a pair h of transformed values the
-// Pauli expectations are c = sc * h with one scale sc per family, so with
-// q = h^2 the running packed sums of q, q^2, q^3 and q log2 q give the
-// family's sums of c^2, c^4, c^6 and c^2 log2 c^2 after one multiplication by
-// sc^2, sc^4, sc^6 and sc^2 (plus sc^2 log2(sc^2) sum q) per tile. FLT_MIN is
-// added inside the log only: it leaves every q >= 2^-102 unchanged and makes
-// q = 0 contribute 0. SWAP orders each pair so that c(z0) comes first (bit k
-// of pm set: swap); CAND keeps the running maximum of q for the nullity
-// candidates.
+// Fused moment sums of Algorithm 1 over one thread's E transformed elements:
+// c = sc * h (a pair of Pauli expectations), q = c^2, and packed running
+// sums of q, q^2, q^3 and q log2 q. FLT_MIN is added inside the log only:
+// it leaves every q >= 2^-102 unchanged and makes q = 0 contribute 0.
+// SWAP orders each pair so that c(z0) comes first (bit k of pm set: swap);
+// CAND keeps the running maximum of q for the nullity candidates.
 template <int E, bool SWAP, bool CAND>
-__device__ __forceinline__ void moment_sums(const float2 (&h)[E], uint32_t pm, float2 &s2, float2 &s4,
+__device__ __forceinline__ void moment_sums(const float2 (&h)[E], float2 sc, uint32_t pm, float2 &s2, float2 &s4,
                                             float2 &s6, float2 &sl, float &qmax) {
     const float2 tiny = make_float2(1.17549435e-38f, 1.17549435e-38f);
 #pragma unroll
     for (int k = 0; k < E; ++k) {
-        float2 c = h[k];
+        float2 c = mul2(sc, h[k]);
         if constexpr (SWAP) {
             if ((pm >> k) & 1u) c = make_float2(c.y, c.x);
         }
         const float2 q = mul2(c, c);
-        const float2 qt = fma2(c, c, tiny);
         const float2 q2 = mul2(q, q);
         s2 = add2(s2, q);
         s4 = add2(s4, q2);
         s6 = fma2(q2, q, s6);
+        const float2 qt = add2(q, tiny);
         sl = fma2(q, make_float2(lg2_ftz(qt.x), lg2_ftz(qt.y)), sl);
         if constexpr (CAND) qmax = fmaxf(qmax, fmaxf(q.x, q.y));
     }
@@ -305,8 +301,8 @@ __device__ __forceinline__ void moment_sums(const float2 (&h)[E], uint32_t pm, f
 // being ordered (c(z0)^2, c(z1)^2); with j < ZR_FINE a half-warp's 2^9 z'
 // yield both c of 2^10 consecutive z. Each range of the family is written by
 // exactly one warp or half-warp.
-__device__ __forceinline__ void fine_range_weights(float2 s2, float sig, unsigned long long x, int j,
-                                                   unsigned long long half, uint32_t zb, float *row, bool active) {
+__device__ __forceinline__ void fine_range_weights(float2 s2, unsigned long long x, int j, unsigned long long half,
+                                                   uint32_t zb, float *row, bool active) {
     const int lane = threadIdx.x & 31;
     const bool split = (x == 0) || (j >= ZR_FINE);
     unsigned long long z0, z1;
@@ -327,11 +323,11 @@ __device__ __forceinline__ void fine_range_weights(float2 s2, float sig, unsigne
         wa += __shfl_xor_sync(0xffffffffu, wa, 16);
         wb += __shfl_xor_sync(0xffffffffu, wb, 16);
         if (active && lane == 0) {
-            row[z0 >> ZR_FINE] = sig * wa;
-            row[z1 >> ZR_FINE] = sig * wb;
+            row[z0 >> ZR_FINE] = wa;
+            row[z1 >> ZR_FINE] = wb;
         }
     } else if (active && (lane & 15) == 0) {
-        row[z0 >> ZR_FINE] = sig * wa;
+        row[z0 >> ZR_FINE] = wa;
     }
 }
 
@@ -423,7 +419,6 @@ __device__ __forceinline__ bool fwht_pass_body(const PassArgs &a, int rep) {
     // ---------------------------------------------------------- prologue
     pass_prologue<Cfg, SRC>(v, a, psi, slot, x, j, half, gbase, t);
 
-
     // --------------------------------------------------------- transform
     if constexpr (PREC == 0) tile_transform<Cfg>(v, sm, t, grp);
     else tc_tile_transform<Cfg, PREC>(v, sm, t, grp);
@@ -514,14 +509,9 @@ __device__ __forceinline__ bool fwht_pass_body(const PassArgs &a, int rep) {
         // a packed pair: moments only need the unordered pair. The z-range
         // weights are read off the packed sum of q: a tile spans two ranges
         // of 2^M consecutive z (range A, then range B).
-        // Sums run on the transform outputs h; c = sc h with sc = 2 s (x != 0)
-        // or s (x = 0, h = (Re + Im, Re - Im)), so each sum is scaled by a
-        // power of sig = sc^2: here (FP32) for the range weights that go
-        // straight to the range rows, per family (FP64) for the tile partials.
         float s;
         if constexpr (S_SHARED) s = s_sh[grp];
         else s = (float)(*s_ptr);
-        const float sig = x ? 4.0f * s * s : s * s;
         const uint32_t zb = (uint32_t)gbase | Cfg::elem(t, 0, 0);
         float2 s2 = make_float2(0.f, 0.f), s4 = s2, s6 = s2, sl = s2, w = s2;
         float qmax = 0.f;
@@ -530,6 +520,7 @@ __device__ __forceinline__ bool fwht_pass_body(const PassArgs &a, int rep) {
         constexpr bool FINE = SRC == SRC_BUF && Cfg::M > ZR_FINE;
         constexpr int RLS = FINE ? ZR_FINE : Cfg::M;
         if (x) {
+            const float2 sc = make_float2(2.0f * s, 2.0f * s);
             if (wr && j >= RLS) {
                 // every c(z0) and every c(z1) of a range block lie in ranges
                 // of their own: order each pair as (c(z0)^2, c(z1)^2) and s2
@@ -537,12 +528,12 @@ __device__ __forceinline__ bool fwht_pass_body(const PassArgs &a, int rep) {
                 // z' = zb | k (z0 then carries the Im part).
                 const uint32_t xd = (uint32_t)((x & ((1ULL << j) - 1ULL)) | ((x >> (j + 1)) << j));
                 const uint32_t pm = walsh_mask5(xd & (Cfg::E - 1)) ^ ((__popc(xd & zb) & 1) ? 0xFFFFFFFFu : 0u);
-                if (cand) moment_sums<Cfg::E, true, true>(v, pm, s2, s4, s6, sl, qmax);
-                else moment_sums<Cfg::E, true, false>(v, pm, s2, s4, s6, sl, qmax);
+                if (cand) moment_sums<Cfg::E, true, true>(v, sc, pm, s2, s4, s6, sl, qmax);
+                else moment_sums<Cfg::E, true, false>(v, sc, pm, s2, s4, s6, sl, qmax);
                 w = s2;
             } else {
-                if (cand) moment_sums<Cfg::E, false, true>(v, 0u, s2, s4, s6, sl, qmax);
-                else moment_sums<Cfg::E, false, false>(v, 0u, s2, s4, s6, sl, qmax);
+                if (cand) moment_sums<Cfg::E, false, true>(v, sc, 0u, s2, s4, s6, sl, qmax);
+                else moment_sums<Cfg::E, false, false>(v, sc, 0u, s2, s4, s6, sl, qmax);
                 if (wr && !FINE) {
                     // both c of a pair lie in the range picked by bit M-1 of z'
                     constexpr int RBIT = Cfg::M > 0 ? Cfg::M - 1 : 0;
@@ -553,7 +544,8 @@ __device__ __forceinline__ bool fwht_pass_body(const PassArgs &a, int rep) {
                         // tiles of at most 2 RB bits: the range bit is a slot bit
 #pragma unroll
                         for (int k = 0; k < Cfg::E; ++k) {
-                            const float qq = v[k].x * v[k].x + v[k].y * v[k].y;
+                            const float2 c = mul2(sc, v[k]);
+                            const float qq = c.x * c.x + c.y * c.y;
                             if ((k >> RBIT) & 1) w.y += qq;
                             else w.x += qq;
                         }
@@ -561,28 +553,27 @@ __device__ __forceinline__ bool fwht_pass_body(const PassArgs &a, int rep) {
                 }
             }
         } else {
+            const float2 sc = make_float2(s, s);
             typename Cfg::C2 hs[Cfg::E];
 #pragma unroll
             for (int k = 0; k < Cfg::E; ++k) hs[k] = make_float2(v[k].x + v[k].y, v[k].x - v[k].y);
-            if (cand) moment_sums<Cfg::E, false, true>(hs, 0u, s2, s4, s6, sl, qmax);
-            else moment_sums<Cfg::E, false, false>(hs, 0u, s2, s4, s6, sl, qmax);
+            if (cand) moment_sums<Cfg::E, false, true>(hs, sc, 0u, s2, s4, s6, sl, qmax);
+            else moment_sums<Cfg::E, false, false>(hs, sc, 0u, s2, s4, s6, sl, qmax);
             w = s2;                    // z' -> range A, z' + d/2 -> range B
         }
         if constexpr (FINE) {
-            if (wr) fine_range_weights(s2, sig, x, j, half, zb, a.rw_out + (size_t)slot * (size_t)a.rw_stride, active);
+            if (wr) fine_range_weights(s2, x, j, half, zb, a.rw_out + (size_t)slot * (size_t)a.rw_stride, active);
         }
         float acc[6] = {s2.x + s2.y, s4.x + s4.y, s6.x + s6.y, sl.x + sl.y, w.x, w.y};
         double out[6];
         float omx;
         group_reduce<Cfg::T, Cfg::NT, 6>(acc, qmax, out, omx, red);
         if (active && t == 0) {
-            // sums in transform units; fam_reduce_kernel scales them to c units
-            // once per family (powers of sig = sc^2 and the log2 sig term)
             const long long tiles = (long long)(half >> Cfg::M) > 0 ? (long long)(half >> Cfg::M) : 1;
             TilePartial &tp = a.tile_out[(size_t)slot * (size_t)tiles + tile];
             tp.m[0] = out[0]; tp.m[1] = out[1]; tp.m[2] = out[2]; tp.m[3] = out[3];
             tp.w[0] = out[4]; tp.w[1] = out[5];
-            tp.cand = (cand && omx * sig > a.cand_thr * a.cand_thr) ? 1u : 0u;
+            tp.cand = (cand && omx > a.cand_thr * a.cand_thr) ? 1u : 0u;
         }
     }
     return true;

@@ -644,7 +644,7 @@ sre_status exact_impl(const void *psi, int N, const sre_opts &o, void *ws, size_
         b.n_fam = nf;
         CS(run_transform(P, b, SRC_PSI_FAMILY, DST_MOMENTS, w.inter, st));
         CK(launch_fam_reduce(w.tiles, nf, (int)P.tiles_last, nullptr, fb, N, P.M_last, P.M_last, w.fm, fb, nullptr,
-                             0, st, nullptr, a.s_ptr, nullptr));
+                             0, st));
         count_launches(1);
     }
     CK(cudaMemsetAsync(w.nflag, 0, sizeof(unsigned long long), st));
@@ -804,7 +804,7 @@ sre_status batch_main(const std::vector<BucketPlan> &B, const BatchWS &w, int co
                 c.n_fam = nf;
                 CS(run_transform(b.P, c, SRC_PSI_FAMILY, DST_MOMENTS, w.inter, st));
                 CK(launch_fam_reduce(w.tiles, nf, (int)b.P.tiles_last, nullptr, fb, b.N, b.P.M_last, b.P.M_last,
-                                     w.fm, fb - f0, nullptr, 0, st, nullptr, nullptr, w.s_list + b.off));
+                                     w.fm, fb - f0, nullptr, 0, st));
                 count_launches(1);
             }
             CK(launch_state_totals(w.fm, f0, b.N, c0, c1 - c0, w.totals + TOT_N * (size_t)b.off, b.flags,
@@ -1187,8 +1187,7 @@ sre_status mixed_impl(const void *psi, int N, int NA, void *ws, size_t ws_bytes,
     cudaError_t e = launch_f32_single(NA - 1, SRC_GRAM, DST_MOMENTS, a, st);
     if (e != cudaSuccess) return fail(SRE_ECUDA, "mixed-state transform (N_A=%d): %s", NA, cudaGetErrorString(e));
     count_launches(1);
-    CK(launch_fam_reduce(w.tiles, (long long)dA, 1, nullptr, 0, NA, NA - 1, NA - 1, w.fm, 0, nullptr, 0, st, nullptr,
-                         a.s_ptr, nullptr));
+    CK(launch_fam_reduce(w.tiles, (long long)dA, 1, nullptr, 0, NA, NA - 1, NA - 1, w.fm, 0, nullptr, 0, st));
     count_launches(1);
     unsigned long long *no_flags = nullptr;
     CK(launch_exact_totals(w.fm, (long long)dA, w.epart, EXACT_PARTS, w.etot, no_flags, nullptr, st));
@@ -1438,7 +1437,7 @@ sre_status sre_mc(const void *psi, int N, int mode, long long n_x, int z_per_x, 
         b.n_fam = nf;
         CS(run_transform(P, b, SRC_PSI_FAMILY, DST_MOMENTS, w.inter, st, (timing && nf == step) ? &T : nullptr));
         CK(launch_fam_reduce(w.tiles, nf, (int)P.tiles_last, xs_run, fb, N, P.M_last, P.RL, w.fm, fb,
-                             (marg && !fine) ? w.Wf : nullptr, nr, st, perm, a.s_ptr, nullptr));
+                             (marg && !fine) ? w.Wf : nullptr, nr, st, perm));
         count_launches(1);
         if (marg) {
             CK(launch_zrange_select(w.Wf, nr, nf, fb, z_per_x, seed, counter0, w.draws, perm, st));

@@ -78,11 +78,9 @@ __host__ __device__ __forceinline__ unsigned long long insert0(unsigned long lon
 // bits of the device error word
 constexpr int SRE_ERR_TIMEOUT = 1;      // a bounded wait ran out
 
-// Per-tile partial sums of the last pass (FP64), in units of the transform
-// output h (c = sc h, sc = 2 s for x != 0, s for x = 0; q = h^2): sum q,
-// sum q^2, sum q^3, sum q log2 q, the two z-range weights (sum q) the tile
-// contributes to, and the FP32 nullity candidate flag (some |c| above
-// PassArgs::cand_thr). fam_reduce_kernel turns them into c units.
+// Per-tile partial sums of the last pass (FP64): c^2, c^4, c^6, c^2 log2 c^2,
+// the two z-range weights the tile contributes to, and the FP32 nullity
+// candidate flag (some |c| above PassArgs::cand_thr).
 struct TilePartial {
     double m[4];
     double w[2];
