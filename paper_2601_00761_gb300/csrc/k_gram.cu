@@ -17,9 +17,10 @@
 //    K in blocks of 32 (64-byte rows, TMA with the 64-byte swizzle), a
 //    two-stage ring of 12 boxes per block (X_I, Y_I, X_J, Y_J, three parts
 //    each, 96 KB per stage); one thread issues the TMA loads and the 48 MMAs
-//    per block (D_re, D_im: 128 TMEM columns each); the four warps write the
-//    tile and, off the diagonal, its conjugate transpose. With several chunks
-//    of K the tile is added to C.
+//    per block into a fresh TMEM accumulator (D_re, D_im), alternating
+//    between two; eight warps add each block's accumulator into FP32
+//    register sums and write the tile and, off the diagonal, its conjugate
+//    transpose. With several chunks of K the tile is added to C.
 // 3. gram_diag_kernel: the diagonal (the trace of rho_A and the x_A = 0
 //    family) summed in FP64 and written over the tiles' diagonal.
 // 4. gram_simt_kernel: small shapes (d_A < 128 or d_B < 32), FP32 products
@@ -73,7 +74,9 @@ constexpr int GRAM_T = 128;                    // tile rows / columns
 constexpr int GRAM_KB = 32;                    // K per block (64-byte rows)
 constexpr uint32_t GRAM_BOX = GRAM_T * 64;     // bytes of one 128 x 32 BF16 box
 constexpr uint32_t GRAM_STAGE = 12 * GRAM_BOX; // X_I, Y_I, X_J, Y_J x 3 parts
-constexpr size_t GRAM_SMEM = 1024 + 2 * (size_t)GRAM_STAGE + 128;
+constexpr int GRAM_EPI = 256;                  // epilogue threads (8 warps)
+constexpr int GRAM_THREADS = GRAM_EPI + 32;    // + one warp issuing TMA and MMA
+constexpr size_t GRAM_SMEM = 1024 + 2 * (size_t)GRAM_STAGE + 256;
 
 // tile index -> (I, J) with I <= J over nt x nt tiles (row-major upper triangle)
 __device__ __forceinline__ void tri_tile(int idx, int nt, int &I, int &J) {
@@ -83,15 +86,28 @@ __device__ __forceinline__ void tri_tile(int idx, int nt, int &I, int &J) {
     J = i + rem;
 }
 
-__global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__ CUtensorMap tp, float2 *C, int NA,
-                                                         int dBc_log2, int accumulate_c, int *err) {
+// The tensor cores' FP32 accumulation is not rounded to nearest: summed over
+// a long K in one accumulator, coherent terms (a diagonal-dominant or pure
+// rho_A) lose about 2^-24 of the sum per addition. Each K block therefore
+// starts a fresh accumulator in one of two TMEM buffers (columns 0..255 and
+// 256..511: D_re, D_im), and the epilogue warps add it, while the next block
+// runs, into FP32 register sums (round to nearest): 24 tensor-core additions
+// per block instead of 24 per block times the number of blocks.
+//
+// Warp 8 (lane 0) loads the stages by TMA and issues the MMAs; warps 0..7
+// drain the TMEM buffers (warp w reads lanes 32 (w % 4) .. + 31, columns
+// 64 (w / 4) .. + 63 of D_re and D_im) and write the tile at the end.
+__global__ void __launch_bounds__(GRAM_THREADS, 1) gram_tc_kernel(const __grid_constant__ CUtensorMap tp, float2 *C,
+                                                                  int NA, int dBc_log2, int accumulate_c, int *err) {
     using namespace tc05;
     extern __shared__ unsigned char smraw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-    uint64_t *full = reinterpret_cast<uint64_t *>(base + 2 * GRAM_STAGE);
-    uint64_t *done = full + 2;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 2);
-    int *last = reinterpret_cast<int *>(tslot + 1);
+    uint64_t *full = reinterpret_cast<uint64_t *>(base + 2 * GRAM_STAGE);   // [2] stage loaded
+    uint64_t *sfree = full + 2;                                           // [2] stage read by the MMAs
+    uint64_t *tready = sfree + 2;                                         // [2] TMEM buffer holds a block
+    uint64_t *tfree = tready + 2;                                         // [2] TMEM buffer drained
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(tfree + 2);
+    int *abort_flag = reinterpret_cast<int *>(tslot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned long long dA = 1ULL << NA;
     const int nt = (int)(dA / GRAM_T);
@@ -99,99 +115,126 @@ __global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__
     tri_tile((int)blockIdx.x, nt, I, J);
     const int r0I = I * GRAM_T, r0J = J * GRAM_T;
     if (warp == 0) {
-        tmem_alloc(tslot, 256);
+        tmem_alloc(tslot, 512);
         tmem_relinquish();
     }
-    if (threadIdx.x == 32) {
-        mbar_init(full, 1);
-        mbar_init(full + 1, 1);
-        mbar_init(done, 1);
-        mbar_init(done + 1, 1);
+    if (threadIdx.x == GRAM_EPI) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(full + i, 1);
+            mbar_init(sfree + i, 1);
+            mbar_init(tready + i, 1);
+            mbar_init(tfree + i, GRAM_EPI);
+        }
+        *abort_flag = 0;
         fence_barrier_init();
         prefetch_tmap(&tp);
     }
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-    const uint32_t tmem = *tslot;            // D_re: columns 0..127, D_im: 128..255
+    const uint32_t tmem = *tslot;
     const int nk = (1 << dBc_log2) / GRAM_KB;
-    if (threadIdx.x == 0) {
-        const long long deadline = clock64() + (1LL << 32);
-        const uint32_t id_pos = idesc_bf16_f32(GRAM_T, GRAM_T, false);
-        const uint32_t id_neg = idesc_bf16_f32(GRAM_T, GRAM_T, true);
-        auto load_stage = [&](int kb, int s) {
-            unsigned char *st = base + s * GRAM_STAGE;
-            mbar_expect_tx(full + s, GRAM_STAGE);
-            // slot (m, p): m = 0 X_I, 1 Y_I, 2 X_J, 3 Y_J; plane = 3 (m & 1) + p
+    const long long deadline = clock64() + (1LL << 32);
+    if (warp == GRAM_EPI / 32) {
+        if (lane == 0) {
+            const uint32_t id_pos = idesc_bf16_f32(GRAM_T, GRAM_T, false);
+            const uint32_t id_neg = idesc_bf16_f32(GRAM_T, GRAM_T, true);
+            auto load_stage = [&](int kb, int s) {
+                unsigned char *st = base + s * GRAM_STAGE;
+                mbar_expect_tx(full + s, GRAM_STAGE);
+                // slot (m, p): m = 0 X_I, 1 Y_I, 2 X_J, 3 Y_J; plane = 3 (m & 1) + p
 #pragma unroll
-            for (int m = 0; m < 4; ++m)
+                for (int m = 0; m < 4; ++m)
 #pragma unroll
-                for (int p = 0; p < 3; ++p)
-                    tma_load_3d(st + (m * 3 + p) * GRAM_BOX, &tp, kb * GRAM_KB, m < 2 ? r0I : r0J, 3 * (m & 1) + p,
-                                full + s);
-        };
-        int committed = -1;
-        bool ok = true;
-        load_stage(0, 0);
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb & 1;
-            if (!mbar_wait(full + s, (uint32_t)((kb >> 1) & 1), deadline)) { ok = false; break; }
-            fence_after_sync();
-            const uint32_t sb = smem_u32(base + s * GRAM_STAGE);
-            auto slot = [&](int m, int p, int ks) { return smem_desc<64>(sb + (m * 3 + p) * GRAM_BOX + 32 * ks); };
+                    for (int p = 0; p < 3; ++p)
+                        tma_load_3d(st + (m * 3 + p) * GRAM_BOX, &tp, kb * GRAM_KB, m < 2 ? r0I : r0J,
+                                    3 * (m & 1) + p, full + s);
+            };
+            bool ok = true;
+            load_stage(0, 0);
+            for (int kb = 0; kb < nk && ok; ++kb) {
+                const int s = kb & 1;                 // smem stage and TMEM buffer
+                const uint32_t par = (uint32_t)((kb >> 1) & 1);
+                if (!mbar_wait(full + s, par, deadline)) { ok = false; break; }
+                if (kb >= 2 && !mbar_wait(tfree + s, par ^ 1u, deadline)) { ok = false; break; }
+                fence_after_sync();
+                const uint32_t sb = smem_u32(base + s * GRAM_STAGE);
+                const uint32_t dre = tmem + 256u * (uint32_t)s, dim = dre + 128u;
+                auto slot = [&](int m, int p, int ks) { return smem_desc<64>(sb + (m * 3 + p) * GRAM_BOX + 32 * ks); };
 #pragma unroll
-            for (int ks = 0; ks < GRAM_KB / 16; ++ks) {
-                // part pairs (p, q) with p + q <= 2
-                const int PP[6] = {0, 0, 1, 0, 2, 1}, QQ[6] = {0, 1, 0, 2, 0, 1};
+                for (int ks = 0; ks < GRAM_KB / 16; ++ks) {
+                    // part pairs (p, q) with p + q <= 2, smallest first
+                    const int PP[6] = {1, 2, 0, 1, 0, 0}, QQ[6] = {1, 0, 2, 0, 1, 0};
 #pragma unroll
-                for (int u = 0; u < 6; ++u) {
-                    const int p = PP[u], q = QQ[u];
-                    const uint32_t acc = (kb > 0 || ks > 0 || u > 0) ? 1u : 0u;
-                    mma_bf16(tmem, slot(0, p, ks), slot(2, q, ks), id_pos, acc);          // X_I X_J^T
-                    mma_bf16(tmem, slot(1, p, ks), slot(3, q, ks), id_pos, 1u);           // + Y_I Y_J^T
-                    mma_bf16(tmem + 128, slot(1, p, ks), slot(2, q, ks), id_pos, acc);    // Y_I X_J^T
-                    mma_bf16(tmem + 128, slot(0, p, ks), slot(3, q, ks), id_neg, 1u);     // - X_I Y_J^T
+                    for (int u = 0; u < 6; ++u) {
+                        const int p = PP[u], q = QQ[u];
+                        const uint32_t acc = (ks > 0 || u > 0) ? 1u : 0u;
+                        mma_bf16(dre, slot(0, p, ks), slot(2, q, ks), id_pos, acc);     // X_I X_J^T
+                        mma_bf16(dre, slot(1, p, ks), slot(3, q, ks), id_pos, 1u);      // + Y_I Y_J^T
+                        mma_bf16(dim, slot(1, p, ks), slot(2, q, ks), id_pos, acc);     // Y_I X_J^T
+                        mma_bf16(dim, slot(0, p, ks), slot(3, q, ks), id_neg, 1u);      // - X_I Y_J^T
+                    }
+                }
+                mma_commit(sfree + s);
+                mma_commit(tready + s);
+                if (kb + 1 < nk) {
+                    const int s1 = (kb + 1) & 1;
+                    if (kb >= 1 && !mbar_wait(sfree + s1, (uint32_t)(((kb - 1) >> 1) & 1), deadline)) { ok = false; break; }
+                    load_stage(kb + 1, s1);
                 }
             }
-            mma_commit(done + s);
-            committed = kb;
-            if (kb + 1 < nk) {
-                const int s1 = (kb + 1) & 1;
-                if (kb >= 1 && !mbar_wait(done + s1, (uint32_t)(((kb - 1) >> 1) & 1), deadline)) { ok = false; break; }
-                load_stage(kb + 1, s1);
+            if (!ok) {
+                atomicOr(err, SRE_ERR_TIMEOUT);
+                atomicExch(abort_flag, 1);
             }
         }
-        if (!ok) atomicOr(err, SRE_ERR_TIMEOUT);
-        *last = committed;
-    }
-    __syncthreads();
-    const int lk = *last;
-    bool have = false;
-    if (lk >= 0) have = mbar_wait(done + (lk & 1), (uint32_t)((lk >> 1) & 1), clock64() + (1LL << 32));
-    if (lk >= 0 && !have && lane == 0) atomicOr(err, SRE_ERR_TIMEOUT);
-    fence_after_sync();
-    if (lk == nk - 1 && have) {
-        const unsigned long long i = (unsigned long long)r0I + 32 * warp + lane;
-        const uint32_t lrow = (uint32_t)(32 * warp) << 16;
-#pragma unroll 1
-        for (int c = 0; c < GRAM_T; c += 32) {
-            float re[32], im[32];
-            tmem_ld32(tmem + lrow + (uint32_t)c, re);
-            tmem_ld32(tmem + lrow + 128u + (uint32_t)c, im);
+    } else {
+        // epilogue warps: FP32 running sums of 64 columns of D_re and D_im
+        float sre_[64], sim_[64];
 #pragma unroll
-            for (int k = 0; k < 32; ++k) {
-                const unsigned long long jj = (unsigned long long)r0J + c + k;
-                float2 v = make_float2(re[k], im[k]);
+        for (int k = 0; k < 64; ++k) { sre_[k] = 0.f; sim_[k] = 0.f; }
+        const uint32_t lrow = (uint32_t)(32 * (warp & 3)) << 16;
+        const uint32_t c0 = 64u * (uint32_t)(warp >> 2);
+        bool ok = true;
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb & 1;
+            bool ready = false;
+            while (!(ready = mbar_test(tready + s, (uint32_t)((kb >> 1) & 1)))) {
+                if (clock64() > deadline || *(volatile int *)abort_flag) break;
+            }
+            if (!__all_sync(0xffffffffu, ready)) { ok = false; break; }
+            fence_after_sync();
+            const uint32_t b = tmem + lrow + 256u * (uint32_t)s + c0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float v[32];
+                tmem_ld32(b + 32u * h, v);
+#pragma unroll
+                for (int k = 0; k < 32; ++k) sre_[32 * h + k] += v[k];
+                tmem_ld32(b + 128u + 32u * h, v);
+#pragma unroll
+                for (int k = 0; k < 32; ++k) sim_[32 * h + k] += v[k];
+            }
+            fence_before_sync();
+            mbar_arrive(tfree + s);
+        }
+        if (!ok && lane == 0) atomicOr(err, SRE_ERR_TIMEOUT);
+        if (ok) {
+            const unsigned long long i = (unsigned long long)r0I + 32 * (warp & 3) + lane;
+#pragma unroll
+            for (int k = 0; k < 64; ++k) {
+                const unsigned long long jj = (unsigned long long)r0J + c0 + k;
+                float2 v = make_float2(sre_[k], sim_[k]);
                 float2 *pc = C + i + dA * jj;
                 if (accumulate_c) { const float2 o = *pc; v.x += o.x; v.y += o.y; }
                 *pc = v;
             }
             if (I != J) {
-                // C[j][i] = conj C[i][j]: 32 consecutive j of this thread's row i
-                float2 *row = C + (unsigned long long)r0J + c + dA * i;
+                // C[j][i] = conj C[i][j]: 64 consecutive j of this thread's row i
+                float2 *row = C + (unsigned long long)r0J + c0 + dA * i;
 #pragma unroll
-                for (int k = 0; k < 32; k += 2) {
-                    float4 w = make_float4(re[k], -im[k], re[k + 1], -im[k + 1]);
+                for (int k = 0; k < 64; k += 2) {
+                    float4 w = make_float4(sre_[k], -sim_[k], sre_[k + 1], -sim_[k + 1]);
                     float4 *pr = reinterpret_cast<float4 *>(row + k);
                     if (accumulate_c) {
                         const float4 o = *pr;
@@ -204,7 +247,7 @@ __global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__
     }
     fence_before_sync();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, 256);
+    if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
 // ------------------------------------------------------------ small shapes
@@ -278,7 +321,7 @@ cudaError_t launch_gram(const float2 *psi, int N, int NA, float2 *C, void *plane
     for (long long e0 = 0; e0 < (1LL << NB); e0 += (long long)dBc) {
         gram_split_kernel<<<dim3((unsigned)(dA / 32), (unsigned)(dBc / 32)), 256, 0, st>>>(
             psi, NA, e0, cl, reinterpret_cast<__nv_bfloat16 *>(planes));
-        gram_tc_kernel<<<ntiles, 128, GRAM_SMEM, st>>>(tp, C, NA, cl, e0 > 0 ? 1 : 0, err);
+        gram_tc_kernel<<<ntiles, GRAM_THREADS, GRAM_SMEM, st>>>(tp, C, NA, cl, e0 > 0 ? 1 : 0, err);
         *launches += 2;
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
