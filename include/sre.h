@@ -296,9 +296,9 @@ SRE_API sre_status sre_philox_blocks(const unsigned long long *ctr_key_dev, unsi
  * paper; it checks the conventions the tensor-core kernels rely on):
  * D = A B^T in FP32 from BF16 operands, A: M x K and B: N x K row-major
  * (K contiguous) device arrays of BF16 bit patterns, 16-byte aligned;
- * D: M x N row-major FP32. M and N multiples of 128, K of 64. swizzle: 128
- * or 64, the bytes per operand row of the shared-memory tiles (K blocks of
- * 64 or 32). err_dev: a caller-owned device int the call clears and the
+ * D: M x N row-major FP32. M and N multiples of 128, K of 64. swizzle: 128,
+ * 64 or 32, the bytes per operand row of the shared-memory tiles (K blocks of
+ * 64, 32 or 16). err_dev: a caller-owned device int the call clears and the
  * kernel sets when a bounded wait runs out (then SRE_ETIMEOUT). Synchronises
  * the stream. */
 SRE_API sre_status sre_tc_gemm_selftest(const void *A_bf16_dev, const void *B_bf16_dev, float *D_dev, int M,

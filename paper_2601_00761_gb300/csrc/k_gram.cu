@@ -14,9 +14,9 @@
 // 1. gram_split_kernel transposes Psi into six K-major BF16 planes
 //    P[c * 3 + p][a][e] (c = 0: X, 1: Y; p the part).
 // 2. gram_tc_kernel: one 128 x 128 tile (I, J) of C per CTA, I <= J only;
-//    K in blocks of 32 (64-byte rows, TMA with the 64-byte swizzle), a
-//    two-stage ring of 12 boxes per block (X_I, Y_I, X_J, Y_J, three parts
-//    each, 96 KB per stage); one thread issues the TMA loads and the 48 MMAs
+//    K in blocks of 16 (32-byte rows, TMA with the 32-byte swizzle), a
+//    four-stage ring of 12 contiguous 4 KB boxes per block (X_I, Y_I, X_J,
+//    Y_J, three parts each); one thread issues the TMA loads and the 24 MMAs
 //    per block into a fresh TMEM accumulator (D_re, D_im), alternating
 //    between two; eight warps add each block's accumulator into FP32
 //    register sums and write the tile and, off the diagonal, its conjugate
@@ -33,7 +33,10 @@
 namespace sre {
 
 // ------------------------------------------------------------ split
-// planes: 6 x dA x dBc BF16 (K-major); this chunk covers columns e0 .. e0 + dBc
+// Planes: 6 x (d_A x dBc) BF16, tiled so that every 128-row x 16-column block
+// the Gram kernel loads is 4 KB of contiguous memory: element (a, e) of a
+// plane at ((a / 128) * (dBc / 16) + e / 16) * 2048 + (a % 128) * 16 + e % 16.
+// This chunk covers columns e0 .. e0 + dBc of Psi.
 __global__ void __launch_bounds__(256) gram_split_kernel(const float2 *psi, int NA, long long e0, int dBc_log2,
                                                          __nv_bfloat16 *planes) {
     __shared__ float2 t[32][33];
@@ -48,11 +51,13 @@ __global__ void __launch_bounds__(256) gram_split_kernel(const float2 *psi, int 
     }
     __syncthreads();
     const size_t plane = (size_t)dA * dBc;
+    const unsigned long long neb = dBc / 16;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int row = ty + 8 * k;                    // a = a0 + row, e = c0 + tx
         const float2 v = t[tx][row];
-        const size_t o = (size_t)(a0 + row) * dBc + c0 + tx;
+        const unsigned long long a = a0 + row, e = c0 + tx;
+        const size_t o = ((a >> 7) * neb + (e >> 4)) * 2048 + (a & 127) * 16 + (e & 15);
         const float xs[2] = {v.x, v.y};
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
@@ -71,12 +76,13 @@ __global__ void __launch_bounds__(256) gram_split_kernel(const float2 *psi, int 
 
 // ------------------------------------------------------------ tensor cores
 constexpr int GRAM_T = 128;                    // tile rows / columns
-constexpr int GRAM_KB = 32;                    // K per block (64-byte rows)
-constexpr uint32_t GRAM_BOX = GRAM_T * 64;     // bytes of one 128 x 32 BF16 box
+constexpr int GRAM_KB = 16;                    // K per block (32-byte rows, one MMA step)
+constexpr uint32_t GRAM_BOX = GRAM_T * 32;     // bytes of one 128 x 16 BF16 box (contiguous)
 constexpr uint32_t GRAM_STAGE = 12 * GRAM_BOX; // X_I, Y_I, X_J, Y_J x 3 parts
+constexpr int GRAM_NS = 4;                     // stages in the ring
 constexpr int GRAM_EPI = 256;                  // epilogue threads (8 warps)
 constexpr int GRAM_THREADS = GRAM_EPI + 32;    // + one warp issuing TMA and MMA
-constexpr size_t GRAM_SMEM = 1024 + 2 * (size_t)GRAM_STAGE + 256;
+constexpr size_t GRAM_SMEM = 1024 + GRAM_NS * (size_t)GRAM_STAGE + 256;
 
 // tile index -> (I, J) with I <= J over nt x nt tiles (row-major upper triangle)
 __device__ __forceinline__ void tri_tile(int idx, int nt, int &I, int &J) {
@@ -102,10 +108,10 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) gram_tc_kernel(const __grid_c
     using namespace tc05;
     extern __shared__ unsigned char smraw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-    uint64_t *full = reinterpret_cast<uint64_t *>(base + 2 * GRAM_STAGE);   // [2] stage loaded
-    uint64_t *sfree = full + 2;                                           // [2] stage read by the MMAs
-    uint64_t *tready = sfree + 2;                                         // [2] TMEM buffer holds a block
-    uint64_t *tfree = tready + 2;                                         // [2] TMEM buffer drained
+    uint64_t *full = reinterpret_cast<uint64_t *>(base + GRAM_NS * GRAM_STAGE);   // [NS] stage loaded
+    uint64_t *sfree = full + GRAM_NS;                                           // [NS] stage read by the MMAs
+    uint64_t *tready = sfree + GRAM_NS;                                         // [2] TMEM buffer holds a block
+    uint64_t *tfree = tready + 2;                                               // [2] TMEM buffer drained
     uint32_t *tslot = reinterpret_cast<uint32_t *>(tfree + 2);
     int *abort_flag = reinterpret_cast<int *>(tslot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -119,9 +125,11 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) gram_tc_kernel(const __grid_c
         tmem_relinquish();
     }
     if (threadIdx.x == GRAM_EPI) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < GRAM_NS; ++i) {
             mbar_init(full + i, 1);
             mbar_init(sfree + i, 1);
+        }
+        for (int i = 0; i < 2; ++i) {
             mbar_init(tready + i, 1);
             mbar_init(tfree + i, GRAM_EPI);
         }
@@ -139,6 +147,7 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) gram_tc_kernel(const __grid_c
         if (lane == 0) {
             const uint32_t id_pos = idesc_bf16_f32(GRAM_T, GRAM_T, false);
             const uint32_t id_neg = idesc_bf16_f32(GRAM_T, GRAM_T, true);
+            // block (row block rb, K block kb) of a plane starts at row (rb * nk + kb) * 128 of the map
             auto load_stage = [&](int kb, int s) {
                 unsigned char *st = base + s * GRAM_STAGE;
                 mbar_expect_tx(full + s, GRAM_STAGE);
@@ -147,40 +156,37 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) gram_tc_kernel(const __grid_c
                 for (int m = 0; m < 4; ++m)
 #pragma unroll
                     for (int p = 0; p < 3; ++p)
-                        tma_load_3d(st + (m * 3 + p) * GRAM_BOX, &tp, kb * GRAM_KB, m < 2 ? r0I : r0J,
+                        tma_load_3d(st + (m * 3 + p) * GRAM_BOX, &tp, 0, ((m < 2 ? I : J) * nk + kb) * GRAM_T,
                                     3 * (m & 1) + p, full + s);
             };
             bool ok = true;
-            load_stage(0, 0);
+            for (int kb = 0; kb < nk && kb < GRAM_NS; ++kb) load_stage(kb, kb);
             for (int kb = 0; kb < nk && ok; ++kb) {
-                const int s = kb & 1;                 // smem stage and TMEM buffer
-                const uint32_t par = (uint32_t)((kb >> 1) & 1);
-                if (!mbar_wait(full + s, par, deadline)) { ok = false; break; }
-                if (kb >= 2 && !mbar_wait(tfree + s, par ^ 1u, deadline)) { ok = false; break; }
+                const int s = kb % GRAM_NS, b = kb & 1;
+                if (!mbar_wait(full + s, (uint32_t)((kb / GRAM_NS) & 1), deadline)) { ok = false; break; }
+                if (kb >= 2 && !mbar_wait(tfree + b, (uint32_t)(((kb - 2) >> 1) & 1), deadline)) { ok = false; break; }
                 fence_after_sync();
                 const uint32_t sb = smem_u32(base + s * GRAM_STAGE);
-                const uint32_t dre = tmem + 256u * (uint32_t)s, dim = dre + 128u;
-                auto slot = [&](int m, int p, int ks) { return smem_desc<64>(sb + (m * 3 + p) * GRAM_BOX + 32 * ks); };
+                const uint32_t dre = tmem + 256u * (uint32_t)b, dim = dre + 128u;
+                auto slot = [&](int m, int p) { return smem_desc<32>(sb + (m * 3 + p) * GRAM_BOX); };
+                // part pairs (p, q) with p + q <= 2, smallest first
+                const int PP[6] = {1, 2, 0, 1, 0, 0}, QQ[6] = {1, 0, 2, 0, 1, 0};
 #pragma unroll
-                for (int ks = 0; ks < GRAM_KB / 16; ++ks) {
-                    // part pairs (p, q) with p + q <= 2, smallest first
-                    const int PP[6] = {1, 2, 0, 1, 0, 0}, QQ[6] = {1, 0, 2, 0, 1, 0};
-#pragma unroll
-                    for (int u = 0; u < 6; ++u) {
-                        const int p = PP[u], q = QQ[u];
-                        const uint32_t acc = (ks > 0 || u > 0) ? 1u : 0u;
-                        mma_bf16(dre, slot(0, p, ks), slot(2, q, ks), id_pos, acc);     // X_I X_J^T
-                        mma_bf16(dre, slot(1, p, ks), slot(3, q, ks), id_pos, 1u);      // + Y_I Y_J^T
-                        mma_bf16(dim, slot(1, p, ks), slot(2, q, ks), id_pos, acc);     // Y_I X_J^T
-                        mma_bf16(dim, slot(0, p, ks), slot(3, q, ks), id_neg, 1u);      // - X_I Y_J^T
-                    }
+                for (int u = 0; u < 6; ++u) {
+                    const int p = PP[u], q = QQ[u];
+                    const uint32_t acc = u > 0 ? 1u : 0u;
+                    mma_bf16(dre, slot(0, p), slot(2, q), id_pos, acc);     // X_I X_J^T
+                    mma_bf16(dre, slot(1, p), slot(3, q), id_pos, 1u);      // + Y_I Y_J^T
+                    mma_bf16(dim, slot(1, p), slot(2, q), id_pos, acc);     // Y_I X_J^T
+                    mma_bf16(dim, slot(0, p), slot(3, q), id_neg, 1u);      // - X_I Y_J^T
                 }
                 mma_commit(sfree + s);
-                mma_commit(tready + s);
-                if (kb + 1 < nk) {
-                    const int s1 = (kb + 1) & 1;
-                    if (kb >= 1 && !mbar_wait(sfree + s1, (uint32_t)(((kb - 1) >> 1) & 1), deadline)) { ok = false; break; }
-                    load_stage(kb + 1, s1);
+                mma_commit(tready + b);
+                // refill the stage of the previous block (its MMAs ran while this block's were queued)
+                if (kb >= 1 && kb - 1 + GRAM_NS < nk) {
+                    const int sp = (kb - 1) % GRAM_NS;
+                    if (!mbar_wait(sfree + sp, (uint32_t)(((kb - 1) / GRAM_NS) & 1), deadline)) { ok = false; break; }
+                    load_stage(kb - 1 + GRAM_NS, sp);
                 }
             }
             if (!ok) {
@@ -316,7 +322,8 @@ cudaError_t launch_gram(const float2 *psi, int N, int NA, float2 *C, void *plane
         attr = true;
     }
     CUtensorMap tp;
-    cudaError_t e = tc05_make_map_bf16(&tp, planes, dA, dBc, dBc, GRAM_T, 64, 6);
+    // each plane as (d_A dBc / 16) rows of 16 columns (the tiled layout of gram_split_kernel)
+    cudaError_t e = tc05_make_map_bf16(&tp, planes, dA * (dBc / GRAM_KB), GRAM_KB, GRAM_KB, GRAM_T, 32, 6);
     if (e != cudaSuccess) return e;
     for (long long e0 = 0; e0 < (1LL << NB); e0 += (long long)dBc) {
         gram_split_kernel<<<dim3((unsigned)(dA / 32), (unsigned)(dBc / 32)), 256, 0, st>>>(

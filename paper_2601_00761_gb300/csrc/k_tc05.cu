@@ -2,7 +2,7 @@
 //
 // The self-test multiplies BF16 matrices with FP32 accumulation in TMEM:
 // D[M x N] = A[M x K] B[N x K]^T (both operands K-major), one 128 x BN tile
-// per CTA, K in blocks of 64 (128-byte swizzle) or 32 (64-byte swizzle)
+// per CTA, K in blocks of 64, 32 or 16 (128-, 64- or 32-byte swizzle)
 // brought in by TMA through a two-stage ring, K = 16 MMAs issued by one
 // thread, then the
 // accumulator read back by the four warps (warp w: rows 32 w .. 32 w + 31).
@@ -33,7 +33,7 @@ cudaError_t tc05_make_map_bf16(CUtensorMap *map, const void *base, unsigned long
     });
     if (g_encode_err != cudaSuccess) return g_encode_err;
     const unsigned box_cols = (unsigned)sw / 2;
-    if ((sw != 128 && sw != 64) || ((uintptr_t)base & 15) || (pitch_elems * 2) % 16 || cols % box_cols ||
+    if ((sw != 128 && sw != 64 && sw != 32) || ((uintptr_t)base & 15) || (pitch_elems * 2) % 16 || cols % box_cols ||
         box_rows == 0 || box_rows > 256 || planes == 0)
         return cudaErrorInvalidValue;
     const cuuint64_t dims[3] = {cols, rows, planes};
@@ -42,7 +42,8 @@ cudaError_t tc05_make_map_bf16(CUtensorMap *map, const void *base, unsigned long
     const cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, planes > 1 ? 3 : 2, const_cast<void *>(base), dims,
                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          sw == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                          sw == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                    : (sw == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B),
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -154,12 +155,13 @@ cudaError_t launch_tc05_gemm_sw(const void *A, const void *B, float *D, int M, i
     return cudaGetLastError();
 }
 
-// swizzle: 128 or 64 (bytes per operand row in shared memory)
+// swizzle: 128, 64 or 32 (bytes per operand row in shared memory)
 cudaError_t launch_tc05_gemm_selftest(const void *A, const void *B, float *D, int M, int N, int K, int swizzle,
                                       int *err, cudaStream_t st) {
     if (M % 128 || N % 128 || K % 64 || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
     if (swizzle == 128) return launch_tc05_gemm_sw<128>(A, B, D, M, N, K, err, st);
     if (swizzle == 64) return launch_tc05_gemm_sw<64>(A, B, D, M, N, K, err, st);
+    if (swizzle == 32) return launch_tc05_gemm_sw<32>(A, B, D, M, N, K, err, st);
     return cudaErrorInvalidValue;
 }
 

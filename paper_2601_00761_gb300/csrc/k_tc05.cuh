@@ -100,18 +100,18 @@ __device__ __forceinline__ void fence_after_sync() {
 
 // ----------------------------------------------------------- descriptors
 // Shared-memory matrix descriptor of a K-major tile whose rows are SW bytes
-// (SW = 128 or 64) swizzled as TMA's SW-byte mode writes them: start address,
+// (SW = 128, 64 or 32) swizzled as TMA's SW-byte mode writes them: start address,
 // leading-dimension byte offset (unused for swizzled K-major tiles), stride
 // between 8-row groups (8 SW bytes), both in 16-byte units, the fixed version
 // bits 46..48 = 0b001, base offset 0, and the layout type in bits 61..63
-// (2 = 128-byte swizzle, 4 = 64-byte swizzle).
+// (2 = 128-byte swizzle, 4 = 64-byte, 6 = 32-byte).
 template <int SW>
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-    static_assert(SW == 128 || SW == 64, "128- or 64-byte swizzle");
+    static_assert(SW == 128 || SW == 64 || SW == 32, "128-, 64- or 32-byte swizzle");
     const uint64_t start = (uint64_t)((saddr & 0x3FFFFu) >> 4);
     const uint64_t lbo = 1;
     const uint64_t sbo = (8 * SW) >> 4;
-    const uint64_t layout = SW == 128 ? 2 : 4;
+    const uint64_t layout = SW == 128 ? 2 : (SW == 64 ? 4 : 6);
     return start | (lbo << 16) | (sbo << 32) | (1ull << 46) | (layout << 61);
 }
 __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) { return smem_desc<128>(saddr); }
@@ -165,7 +165,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 // Host: a tensor map over row-major BF16 matrices (planes x rows x cols, cols
 // contiguous, row pitch `pitch_elems`, plane pitch rows * pitch_elems) with
 // boxes of sw/2 columns x box_rows rows x 1 plane and the sw-byte swizzle
-// (sw = 128 or 64). planes = 1 gives a 2-D map. Returns cudaSuccess or an
+// (sw = 128, 64 or 32). planes = 1 gives a 2-D map. Returns cudaSuccess or an
 // error.
 cudaError_t tc05_make_map_bf16(CUtensorMap *map, const void *base, unsigned long long rows, unsigned long long cols,
                                unsigned long long pitch_elems, unsigned box_rows, int sw = 128,

@@ -1788,7 +1788,8 @@ sre_status sre_tc_gemm_selftest(const void *A_bf16_dev, const void *B_bf16_dev, 
     if (M <= 0 || N <= 0 || K <= 0 || M % 128 || N % 128 || K % 64)
         return fail(SRE_EINVAL, "tc gemm self-test: M, N must be multiples of 128 and K of 64 (got %d, %d, %d)", M, N, K);
     if (((uintptr_t)A_bf16_dev | (uintptr_t)B_bf16_dev) & 15) return fail(SRE_EINVAL, "tc gemm self-test: operands must be 16-byte aligned");
-    if (swizzle != 128 && swizzle != 64) return fail(SRE_EINVAL, "tc gemm self-test: swizzle must be 128 or 64");
+    if (swizzle != 128 && swizzle != 64 && swizzle != 32)
+        return fail(SRE_EINVAL, "tc gemm self-test: swizzle must be 128, 64 or 32");
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaMemsetAsync(err_dev, 0, sizeof(int), st));
     CK(launch_tc05_gemm_selftest(A_bf16_dev, B_bf16_dev, D_dev, M, N, K, swizzle, err_dev, st));

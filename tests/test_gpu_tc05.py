@@ -22,7 +22,7 @@ def _ref(A, B):
     return A.double().cpu().numpy() @ B.double().cpu().numpy().T
 
 
-@pytest.mark.parametrize("swizzle", [128, 64])
+@pytest.mark.parametrize("swizzle", [128, 64, 32])
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 384, 256), (128, 256, 1024), (384, 128, 192)])
 def test_gemm_random(sre, M, N, K, swizzle):
     g = torch.Generator().manual_seed(M * 7 + N * 3 + K)
@@ -34,7 +34,7 @@ def test_gemm_random(sre, M, N, K, swizzle):
     assert np.max(np.abs(D - ref)) <= bound
 
 
-@pytest.mark.parametrize("swizzle", [128, 64])
+@pytest.mark.parametrize("swizzle", [128, 64, 32])
 def test_gemm_layout_is_exact_on_permutations(sre, swizzle):
     """A = a row permutation of the identity: D must be B's rows permuted,
     exactly (every product is one nonzero term)."""
