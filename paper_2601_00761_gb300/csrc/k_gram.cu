@@ -278,15 +278,29 @@ __global__ void __launch_bounds__(256) gram_simt_kernel(const float2 *psi, int N
 // accumulation leaves them about 1e-6 off, summed in FP64 they carry only
 // the final FP32 rounding.
 __global__ void __launch_bounds__(256) gram_diag_kernel(const float2 *psi, int NA, int NB, float2 *C) {
+    // one block per 32 consecutive a (coalesced 256-byte rows of Psi); warp
+    // w sums e = w, w + 8, ...; the eight partial sums are added in a fixed
+    // order, so the result does not depend on scheduling
+    __shared__ double part[8][32];
     const unsigned long long dA = 1ULL << NA, dB = 1ULL << NB;
-    const unsigned long long a = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= dA) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned long long a = (unsigned long long)blockIdx.x * 32 + lane;
     double acc = 0.0;
-    for (unsigned long long e = 0; e < dB; ++e) {
-        const float2 v = psi[a + dA * e];
-        acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+    if (a < dA) {
+#pragma unroll 4
+        for (unsigned long long e = (unsigned long long)w; e < dB; e += 8) {
+            const float2 v = psi[a + dA * e];
+            acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+        }
     }
-    C[a + dA * a] = make_float2((float)acc, 0.0f);
+    part[w][lane] = acc;
+    __syncthreads();
+    if (w == 0 && a < dA) {
+        double t = 0.0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t += part[i][lane];
+        C[a + dA * a] = make_float2((float)t, 0.0f);
+    }
 }
 
 // K chunk (columns of Psi per split) bounded so the planes stay within 2^27 elements each
@@ -333,7 +347,7 @@ cudaError_t launch_gram(const float2 *psi, int N, int NA, float2 *C, void *plane
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    gram_diag_kernel<<<(unsigned)((dA + 255) / 256), 256, 0, st>>>(psi, NA, NB, C);
+    gram_diag_kernel<<<(unsigned)((dA + 31) / 32), 256, 0, st>>>(psi, NA, NB, C);
     *launches += 1;
     return cudaGetLastError();
 }
