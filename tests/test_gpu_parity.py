@@ -532,7 +532,13 @@ def test_gates_vs_oracle(sre, N, n):
     p = dev(psi)
     sre.apply_clifford_tdoped_circuit(p, gates)
     got = p.cpu().numpy()
-    assert np.max(np.abs(got - want)) < 2e-6 * math.sqrt(n) + 1e-6
+    # per amplitude: the 1e-6 target; in l2 norm: the FP32 rounding bound of
+    # the gate kernels, 3 u per H or T gate (one add, one multiply and the
+    # rounded 1/sqrt2 per output), S and CNOT exact
+    d = got - want
+    n_ht = int(sum(1 for r in rows if r[0] in (inputs.GATE_H, inputs.GATE_T, inputs.GATE_TDG)))
+    assert np.max(np.abs(d)) < 1e-6
+    assert np.linalg.norm(d) <= 3 * 2.0**-24 * n_ht * np.linalg.norm(want) + 1e-12
 
 
 def test_gates_then_exact_matches_oracle_pipeline(sre):
