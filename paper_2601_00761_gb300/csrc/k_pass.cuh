@@ -294,15 +294,19 @@ __device__ __forceinline__ void moment_sums(const float2 (&h)[E], float2 sc, uin
     }
 }
 
-// Weights of the 2^ZR_FINE-z ranges of a last-pass tile (at least 64
-// threads; slot bits are z' bits 0..4 and thread t holds z' = zb + k, so a
-// warp spans 2^10 consecutive z'). With j >= ZR_FINE (or x = 0, pair
-// (z', z' + d/2)) a warp's c(z0) fill one range and its c(z1) another, s2
-// being ordered (c(z0)^2, c(z1)^2); with j < ZR_FINE a half-warp's 2^9 z'
-// yield both c of 2^10 consecutive z. Each range of the family is written by
-// exactly one warp or half-warp.
+// Weights of the 2^ZR_FINE-z ranges of a last-pass tile (slot bits are z'
+// bits 0 .. RB-1 and thread t holds z' = zb + k, so L consecutive lanes span
+// L E consecutive z'). With j >= ZR_FINE (or x = 0, pair (z', z' + d/2)) the
+// c(z0) of 2^ZR_FINE consecutive z' fill one range and their c(z1) another,
+// s2 being ordered (c(z0)^2, c(z1)^2); with j < ZR_FINE, 2^(ZR_FINE-1) z'
+// yield both c of 2^ZR_FINE consecutive z. A range spans 2^ZR_FINE / E (split)
+// or 2^(ZR_FINE-1) / E lanes: within a warp its sum is written by one lane;
+// across two warps (E = 16, split) both add into the zeroed row, and the sum
+// of two FP32 terms does not depend on their order.
+template <int E>
 __device__ __forceinline__ void fine_range_weights(float2 s2, unsigned long long x, int j, unsigned long long half,
                                                    uint32_t zb, float *row, bool active) {
+    static_assert(E == 32 || E == 16, "16 or 32 points per thread");
     const int lane = threadIdx.x & 31;
     const bool split = (x == 0) || (j >= ZR_FINE);
     unsigned long long z0, z1;
@@ -314,22 +318,37 @@ __device__ __forceinline__ void fine_range_weights(float2 s2, unsigned long long
         z1 = (unsigned long long)zb | half;
     }
     float wa = split ? s2.x : s2.x + s2.y, wb = s2.y;
+    constexpr int LS = (1 << ZR_FINE) / E;          // lanes of a range when split (32 or 64)
+    constexpr int LN = (1 << (ZR_FINE - 1)) / E;    // lanes of a range otherwise (16 or 32)
 #pragma unroll
-    for (int o = 1; o < 16; o <<= 1) {
+    for (int o = 1; o < LN; o <<= 1) {
         wa += __shfl_xor_sync(0xffffffffu, wa, o);
         wb += __shfl_xor_sync(0xffffffffu, wb, o);
     }
     if (split) {
-        wa += __shfl_xor_sync(0xffffffffu, wa, 16);
-        wb += __shfl_xor_sync(0xffffffffu, wb, 16);
-        if (active && lane == 0) {
-            row[z0 >> ZR_FINE] = wa;
-            row[z1 >> ZR_FINE] = wb;
+        if constexpr (LS > LN) {
+            if constexpr (LN < 32) {
+                wa += __shfl_xor_sync(0xffffffffu, wa, LN);
+                wb += __shfl_xor_sync(0xffffffffu, wb, LN);
+            }
         }
-    } else if (active && (lane & 15) == 0) {
+        if (active && lane == 0) {
+            if constexpr (LS > 32) {
+                atomicAdd(row + (z0 >> ZR_FINE), wa);
+                atomicAdd(row + (z1 >> ZR_FINE), wb);
+            } else {
+                row[z0 >> ZR_FINE] = wa;
+                row[z1 >> ZR_FINE] = wb;
+            }
+        }
+    } else if (active && (lane & (LN - 1)) == 0) {
         row[z0 >> ZR_FINE] = wa;
     }
 }
+
+// true when the range rows of a last pass with E points per thread must be
+// zeroed before it (two warps add into each range)
+__host__ __device__ constexpr bool ranges_accumulate(int E) { return (1 << ZR_FINE) / E > 32; }
 
 // Families a CTA of a psi-reading strided pass transforms in turn, on the
 // same tile. Neighbouring families in the sorted order share their own-half
@@ -562,7 +581,7 @@ __device__ __forceinline__ bool fwht_pass_body(const PassArgs &a, int rep) {
             w = s2;                    // z' -> range A, z' + d/2 -> range B
         }
         if constexpr (FINE) {
-            if (wr) fine_range_weights(s2, x, j, half, zb, a.rw_out + (size_t)slot * (size_t)a.rw_stride, active);
+            if (wr) fine_range_weights<Cfg::E>(s2, x, j, half, zb, a.rw_out + (size_t)slot * (size_t)a.rw_stride, active);
         }
         float acc[6] = {s2.x + s2.y, s4.x + s4.y, s6.x + s6.y, sl.x + sl.y, w.x, w.y};
         double out[6];

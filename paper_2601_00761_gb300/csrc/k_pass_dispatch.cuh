@@ -107,6 +107,15 @@ cudaError_t launch_f64_row(int M, int src, int dst, const PassArgs &a, int tiles
 // at least 8 columns = 64 contiguous bytes per row, two CTAs per SM so one
 // CTA's loads overlap the other's butterflies); FP64 MS = 13 (128 KB)
 constexpr int F32_STRIDED_KMAX = 10, F32_ROW_MMIN = 10, F32_ROW_MMAX = 14, F32_SINGLE_MMAX = 14;
+// register bits of the 13-bit FP32 row pass: 4 (512 threads x 16 points, two
+// CTAs per SM: 32 warps) or 5 (256 x 32)
+#ifndef SRE_ROW13_RB
+#define SRE_ROW13_RB 4
+#endif
+constexpr int F32_ROW13_RB = SRE_ROW13_RB;
+// whether the FP32 row pass of M bits accumulates its z-range weights (the
+// caller zeroes the rows first)
+constexpr bool f32_row_ranges_accumulate(int M) { return ranges_accumulate(1 << (M == 13 ? F32_ROW13_RB : 5)); }
 __host__ __device__ constexpr int f32_strided_ms(int K) { return K + 3 > 13 ? K + 3 : 13; }
 constexpr int F64_STRIDED_M = 13, F64_STRIDED_KMAX = 9, F64_ROW_M = 12, F64_SINGLE_MMAX = 12;
 

@@ -12,7 +12,7 @@ cudaError_t launch_f32_strided(int MS, int K, int src, int dst, const PassArgs &
 }
 cudaError_t launch_f32_row(int M, int src, int dst, const PassArgs &a, int tiles, cudaStream_t st) {
     switch (M) {
-#define C(m) case m: return launch_sd<KIND_ROW, TileCfg<float, m, 0, 5, 1>>(src, dst, a, tiles, st);
+#define C(m) case m: return launch_sd<KIND_ROW, TileCfg<float, m, 0, (m == 13 ? F32_ROW13_RB : 5), 1>>(src, dst, a, tiles, st);
     C(10) C(11) C(12) C(13) C(14)
 #undef C
     default: return cudaErrorInvalidValue;

@@ -1435,6 +1435,9 @@ sre_status sre_mc(const void *psi, int N, int mode, long long n_x, int z_per_x, 
         PassArgs b = a;
         b.fam_base = fb;
         b.n_fam = nf;
+        // a last pass that adds two warps' sums into each range needs zeroed rows
+        if (marg && fine && f32_row_ranges_accumulate(P.M_last))
+            CK(cudaMemsetAsync(w.Wf, 0, sizeof(float) * (size_t)nf * (size_t)nr, st));
         CS(run_transform(P, b, SRC_PSI_FAMILY, DST_MOMENTS, w.inter, st, (timing && nf == step) ? &T : nullptr));
         CK(launch_fam_reduce(w.tiles, nf, (int)P.tiles_last, xs_run, fb, N, P.M_last, P.RL, w.fm, fb,
                              (marg && !fine) ? w.Wf : nullptr, nr, st, perm));

@@ -113,7 +113,8 @@ struct TileCfg {
     static constexpr int SIZE = 1 << M;
     // CTAs per SM the register budget is sized for: tiles of at most 64 KB
     // (FP32 M <= 13) run several per SM so load and compute phases overlap
-    static constexpr int MINB = (G == 1 && sizeof(C2) * SIZE <= 65536 && NT == 256) ? SRE_MINB_SMALL : 1;
+    // (256 threads with 32 points each, or 512 threads with 16)
+    static constexpr int MINB = (G == 1 && sizeof(C2) * SIZE <= 65536 && (NT == 256 || NT == 512)) ? SRE_MINB_SMALL : 1;
     static_assert(TB >= 0, "tile smaller than a thread's registers");
     static_assert(K >= 0, "bad tile");
 
