@@ -113,6 +113,12 @@ constexpr int F32_STRIDED_KMAX = 10, F32_ROW_MMIN = 10, F32_ROW_MMAX = 14, F32_S
 #define SRE_ROW13_RB 4
 #endif
 constexpr int F32_ROW13_RB = SRE_ROW13_RB;
+// register bits of the 10-row strided FP32 pass (2^10 rows x 8 columns):
+// 5 (256 threads x 32 points) or 4 (512 threads x 16 points)
+#ifndef SRE_STRIDED10_RB
+#define SRE_STRIDED10_RB 5
+#endif
+constexpr int F32_STRIDED10_RB = SRE_STRIDED10_RB;
 // whether the FP32 row pass of M bits accumulates its z-range weights (the
 // caller zeroes the rows first)
 constexpr bool f32_row_ranges_accumulate(int M) { return ranges_accumulate(1 << (M == 13 ? F32_ROW13_RB : 5)); }

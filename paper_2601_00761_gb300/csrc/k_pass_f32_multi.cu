@@ -4,7 +4,7 @@ namespace sre {
 cudaError_t launch_f32_strided(int MS, int K, int src, int dst, const PassArgs &a, int tiles, cudaStream_t st) {
     if (MS != f32_strided_ms(K)) return cudaErrorInvalidValue;
     switch (K) {
-#define C(k) case k: return launch_sd<KIND_STRIDED, TileCfg<float, f32_strided_ms(k), f32_strided_ms(k) - k, 5, 1>>(src, dst, a, tiles, st);
+#define C(k) case k: return launch_sd<KIND_STRIDED, TileCfg<float, f32_strided_ms(k), f32_strided_ms(k) - k, (k == 10 ? F32_STRIDED10_RB : 5), 1>>(src, dst, a, tiles, st);
     C(1) C(2) C(3) C(4) C(5) C(6) C(7) C(8) C(9) C(10)
 #undef C
     default: return cudaErrorInvalidValue;
