@@ -110,7 +110,7 @@ constexpr int F32_STRIDED_KMAX = 10, F32_ROW_MMIN = 10, F32_ROW_MMAX = 14, F32_S
 // register bits of the 13-bit FP32 row pass: 4 (512 threads x 16 points, two
 // CTAs per SM: 32 warps) or 5 (256 x 32)
 #ifndef SRE_ROW13_RB
-#define SRE_ROW13_RB 4
+#define SRE_ROW13_RB 5
 #endif
 constexpr int F32_ROW13_RB = SRE_ROW13_RB;
 // register bits of the 10-row strided FP32 pass (2^10 rows x 8 columns):
