@@ -325,6 +325,17 @@ SRE_API unsigned long long sre_device_allocations(void);
  * SRE_ECUDA. Synchronises the stream. */
 SRE_API sre_status sre_selftest_bounded_wait(void *stream);
 
+/* Self-test of the bounded dependency waits of the persistent batched sweep
+ * (no counterpart in the paper). sre_exact_batched runs every family of every
+ * state as one queue of work items in one launch; an item that needs earlier
+ * items (the row pass of a family batch after its strided pass, a ring slot
+ * after its previous batch) waits on a device counter for at most about a
+ * second of the global timer, then raises SRE_ERR_TIMEOUT and an abort flag
+ * that ends the launch. This test launches one row item whose strided items
+ * never run, so its wait can only end by the bound: it returns SRE_ETIMEOUT
+ * (about a second) and leaves the context usable. Synchronises the stream. */
+SRE_API sre_status sre_selftest_queue_wait(void *stream);
+
 /* Pass timing inside sre_mc: enable = 1 clears the counters and starts
  * recording CUDA events around every full-batch family-transform pass launch
  * of subsequent sre_mc calls; enable = 0 stops. Either call first copies the

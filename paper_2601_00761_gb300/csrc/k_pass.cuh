@@ -363,8 +363,32 @@ template <class Cfg, int SRC> struct FamPerCta {
 
 // One tile of one family (the rep-th family of the CTA); false when the CTA
 // has no rep-th family.
+// The tile of the CTA's rep-th family (one family per group when G > 1) in
+// the launch's grid: (slot of group 0, tile), or false when the CTA has no
+// rep-th family.
+template <class Cfg, int SRC>
+__device__ __forceinline__ bool pass_grid_item(const PassArgs &a, int rep, long long &slot0,
+                                               unsigned long long &tile) {
+    if constexpr (Cfg::G > 1) {
+        slot0 = (long long)blockIdx.x * Cfg::G;
+        tile = 0;
+    } else if (a.fam_fast) {
+        constexpr int FPC = FamPerCta<Cfg, SRC>::v;
+        const unsigned long long L = blockIdx.x;
+        const unsigned long long np = ((unsigned long long)a.n_fam + FPC - 1) / FPC;
+        slot0 = (long long)(L % np) * FPC + rep;
+        tile = L / np;
+        if (rep > 0 && slot0 >= a.n_fam) return false;
+    } else {
+        slot0 = (long long)blockIdx.y + 65535LL * (long long)blockIdx.z;
+        tile = blockIdx.x;
+    }
+    return true;
+}
+
+// One tile of the families slot0 + grp (grp < G) of a launch.
 template <class Cfg, int SRC, int DST, int PREC>
-__device__ __forceinline__ bool fwht_pass_body(const PassArgs &a, int rep) {
+__device__ __forceinline__ void fwht_pass_body(const PassArgs &a, long long slot0, unsigned long long tile) {
     typedef typename Cfg::Real R;
     typedef typename Cfg::C2 C2;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -376,22 +400,7 @@ __device__ __forceinline__ bool fwht_pass_body(const PassArgs &a, int rep) {
     const uint32_t grp = tid >> Cfg::TB;
     const uint32_t t = tid & (Cfg::T - 1);
 
-    long long slot;
-    unsigned long long tile;
-    if constexpr (Cfg::G > 1) {
-        slot = (long long)blockIdx.x * Cfg::G + grp;
-        tile = 0;
-    } else if (a.fam_fast) {
-        constexpr int FPC = FamPerCta<Cfg, SRC>::v;
-        const unsigned long long L = blockIdx.x;
-        const unsigned long long np = ((unsigned long long)a.n_fam + FPC - 1) / FPC;
-        slot = (long long)(L % np) * FPC + rep;
-        tile = L / np;
-        if (rep > 0 && slot >= a.n_fam) return false;
-    } else {
-        slot = (long long)blockIdx.y + 65535LL * (long long)blockIdx.z;
-        tile = blockIdx.x;
-    }
+    long long slot = slot0 + (Cfg::G > 1 ? (long long)grp : 0LL);
     const bool active = slot < a.n_fam;
     if (!active) slot = a.n_fam - 1;   // run on valid data, write nothing
 
@@ -587,7 +596,11 @@ __device__ __forceinline__ bool fwht_pass_body(const PassArgs &a, int rep) {
         double out[6];
         float omx;
         group_reduce<Cfg::T, Cfg::NT, 6>(acc, qmax, out, omx, red);
-        if (active && t == 0) {
+        if (active && t == 0 && a.fam_out) {
+            FamMoments &o = a.fam_out[a.fam_base + slot];
+            o.m[0] = out[0]; o.m[1] = out[1]; o.m[2] = out[2]; o.m[3] = out[3];
+            o.cand = (cand && omx > a.cand_thr * a.cand_thr) ? 1ull : 0ull;
+        } else if (active && t == 0) {
             const long long tiles = (long long)(half >> Cfg::M) > 0 ? (long long)(half >> Cfg::M) : 1;
             TilePartial &tp = a.tile_out[(size_t)slot * (size_t)tiles + tile];
             tp.m[0] = out[0]; tp.m[1] = out[1]; tp.m[2] = out[2]; tp.m[3] = out[3];
@@ -595,23 +608,27 @@ __device__ __forceinline__ bool fwht_pass_body(const PassArgs &a, int rep) {
             tp.cand = (cand && omx > a.cand_thr * a.cand_thr) ? 1u : 0u;
         }
     }
-    return true;
 }
 
 template <class Cfg, int SRC, int DST, int PREC = 0>
 __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) fwht_pass_kernel(const PassArgs a) {
     constexpr int FPC = FamPerCta<Cfg, SRC>::v;
+    long long slot0;
+    unsigned long long tile;
     if constexpr (FPC == 1) {
-        fwht_pass_body<Cfg, SRC, DST, PREC>(a, 0);
+        pass_grid_item<Cfg, SRC>(a, 0, slot0, tile);
+        fwht_pass_body<Cfg, SRC, DST, PREC>(a, slot0, tile);
     } else {
         if (!a.fam_fast) {
-            fwht_pass_body<Cfg, SRC, DST, PREC>(a, 0);
+            pass_grid_item<Cfg, SRC>(a, 0, slot0, tile);
+            fwht_pass_body<Cfg, SRC, DST, PREC>(a, slot0, tile);
             return;
         }
 #pragma unroll 1
         for (int r = 0; r < FPC; ++r) {
             if (r) __syncthreads();                 // the tile buffer is reused
-            if (!fwht_pass_body<Cfg, SRC, DST, PREC>(a, r)) break;
+            if (!pass_grid_item<Cfg, SRC>(a, r, slot0, tile)) break;
+            fwht_pass_body<Cfg, SRC, DST, PREC>(a, slot0, tile);
         }
     }
 }

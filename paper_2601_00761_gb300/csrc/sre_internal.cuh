@@ -252,6 +252,9 @@ struct PassArgs {
     unsigned *cand_cnt;
     unsigned *cand_z;
     int cand_max;
+    // DST_MOMENTS on single-tile families: when set, the family's sums go
+    // straight to fam_out[fam_base + slot] instead of a tile partial
+    FamMoments *fam_out;
 };
 
 
