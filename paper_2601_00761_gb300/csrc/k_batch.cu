@@ -78,7 +78,9 @@ __device__ __forceinline__ void run_strided(const PassArgs &a, long long slot0, 
 
 __global__ void __launch_bounds__(256, 2) batch_persistent_kernel(const BatchQueue q) {
     __shared__ long long s_item;
+    __shared__ int s_seg;
     const int tid = threadIdx.x;
+    if (tid == 0) s_seg = 0;
 #pragma unroll 1
     for (;;) {
         __syncthreads();                                 // the previous item is done with s_item and smem
@@ -86,18 +88,19 @@ __global__ void __launch_bounds__(256, 2) batch_persistent_kernel(const BatchQue
             long long it = (long long)atomicAdd(q.next, 1ull);
             if (it >= q.n_items || *(volatile int *)q.abort_flag) it = -1;
             s_item = it;
+            // the item's segment: the last with start <= it. A CTA's items come
+            // in increasing order, so the search starts at its previous segment
+            // and almost always stops there or at the next one.
+            if (it >= 0) {
+                int g = s_seg;
+                while (g + 1 < q.n_segs && q.segs[g + 1].start <= it) ++g;
+                s_seg = g;
+            }
         }
         __syncthreads();
         const long long it = s_item;
         if (it < 0) return;
-        // the item's segment: the last with start <= it
-        int lo = 0, hi = q.n_segs - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (q.segs[mid].start <= it) lo = mid;
-            else hi = mid - 1;
-        }
-        const BatchSeg sg = q.segs[lo];
+        const BatchSeg sg = q.segs[s_seg];
         const long long l = it - sg.start;
         struct { int kind, bucket, batch, tile; long long slot0; } item;
         item.kind = sg.kind;
@@ -123,19 +126,26 @@ __global__ void __launch_bounds__(256, 2) batch_persistent_kernel(const BatchQue
         const int rs = item.batch % q.ring;               // ring slot (shared by all buckets in turn)
         const long long fb = (long long)kk * bk.B;
         const long long nf = bk.fam_total - fb < bk.B ? bk.fam_total - fb : bk.B;
-        __shared__ PassArgs s_args;
+        __shared__ __align__(16) PassArgs s_args;
         __shared__ int s_ok;
+        {
+            // the pass's arguments, copied by 16-byte words across the threads
+            static_assert(sizeof(PassArgs) % 8 == 0, "PassArgs copies in 8-byte words");
+            const unsigned long long *src = reinterpret_cast<const unsigned long long *>(
+                item.kind == BI_STRIDED ? &bk.strided : &bk.row);
+            unsigned long long *dst = reinterpret_cast<unsigned long long *>(&s_args);
+            for (int w = tid; w < (int)(sizeof(PassArgs) / 8); w += blockDim.x) dst[w] = src[w];
+        }
+        __syncthreads();
         if (tid == 0) {
             bool ok;
             if (item.kind == BI_STRIDED) {
                 // the ring slot's previous batch (of any bucket) must be done
                 ok = item.batch < q.ring ||
                      wait_count(q.done_row + (item.batch - q.ring), q.need_row[item.batch - q.ring], q.abort_flag, q.err);
-                s_args = bk.strided;
                 s_args.src = s_args.dst = (char *)q.inter + (size_t)rs * q.inter_slot_bytes;
             } else {
                 ok = wait_count(q.done_str + item.batch, q.need_str[item.batch], q.abort_flag, q.err);
-                s_args = bk.row;
                 s_args.src = (char *)q.inter + (size_t)rs * q.inter_slot_bytes;
                 s_args.tile_out = q.tiles + (size_t)rs * q.tiles_slot;
             }

@@ -57,16 +57,28 @@ def test_batched_graph_replay_with_new_states(sre):
 
 
 def test_batched_graph_follows_the_plan(sre):
-    """The same batch shape with another family batch size runs its own
-    launch sequence (a cached graph is keyed on the plan as well as the
-    shape): 4^16 families in launches of 1024, then of 4096."""
+    """The FP32 sweep of a batch is one persistent launch between the norms and
+    the per-state totals, whatever the family batch size asked for; the
+    tensor-core form runs the chunked launch sequence, whose cached graph is
+    keyed on the plan as well as the shape (4^16 families in launches of 1024,
+    then of 4096)."""
     p = torch.from_numpy(inputs.haar_state(16, 16).astype(np.complex64)).cuda()
     counts = []
-    for xb in (1024, 4096, 1024):
+    for xb in (1024, 4096):
         k0 = sre.sre_kernel_launches()
         r = sre.sre_exact_batched([p], x_batch=xb)[0]
         counts.append(sre.sre_kernel_launches() - k0)
         ref = sre.sre_exact(p, x_batch=xb, allow_nullity_error=True)
+        assert np.max(np.abs(np.array(r["M"]) - np.array(ref["M"]))) < TOL_M
+    # 2 norm kernels, the persistent sweep, the totals, and the FP64 recount of
+    # the flagged families (the x = 0 family always holds c = 1)
+    assert counts[0] == counts[1] <= 10
+    counts = []
+    for xb in (1024, 4096, 1024):
+        k0 = sre.sre_kernel_launches()
+        r = sre.sre_exact_batched([p], x_batch=xb, precision=sre.SRE_BF16X3_TC)[0]
+        counts.append(sre.sre_kernel_launches() - k0)
+        ref = sre.sre_exact(p, x_batch=xb, allow_nullity_error=True, precision=sre.SRE_BF16X3_TC)
         assert np.max(np.abs(np.array(r["M"]) - np.array(ref["M"]))) < TOL_M
     assert counts[0] == counts[2] and counts[0] > counts[1]
 
