@@ -8,10 +8,9 @@
 //   BI_STRIDED the strided pass of FPC families of a family batch of a
 //              two-pass state (N >= 15), one tile, into the batch's slot of an
 //              intermediate ring;
-//   BI_ROW     the row pass of one family of a batch, one tile, with the
-//              fused moments into a tile-partial ring; the last tile of a
-//              family to finish sums its tiles (fixed order) into the family
-//              sums.
+//   BI_ROW     the row pass of one family of a batch, all its tiles in turn,
+//              with the fused moments into a tile-partial ring, then the
+//              family's sums in tile order.
 // A batch's row items wait until all its strided items are done; a batch's
 // strided items wait until the batch that last used its ring slot is done.
 // Every item waits only on items earlier in the queue, which were dequeued by
@@ -79,8 +78,15 @@ __device__ __forceinline__ void run_strided(const PassArgs &a, long long slot0, 
 __global__ void __launch_bounds__(256, 2) batch_persistent_kernel(const BatchQueue q) {
     __shared__ long long s_item;
     __shared__ int s_seg;
+    __shared__ __align__(16) PassArgs s_args;            // arguments of the current two-pass item
+    __shared__ int s_ok;
+    __shared__ int s_have_kind, s_have_batch;           // whose arguments s_args holds (dependency met)
     const int tid = threadIdx.x;
-    if (tid == 0) s_seg = 0;
+    if (tid == 0) {
+        s_seg = 0;
+        s_have_kind = -1;
+        s_have_batch = -1;
+    }
 #pragma unroll 1
     for (;;) {
         __syncthreads();                                 // the previous item is done with s_item and smem
@@ -108,7 +114,7 @@ __global__ void __launch_bounds__(256, 2) batch_persistent_kernel(const BatchQue
         item.batch = sg.batch;
         if (sg.kind == BI_SINGLE) { item.slot0 = l * sg.aux; item.tile = 0; }
         else if (sg.kind == BI_STRIDED) { item.tile = (int)(l / sg.aux); item.slot0 = (l % sg.aux) * q.fpc; }
-        else { item.slot0 = l / sg.aux; item.tile = (int)(l % sg.aux); }
+        else { item.slot0 = l; item.tile = 0; }
         const BatchBucket &bk = q.buckets[item.bucket];
         if (item.kind == BI_SINGLE) {
             switch (bk.M) {
@@ -126,10 +132,11 @@ __global__ void __launch_bounds__(256, 2) batch_persistent_kernel(const BatchQue
         const int rs = item.batch % q.ring;               // ring slot (shared by all buckets in turn)
         const long long fb = (long long)kk * bk.B;
         const long long nf = bk.fam_total - fb < bk.B ? bk.fam_total - fb : bk.B;
-        __shared__ __align__(16) PassArgs s_args;
-        __shared__ int s_ok;
+        if (s_have_kind != item.kind || s_have_batch != item.batch) {
+            // (when the CTA's previous two-pass item was of the same pass and
+            // batch, its arguments are in place and its dependency is met)
         {
-            // the pass's arguments, copied by 16-byte words across the threads
+            // the pass's arguments, copied by 8-byte words across the threads
             static_assert(sizeof(PassArgs) % 8 == 0, "PassArgs copies in 8-byte words");
             const unsigned long long *src = reinterpret_cast<const unsigned long long *>(
                 item.kind == BI_STRIDED ? &bk.strided : &bk.row);
@@ -152,9 +159,12 @@ __global__ void __launch_bounds__(256, 2) batch_persistent_kernel(const BatchQue
             s_args.fam_base = fb;
             s_args.n_fam = nf;
             s_ok = ok;
+            s_have_kind = ok ? item.kind : -1;
+            s_have_batch = ok ? item.batch : -1;
         }
         __syncthreads();
         if (!s_ok) continue;
+        }
         const PassArgs &a = s_args;
         if (item.kind == BI_STRIDED) {
             switch (bk.K) {
@@ -167,46 +177,36 @@ __global__ void __launch_bounds__(256, 2) batch_persistent_kernel(const BatchQue
             if (tid == 0) release_add(q.done_str + item.batch, 1u);
             continue;
         }
-        // BI_ROW
+        // BI_ROW: every row tile of one family in turn, then its sums in tile order
         {
-            fwht_pass_body<TileCfg<float, 13, 0, 5, 1>, SRC_BUF, DST_MOMENTS, 0>(a, item.slot0, (unsigned long long)item.tile);
-            __syncthreads();
-            __shared__ unsigned s_last;
-            if (tid == 0) {
-                __threadfence();
-                unsigned *fc = q.fam_cnt + (size_t)rs * q.fam_slot + (size_t)item.slot0;   // one counter per family
-                s_last = atomicAdd(fc, 1u) == (unsigned)bk.tiles_row - 1u;
-                if (s_last) *fc = 0u;                     // ready for the slot's next batch
+#pragma unroll 1
+            for (int t = 0; t < bk.tiles_row; ++t) {
+                if (t) __syncthreads();                   // the tile buffer is reused
+                fwht_pass_body<TileCfg<float, 13, 0, 5, 1>, SRC_BUF, DST_MOMENTS, 0>(a, item.slot0, (unsigned long long)t);
             }
             __syncthreads();
-            if (s_last) {
-                // the family's tile partials, summed in tile order by one warp
-                if (tid < 32) {
-                    __threadfence();
-                    const TilePartial *tp = a.tile_out + (size_t)item.slot0 * (size_t)bk.tiles_row;
-                    double m0 = 0, m1 = 0, m2 = 0, m3 = 0, c = 0;
-                    for (int t = tid; t < bk.tiles_row; t += 32) {
-                        m0 += __ldcg(&tp[t].m[0]); m1 += __ldcg(&tp[t].m[1]);
-                        m2 += __ldcg(&tp[t].m[2]); m3 += __ldcg(&tp[t].m[3]);
-                        c += (double)__ldcg(&tp[t].cand);
-                    }
+            if (tid < 32) {
+                const TilePartial *tp = a.tile_out + (size_t)item.slot0 * (size_t)bk.tiles_row;
+                double m0 = 0, m1 = 0, m2 = 0, m3 = 0, c = 0;
+                for (int t = tid; t < bk.tiles_row; t += 32) {
+                    m0 += tp[t].m[0]; m1 += tp[t].m[1]; m2 += tp[t].m[2]; m3 += tp[t].m[3];
+                    c += (double)tp[t].cand;
+                }
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        m0 += __shfl_xor_sync(0xffffffffu, m0, o);
-                        m1 += __shfl_xor_sync(0xffffffffu, m1, o);
-                        m2 += __shfl_xor_sync(0xffffffffu, m2, o);
-                        m3 += __shfl_xor_sync(0xffffffffu, m3, o);
-                        c += __shfl_xor_sync(0xffffffffu, c, o);
-                    }
-                    if (tid == 0) {
-                        FamMoments &o = bk.fm[fb + item.slot0];
-                        o.m[0] = m0; o.m[1] = m1; o.m[2] = m2; o.m[3] = m3;
-                        o.cand = (unsigned long long)c;
-                    }
+                for (int o = 16; o > 0; o >>= 1) {
+                    m0 += __shfl_xor_sync(0xffffffffu, m0, o);
+                    m1 += __shfl_xor_sync(0xffffffffu, m1, o);
+                    m2 += __shfl_xor_sync(0xffffffffu, m2, o);
+                    m3 += __shfl_xor_sync(0xffffffffu, m3, o);
+                    c += __shfl_xor_sync(0xffffffffu, c, o);
+                }
+                if (tid == 0) {
+                    FamMoments &o = bk.fm[fb + item.slot0];
+                    o.m[0] = m0; o.m[1] = m1; o.m[2] = m2; o.m[3] = m3;
+                    o.cand = (unsigned long long)c;
+                    release_add(q.done_row + item.batch, 1u);
                 }
             }
-            __syncthreads();
-            if (tid == 0) release_add(q.done_row + item.batch, 1u);
         }
     }
 }

@@ -13,7 +13,7 @@ enum BatchItemKind { BI_SINGLE = 0, BI_STRIDED = 1, BI_ROW = 2 };
 //   BI_SINGLE:  slot0 = l * aux (aux = families per CTA)
 //   BI_STRIDED: tile = l / aux, slot0 = (l % aux) * fpc (aux = family groups
 //               of the batch; tiles outer, so the CTAs in flight share a tile)
-//   BI_ROW:     slot0 = l / aux, tile = l % aux (aux = row tiles per family)
+//   BI_ROW:     slot0 = l (one family, all its row tiles)
 struct BatchSeg {
     int kind;           // BatchItemKind
     int bucket;         // index into BatchQueue::buckets
@@ -44,12 +44,10 @@ struct BatchQueue {
     unsigned long long *next;    // queue head (zeroed before the launch)
     unsigned *done_str, *done_row;   // per global batch: strided / row items done (zeroed)
     const unsigned *need_str, *need_row;   // per global batch: item counts
-    unsigned *fam_cnt;           // per ring slot and family: row tiles done (zero; reset by the last tile)
     void *inter;                 // intermediate ring: `ring` slots of inter_slot_bytes
     size_t inter_slot_bytes;
     TilePartial *tiles;          // tile-partial ring: `ring` slots of tiles_slot partials
     size_t tiles_slot;
-    size_t fam_slot;             // families per ring slot (counters)
     int ring;
     int fpc;                     // families per strided item
     int *err;                    // device error word (SRE_ERR_TIMEOUT)

@@ -719,7 +719,6 @@ struct BatchWS {
     BatchBucket *pbuckets;
     BatchSeg *psegs;
     unsigned *need, *done;               // per global batch: [need_str, need_row], [done_str, done_row]
-    unsigned *fam_cnt;
     unsigned long long *next;
     int *abort_flag, *err;
     void *ring;
@@ -730,8 +729,8 @@ struct BatchWS {
 // bucket's families in two-pass batches (N >= 15: a strided pass of N - 14
 // rows and a 13-bit row pass) or single-pass CTAs (N <= 14).
 constexpr int PERSIST_RING = 3;                       // intermediate ring slots
-constexpr size_t PERSIST_SLOT_BYTES = 32ull << 20;   // intermediate bytes per ring slot
-constexpr int PERSIST_FPC = 4;                        // families per strided item
+constexpr size_t PERSIST_SLOT_BYTES = 64ull << 20;   // intermediate bytes per ring slot
+constexpr int PERSIST_FPC = 8;                        // families per strided item
 constexpr int PERSIST_NMAX = 20;
 
 struct PersistLayout {
@@ -740,10 +739,13 @@ struct PersistLayout {
     std::vector<unsigned> need_str, need_row;         // per global batch
     long long n_items = 0;
     int batches = 0;
-    size_t fm_total = 0, fam_slot = 0, tiles_slot = 0;
+    size_t fm_total = 0, tiles_slot = 0;
 };
 
 bool persist_ok(const std::vector<BucketPlan> &B, int prec) {
+#ifdef SRE_NO_PERSIST
+    return false;
+#endif
     if (prec != 0) return false;
     for (const auto &b : B)
         if (b.N > PERSIST_NMAX) return false;
@@ -784,7 +786,6 @@ void persist_plan(const std::vector<BucketPlan> &B, PersistLayout &L) {
         const long long Bf = persist_batch_families(N);
         const int tiles = 1 << (N - 1 - 13);
         L.buckets[bi].first_batch = L.batches;
-        L.fam_slot = std::max(L.fam_slot, (size_t)Bf);
         L.tiles_slot = std::max(L.tiles_slot, (size_t)(Bf * tiles));
         for (long long fb = 0; fb < fams; fb += Bf) {
             const long long nf = std::min(Bf, fams - fb);
@@ -792,9 +793,9 @@ void persist_plan(const std::vector<BucketPlan> &B, PersistLayout &L) {
             const int k = L.batches++;
             push(BI_STRIDED, (int)bi, k, groups, (long long)tiles * groups);
             if (pending_row >= 0) push(BI_ROW, pending_bucket, pending_row, pending_aux, pending_count);
-            pending_row = k; pending_bucket = (int)bi; pending_aux = tiles; pending_count = nf * tiles;
+            pending_row = k; pending_bucket = (int)bi; pending_aux = 1; pending_count = nf;
             L.need_str.push_back((unsigned)((long long)tiles * groups));
-            L.need_row.push_back((unsigned)(nf * tiles));
+            L.need_row.push_back((unsigned)nf);
         }
     }
     if (pending_row >= 0) push(BI_ROW, pending_bucket, pending_row, pending_aux, pending_count);
@@ -914,7 +915,6 @@ void layout_batch(Arena &A, int count, std::vector<BucketPlan> &B, BatchWS &w, c
         w.psegs = A.take<BatchSeg>(L->segs.size());
         w.need = A.take<unsigned>(2 * (size_t)L->batches + 2);
         w.done = A.take<unsigned>(2 * (size_t)L->batches + 2);
-        w.fam_cnt = A.take<unsigned>((size_t)PERSIST_RING * L->fam_slot + 1);
         w.next = A.take<unsigned long long>(1);
         w.abort_flag = A.take<int>(1);
         w.err = A.take<int>(1);
@@ -954,7 +954,6 @@ sre_status persist_main(const std::vector<BucketPlan> &B, const BatchWS &w, cons
         count_launches(2);
     }
     CK(cudaMemsetAsync(w.done, 0, sizeof(unsigned) * (2 * (size_t)L.batches + 2), st));
-    CK(cudaMemsetAsync(w.fam_cnt, 0, sizeof(unsigned) * ((size_t)PERSIST_RING * L.fam_slot + 1), st));
     CK(cudaMemsetAsync(w.next, 0, sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(w.abort_flag, 0, sizeof(int), st));
     CK(cudaMemsetAsync(w.err, 0, sizeof(int), st));
@@ -969,12 +968,10 @@ sre_status persist_main(const std::vector<BucketPlan> &B, const BatchWS &w, cons
     q.done_row = w.done + L.batches;
     q.need_str = w.need;
     q.need_row = w.need + L.batches;
-    q.fam_cnt = w.fam_cnt;
     q.inter = w.ring;
     q.inter_slot_bytes = PERSIST_SLOT_BYTES;
     q.tiles = w.ring_tiles;
     q.tiles_slot = L.tiles_slot;
-    q.fam_slot = L.fam_slot;
     q.ring = PERSIST_RING;
     q.fpc = PERSIST_FPC;
     q.err = w.err;
@@ -1958,7 +1955,6 @@ sre_status sre_selftest_queue_wait(void *stream) {
     q.need_row = u + 1;
     q.done_str = u + 2;
     q.done_row = u + 3;
-    q.fam_cnt = u + 4;
     q.ring = PERSIST_RING;
     q.fpc = PERSIST_FPC;
     q.err = fl;
