@@ -57,19 +57,29 @@ __device__ __forceinline__ void release_add(unsigned *ctr, unsigned v) {
     atomicAdd(ctr, v);
 }
 
+// The pass bodies are separate functions so that each is register-allocated
+// on its own rather than together with every other instantiation.
 template <int M>
-__device__ __forceinline__ void run_single(const PassArgs &a, long long slot0) {
+__device__ __noinline__ void run_single(const PassArgs &a, long long slot0) {
     fwht_pass_body<typename SingleCfgOf<float, M>::type, SRC_PSI_FAMILY, DST_MOMENTS, 0>(a, slot0, 0);
 }
 
 template <int K>
-__device__ __forceinline__ void run_strided(const PassArgs &a, long long slot0, int fpc, unsigned long long tile) {
+__device__ __noinline__ void run_strided(const PassArgs &a, long long slot0, int fpc, unsigned long long tile) {
     typedef TileCfg<float, 13, 13 - K, 5, 1> Cfg;
 #pragma unroll 1
     for (int r = 0; r < fpc; ++r) {
         if (slot0 + r >= a.n_fam) break;
         if (r) __syncthreads();                       // the tile buffer is reused
         fwht_pass_body<Cfg, SRC_PSI_FAMILY, DST_BUF, 0>(a, slot0 + r, tile);
+    }
+}
+
+__device__ __noinline__ void run_row(const PassArgs &a, long long slot, int tiles) {
+#pragma unroll 1
+    for (int t = 0; t < tiles; ++t) {
+        if (t) __syncthreads();                           // the tile buffer is reused
+        fwht_pass_body<TileCfg<float, 13, 0, 5, 1>, SRC_BUF, DST_MOMENTS, 0>(a, slot, (unsigned long long)t);
     }
 }
 
@@ -179,11 +189,7 @@ __global__ void __launch_bounds__(256, 2) batch_persistent_kernel(const BatchQue
         }
         // BI_ROW: every row tile of one family in turn, then its sums in tile order
         {
-#pragma unroll 1
-            for (int t = 0; t < bk.tiles_row; ++t) {
-                if (t) __syncthreads();                   // the tile buffer is reused
-                fwht_pass_body<TileCfg<float, 13, 0, 5, 1>, SRC_BUF, DST_MOMENTS, 0>(a, item.slot0, (unsigned long long)t);
-            }
+            run_row(a, item.slot0, bk.tiles_row);
             __syncthreads();
             if (tid < 32) {
                 const TilePartial *tp = a.tile_out + (size_t)item.slot0 * (size_t)bk.tiles_row;

@@ -728,8 +728,9 @@ struct BatchWS {
 // The persistent sweep's work layout, built on the host (k_batch.cuh): every
 // bucket's families in two-pass batches (N >= 15: a strided pass of N - 14
 // rows and a 13-bit row pass) or single-pass CTAs (N <= 14).
-constexpr int PERSIST_RING = 3;                       // intermediate ring slots
-constexpr size_t PERSIST_SLOT_BYTES = 64ull << 20;   // intermediate bytes per ring slot
+constexpr int PERSIST_AHEAD = 2;                      // strided batches issued ahead of a batch's row items
+constexpr int PERSIST_RING = PERSIST_AHEAD + 3;       // intermediate ring slots
+constexpr size_t PERSIST_SLOT_BYTES = 48ull << 20;   // intermediate bytes per ring slot
 constexpr int PERSIST_FPC = 8;                        // families per strided item
 constexpr int PERSIST_NMAX = 20;
 
@@ -777,8 +778,10 @@ void persist_plan(const std::vector<BucketPlan> &B, PersistLayout &L) {
         L.n_items += count;
     };
     L.buckets.resize(B.size());
-    int pending_row = -1, pending_bucket = -1, pending_aux = 0;
-    long long pending_count = 0;
+    // a batch's row items follow the strided items of the PERSIST_AHEAD
+    // batches after it, so that they rarely wait
+    struct RowSeg { int bucket, batch; long long nf; };
+    std::vector<RowSeg> pending;
     for (size_t bi = 0; bi < B.size(); ++bi) {
         const int N = B[bi].N;
         if (N < 15) continue;
@@ -792,13 +795,16 @@ void persist_plan(const std::vector<BucketPlan> &B, PersistLayout &L) {
             const int groups = (int)((nf + PERSIST_FPC - 1) / PERSIST_FPC);
             const int k = L.batches++;
             push(BI_STRIDED, (int)bi, k, groups, (long long)tiles * groups);
-            if (pending_row >= 0) push(BI_ROW, pending_bucket, pending_row, pending_aux, pending_count);
-            pending_row = k; pending_bucket = (int)bi; pending_aux = 1; pending_count = nf;
+            pending.push_back({(int)bi, k, nf});
+            if ((int)pending.size() > PERSIST_AHEAD) {
+                push(BI_ROW, pending.front().bucket, pending.front().batch, 1, pending.front().nf);
+                pending.erase(pending.begin());
+            }
             L.need_str.push_back((unsigned)((long long)tiles * groups));
             L.need_row.push_back((unsigned)nf);
         }
     }
-    if (pending_row >= 0) push(BI_ROW, pending_bucket, pending_row, pending_aux, pending_count);
+    for (const RowSeg &r : pending) push(BI_ROW, r.bucket, r.batch, 1, r.nf);
     for (size_t bi = 0; bi < B.size(); ++bi) {
         const int N = B[bi].N;
         if (N >= 15) continue;
