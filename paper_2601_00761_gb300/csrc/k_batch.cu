@@ -8,9 +8,9 @@
 //   BI_STRIDED the strided pass of FPC families of a family batch of a
 //              two-pass state (N >= 15), one tile, into the batch's slot of an
 //              intermediate ring;
-//   BI_ROW     the row pass of one family of a batch, all its tiles in turn,
-//              with the fused moments into a tile-partial ring, then the
-//              family's sums in tile order.
+//   BI_ROW     the row pass of RPI families of a batch, each with all its
+//              tiles in turn and the fused moments into a tile-partial ring,
+//              then the family's sums in tile order.
 // A batch's row items wait until all its strided items are done; a batch's
 // strided items wait until the batch that last used its ring slot is done.
 // Every item waits only on items earlier in the queue, which were dequeued by
@@ -91,8 +91,10 @@ __global__ void __launch_bounds__(256, 2) batch_persistent_kernel(const BatchQue
     __shared__ __align__(16) PassArgs s_args;            // arguments of the current two-pass item
     __shared__ int s_ok;
     __shared__ int s_have_kind, s_have_batch;           // whose arguments s_args holds (dependency met)
+    __shared__ long long s_next;
     const int tid = threadIdx.x;
     if (tid == 0) {
+        s_next = (long long)atomicAdd(q.next, 1ull);
         s_seg = 0;
         s_have_kind = -1;
         s_have_batch = -1;
@@ -101,7 +103,10 @@ __global__ void __launch_bounds__(256, 2) batch_persistent_kernel(const BatchQue
     for (;;) {
         __syncthreads();                                 // the previous item is done with s_item and smem
         if (tid == 0) {
-            long long it = (long long)atomicAdd(q.next, 1ull);
+            // the item taken from the queue one item ago (its dequeue overlapped
+            // the previous item's work), and the next one taken now
+            long long it = s_next;
+            s_next = (long long)atomicAdd(q.next, 1ull);
             if (it >= q.n_items || *(volatile int *)q.abort_flag) it = -1;
             s_item = it;
             // the item's segment: the last with start <= it. A CTA's items come
@@ -124,7 +129,7 @@ __global__ void __launch_bounds__(256, 2) batch_persistent_kernel(const BatchQue
         item.batch = sg.batch;
         if (sg.kind == BI_SINGLE) { item.slot0 = l * sg.aux; item.tile = 0; }
         else if (sg.kind == BI_STRIDED) { item.tile = (int)(l / sg.aux); item.slot0 = (l % sg.aux) * q.fpc; }
-        else { item.slot0 = l; item.tile = 0; }
+        else { item.slot0 = l * sg.aux; item.tile = 0; }
         const BatchBucket &bk = q.buckets[item.bucket];
         if (item.kind == BI_SINGLE) {
             switch (bk.M) {
@@ -187,12 +192,16 @@ __global__ void __launch_bounds__(256, 2) batch_persistent_kernel(const BatchQue
             if (tid == 0) release_add(q.done_str + item.batch, 1u);
             continue;
         }
-        // BI_ROW: every row tile of one family in turn, then its sums in tile order
-        {
-            run_row(a, item.slot0, bk.tiles_row);
+        // BI_ROW: families slot0 .. slot0 + aux - 1 in turn, every row tile of a
+        // family, then its sums in tile order
+        const long long fam_end = item.slot0 + sg.aux < nf ? item.slot0 + sg.aux : nf;
+#pragma unroll 1
+        for (long long f = item.slot0; f < fam_end; ++f) {
+            if (f > item.slot0) __syncthreads();          // the tile buffer is reused
+            run_row(a, f, bk.tiles_row);
             __syncthreads();
             if (tid < 32) {
-                const TilePartial *tp = a.tile_out + (size_t)item.slot0 * (size_t)bk.tiles_row;
+                const TilePartial *tp = a.tile_out + (size_t)f * (size_t)bk.tiles_row;
                 double m0 = 0, m1 = 0, m2 = 0, m3 = 0, c = 0;
                 for (int t = tid; t < bk.tiles_row; t += 32) {
                     m0 += tp[t].m[0]; m1 += tp[t].m[1]; m2 += tp[t].m[2]; m3 += tp[t].m[3];
@@ -207,13 +216,13 @@ __global__ void __launch_bounds__(256, 2) batch_persistent_kernel(const BatchQue
                     c += __shfl_xor_sync(0xffffffffu, c, o);
                 }
                 if (tid == 0) {
-                    FamMoments &o = bk.fm[fb + item.slot0];
+                    FamMoments &o = bk.fm[fb + f];
                     o.m[0] = m0; o.m[1] = m1; o.m[2] = m2; o.m[3] = m3;
                     o.cand = (unsigned long long)c;
-                    release_add(q.done_row + item.batch, 1u);
                 }
             }
         }
+        if (tid == 0) release_add(q.done_row + item.batch, (unsigned)(fam_end - item.slot0));
     }
 }
 

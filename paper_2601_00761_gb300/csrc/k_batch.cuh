@@ -13,7 +13,7 @@ enum BatchItemKind { BI_SINGLE = 0, BI_STRIDED = 1, BI_ROW = 2 };
 //   BI_SINGLE:  slot0 = l * aux (aux = families per CTA)
 //   BI_STRIDED: tile = l / aux, slot0 = (l % aux) * fpc (aux = family groups
 //               of the batch; tiles outer, so the CTAs in flight share a tile)
-//   BI_ROW:     slot0 = l (one family, all its row tiles)
+//   BI_ROW:     slot0 = l * aux (aux = families per CTA, all their row tiles)
 struct BatchSeg {
     int kind;           // BatchItemKind
     int bucket;         // index into BatchQueue::buckets

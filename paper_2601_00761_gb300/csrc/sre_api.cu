@@ -731,7 +731,8 @@ struct BatchWS {
 constexpr int PERSIST_AHEAD = 2;                      // strided batches issued ahead of a batch's row items
 constexpr int PERSIST_RING = PERSIST_AHEAD + 3;       // intermediate ring slots
 constexpr size_t PERSIST_SLOT_BYTES = 48ull << 20;   // intermediate bytes per ring slot
-constexpr int PERSIST_FPC = 8;                        // families per strided item
+constexpr int PERSIST_FPC = 16;                       // families per strided item
+constexpr int PERSIST_RPI = 4;                        // families per row item
 constexpr int PERSIST_NMAX = 20;
 
 struct PersistLayout {
@@ -797,14 +798,15 @@ void persist_plan(const std::vector<BucketPlan> &B, PersistLayout &L) {
             push(BI_STRIDED, (int)bi, k, groups, (long long)tiles * groups);
             pending.push_back({(int)bi, k, nf});
             if ((int)pending.size() > PERSIST_AHEAD) {
-                push(BI_ROW, pending.front().bucket, pending.front().batch, 1, pending.front().nf);
+                push(BI_ROW, pending.front().bucket, pending.front().batch, PERSIST_RPI,
+                     (pending.front().nf + PERSIST_RPI - 1) / PERSIST_RPI);
                 pending.erase(pending.begin());
             }
             L.need_str.push_back((unsigned)((long long)tiles * groups));
             L.need_row.push_back((unsigned)nf);
         }
     }
-    for (const RowSeg &r : pending) push(BI_ROW, r.bucket, r.batch, 1, r.nf);
+    for (const RowSeg &r : pending) push(BI_ROW, r.bucket, r.batch, PERSIST_RPI, (r.nf + PERSIST_RPI - 1) / PERSIST_RPI);
     for (size_t bi = 0; bi < B.size(); ++bi) {
         const int N = B[bi].N;
         if (N >= 15) continue;
