@@ -91,11 +91,15 @@ __global__ void __launch_bounds__(256, 2) batch_persistent_kernel(const BatchQue
     __shared__ __align__(16) PassArgs s_args;            // arguments of the current two-pass item
     __shared__ int s_ok;
     __shared__ int s_have_kind, s_have_batch;           // whose arguments s_args holds (dependency met)
-    __shared__ long long s_next;
+    __shared__ long long s_seg_end;
     const int tid = threadIdx.x;
+    // thread 0's next item: taken from the queue while the current item runs,
+    // needed only at the top of the next iteration
+    unsigned long long next_it = 0;
     if (tid == 0) {
-        s_next = (long long)atomicAdd(q.next, 1ull);
+        next_it = atomicAdd(q.next, 1ull);
         s_seg = 0;
+        s_seg_end = 0;
         s_have_kind = -1;
         s_have_batch = -1;
     }
@@ -103,19 +107,19 @@ __global__ void __launch_bounds__(256, 2) batch_persistent_kernel(const BatchQue
     for (;;) {
         __syncthreads();                                 // the previous item is done with s_item and smem
         if (tid == 0) {
-            // the item taken from the queue one item ago (its dequeue overlapped
-            // the previous item's work), and the next one taken now
-            long long it = s_next;
-            s_next = (long long)atomicAdd(q.next, 1ull);
+            // the item taken from the queue one item ago (its dequeue ran during
+            // the previous item's work)
+            long long it = (long long)next_it;
             if (it >= q.n_items || *(volatile int *)q.abort_flag) it = -1;
             s_item = it;
             // the item's segment: the last with start <= it. A CTA's items come
             // in increasing order, so the search starts at its previous segment
-            // and almost always stops there or at the next one.
-            if (it >= 0) {
+            // (whose end is kept in shared memory) and almost always stops there.
+            if (it >= 0 && it >= s_seg_end) {
                 int g = s_seg;
                 while (g + 1 < q.n_segs && q.segs[g + 1].start <= it) ++g;
                 s_seg = g;
+                s_seg_end = g + 1 < q.n_segs ? q.segs[g + 1].start : q.n_items;
             }
         }
         __syncthreads();
@@ -131,6 +135,7 @@ __global__ void __launch_bounds__(256, 2) batch_persistent_kernel(const BatchQue
         else if (sg.kind == BI_STRIDED) { item.tile = (int)(l / sg.aux); item.slot0 = (l % sg.aux) * q.fpc; }
         else { item.slot0 = l * sg.aux; item.tile = 0; }
         const BatchBucket &bk = q.buckets[item.bucket];
+        if (tid == 0) next_it = atomicAdd(q.next, 1ull);
         if (item.kind == BI_SINGLE) {
             switch (bk.M) {
 #define C(m) case m: run_single<m>(bk.single, item.slot0); break;

@@ -728,11 +728,11 @@ struct BatchWS {
 // The persistent sweep's work layout, built on the host (k_batch.cuh): every
 // bucket's families in two-pass batches (N >= 15: a strided pass of N - 14
 // rows and a 13-bit row pass) or single-pass CTAs (N <= 14).
-constexpr int PERSIST_AHEAD = 2;                      // strided batches issued ahead of a batch's row items
-constexpr int PERSIST_RING = PERSIST_AHEAD + 3;       // intermediate ring slots
-constexpr size_t PERSIST_SLOT_BYTES = 48ull << 20;   // intermediate bytes per ring slot
-constexpr int PERSIST_FPC = 16;                       // families per strided item
-constexpr int PERSIST_RPI = 4;                        // families per row item
+constexpr int PERSIST_AHEAD = 1;                      // strided batches issued ahead of a batch's row items
+constexpr int PERSIST_RING = PERSIST_AHEAD + 2;       // intermediate ring slots
+constexpr size_t PERSIST_SLOT_BYTES = 1ull << 30;    // intermediate bytes per ring slot (4096 families at N = 16)
+constexpr int PERSIST_FPC = 8;                        // families per strided item
+constexpr int PERSIST_RPI = 2;                        // families per row item
 constexpr int PERSIST_NMAX = 20;
 
 struct PersistLayout {
