@@ -166,11 +166,13 @@ SRE_API sre_status sre_exact(const void *psi_c64_dev, int N, const sre_opts *opt
 
 /* Exact M_1..M_3 and nullity of `count` states of possibly different N in
  * one call (Algorithm 1 per state; psi_ptrs_host[i] a device pointer,
- * Ns_host[i] in 1..20). States are grouped by N; each launch covers every
- * (state, family) item of a chunk of same-N states, and the launch sequence
- * of the whole batch is captured once into a CUDA graph (cached for the same
- * batch shape) and replayed; the FP64 nullity recount of candidate families
- * follows, as in sre_exact. Plans come from sre_autotune's table when opts leaves the tiling
+ * Ns_host[i] in 1..20). States are grouped by N. In the FP32 sweep every
+ * family of every state with N <= 14 (one shared-memory tile per family) is
+ * one item of a single persistent launch; each launch for N >= 15 covers the
+ * (state, family) items of a chunk of same-N states. The launch sequence of
+ * the whole batch is captured once into a CUDA graph (cached for the same
+ * batch shape and plans) and replayed; the FP64 nullity recount of candidate
+ * families follows, as in sre_exact. Plans come from sre_autotune's table when opts leaves the tiling
  * at 0. out: host array of `count` results (a state whose stabilizer count is
  * not a power of two gets nullity -1). workspace must be NULL (library
  * workspace). Returns SRE_EZERO if a state has zero norm. */
@@ -324,17 +326,6 @@ SRE_API unsigned long long sre_device_allocations(void);
  * (about a second), SRE_OK if the wait completed (a broken barrier), or
  * SRE_ECUDA. Synchronises the stream. */
 SRE_API sre_status sre_selftest_bounded_wait(void *stream);
-
-/* Self-test of the bounded dependency waits of the persistent batched sweep
- * (no counterpart in the paper). sre_exact_batched runs every family of every
- * state as one queue of work items in one launch; an item that needs earlier
- * items (the row pass of a family batch after its strided pass, a ring slot
- * after its previous batch) waits on a device counter for at most about a
- * second of the global timer, then raises SRE_ERR_TIMEOUT and an abort flag
- * that ends the launch. This test launches one row item whose strided items
- * never run, so its wait can only end by the bound: it returns SRE_ETIMEOUT
- * (about a second) and leaves the context usable. Synchronises the stream. */
-SRE_API sre_status sre_selftest_queue_wait(void *stream);
 
 /* Pass timing inside sre_mc: enable = 1 clears the counters and starts
  * recording CUDA events around every full-batch family-transform pass launch

@@ -20,7 +20,7 @@ __all__ = ["sre_version", "sre_last_error", "sre_default_opts", "sre_make_plan",
            "sre_release_workspace", "sre_norm2", "sre_exact", "sre_exact_batched", "sre_mc",
            "pauli_x_marginal", "stabilizer_nullity", "apply_clifford_tdoped_circuit",
            "sre_family_spectrum", "sre_family_spectrum_f64", "sre_philox_blocks", "sre_kernel_launches", "sre_device_allocations", "sre_tc_gemm_selftest",
-           "sre_selftest_bounded_wait", "sre_selftest_queue_wait",
+           "sre_selftest_bounded_wait",
            "sre_profile_passes", "sre_pass_timing", "sre_exact_noalloc", "sre_autotune", "SreError",
            "SRE_FP32_SIMT", "SRE_BF16X2_TC", "SRE_BF16X3_TC", "SRE_MC_UNIFORM", "SRE_MC_MARGINAL",
            "lib_path", "load"]
@@ -125,7 +125,6 @@ def load():
         "sre_tc_gemm_selftest": ([_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp],
                                  st),
         "sre_selftest_bounded_wait": ([_vp], st),
-        "sre_selftest_queue_wait": ([_vp], st),
         "sre_autotune": ([_vp, ctypes.c_int, _vp, ctypes.POINTER(Opts)], st),
         "sre_exact_noalloc": ([_vp, ctypes.c_int, ctypes.POINTER(Opts), _vp, ctypes.POINTER(Result)], st),
         "sre_pass_timing": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
@@ -374,12 +373,6 @@ def sre_philox_blocks(ctr_key):
     _check(load().sre_philox_blocks(ctypes.c_void_p(ctr_key.data_ptr()), ctypes.c_void_p(out.data_ptr()), n,
                                     _stream()))
     return out
-
-
-def sre_selftest_queue_wait() -> int:
-    """Run the persistent-queue wait self-test on the current stream; returns
-    the status (SRE_ETIMEOUT when the bound works)."""
-    return int(load().sre_selftest_queue_wait(_stream()))
 
 
 def sre_selftest_bounded_wait() -> int:

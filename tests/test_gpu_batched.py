@@ -1,6 +1,7 @@
-"""GPU: the batched exact sweep (one launch per same-N chunk, captured into a
-CUDA graph) against sre_exact per state, the graph replay on new states of
-the same shape, and the autotuner."""
+"""GPU: the batched exact sweep (one persistent launch over the single-pass
+states, one launch per same-N chunk of the larger ones, captured into a CUDA
+graph) against sre_exact per state, the graph replay on new states of the same
+shape, and the autotuner."""
 import numpy as np
 import pytest
 
@@ -57,30 +58,46 @@ def test_batched_graph_replay_with_new_states(sre):
 
 
 def test_batched_graph_follows_the_plan(sre):
-    """The FP32 sweep of a batch is one persistent launch between the norms and
-    the per-state totals, whatever the family batch size asked for; the
-    tensor-core form runs the chunked launch sequence, whose cached graph is
-    keyed on the plan as well as the shape (4^16 families in launches of 1024,
-    then of 4096)."""
+    """A two-pass state (N = 16) runs the chunked launch sequence, whose cached
+    graph is keyed on the plan as well as the shape: 4^16 families in launches
+    of 1024 families, then of 4096, then of 1024 again (the first graph
+    replayed), in the FP32 and the tensor-core forms."""
     p = torch.from_numpy(inputs.haar_state(16, 16).astype(np.complex64)).cuda()
-    counts = []
-    for xb in (1024, 4096):
+    for prec in (sre.SRE_FP32_SIMT, sre.SRE_BF16X3_TC):
+        counts = []
+        for xb in (1024, 4096, 1024):
+            k0 = sre.sre_kernel_launches()
+            r = sre.sre_exact_batched([p], x_batch=xb, precision=prec)[0]
+            counts.append(sre.sre_kernel_launches() - k0)
+            ref = sre.sre_exact(p, x_batch=xb, allow_nullity_error=True, precision=prec)
+            assert np.max(np.abs(np.array(r["M"]) - np.array(ref["M"]))) < TOL_M
+        assert counts[0] == counts[2] and counts[0] > counts[1]
+
+
+def test_batched_single_pass_states_share_one_launch(sre):
+    """Every family of every FP32 state with N <= 14 is an item of one
+    persistent launch: batches of one and of two states of each N = 1 .. 14
+    (then with a chunked N = 15 state and product states) match the per-state
+    sweeps, and the second state of each N adds no kernel launch."""
+    def launches(states):
         k0 = sre.sre_kernel_launches()
-        r = sre.sre_exact_batched([p], x_batch=xb)[0]
-        counts.append(sre.sre_kernel_launches() - k0)
-        ref = sre.sre_exact(p, x_batch=xb, allow_nullity_error=True)
-        assert np.max(np.abs(np.array(r["M"]) - np.array(ref["M"]))) < TOL_M
-    # 2 norm kernels, the persistent sweep, the totals, and the FP64 recount of
-    # the flagged families (the x = 0 family always holds c = 1)
-    assert counts[0] == counts[1] <= 10
-    counts = []
-    for xb in (1024, 4096, 1024):
-        k0 = sre.sre_kernel_launches()
-        r = sre.sre_exact_batched([p], x_batch=xb, precision=sre.SRE_BF16X3_TC)[0]
-        counts.append(sre.sre_kernel_launches() - k0)
-        ref = sre.sre_exact(p, x_batch=xb, allow_nullity_error=True, precision=sre.SRE_BF16X3_TC)
-        assert np.max(np.abs(np.array(r["M"]) - np.array(ref["M"]))) < TOL_M
-    assert counts[0] == counts[2] and counts[0] > counts[1]
+        res = sre.sre_exact_batched(states)
+        return res, sre.sre_kernel_launches() - k0
+    one = [torch.from_numpy(inputs.haar_state(N, 300 + N)).cuda() for N in range(1, 15)]
+    two = one + [torch.from_numpy(inputs.haar_state(N, 400 + N)).cuda() for N in range(1, 15)]
+    more = two + [torch.from_numpy(inputs.haar_state(15, 7)).cuda()] + \
+        [torch.from_numpy(inputs.t_product_state(N, N // 2)).cuda() for N in range(1, 15)]
+    r1, c1 = launches(one)
+    r2, c2 = launches(two)
+    r3, _ = launches(more)
+    _check(sre, two, r2)
+    _check(sre, more, r3)
+    for r, q in zip(r1, r2):
+        assert r["M"] == q["M"] and r["nullity"] == q["nullity"]
+    # per bucket 2 norm kernels, the totals, the FP64 recount of the flagged
+    # families (the x = 0 family of every state) and its scatter, plus the one
+    # persistent launch: the same for one state of each N as for two
+    assert c1 == c2
 
 
 def test_batched_small_vs_oracle(sre):
