@@ -772,9 +772,10 @@ def run_n30(a):
     """Large MC with Clifford preconditioning at N = 30 (8 GB state): a T-doped
     random Clifford circuit (eta = 16, n_T = 60: 960 Cliffords + 60 T) from
     |0>, then 2000 random {H, S, CNOT} gates, both applied on the device; then
-    the marginal MC, 16 z per x. A 256-family pilot gives the family count that
-    would bring the standard errors of M_1 and M_2 to 1e-3 (reported); the timed
-    step is one sre_mc call of that many families, at most --nx."""
+    the marginal MC, 16 z per x. r_2 is sampled (512 uniform x) before and
+    after the preconditioner; a 256-family pilot gives the family count that
+    brings the standard errors of M_1 and of M_2 to 1e-3 (reported apart); the
+    timed step is one sre_mc call of that many families, at most --nx."""
     import torch
     from paper_2601_00761_gb300 import build as sre_build
     sre_build.build()
@@ -787,16 +788,18 @@ def run_n30(a):
     circ = inputs.random_clifford_tdoped_gates(N, 960, 16, 30)
     pre = inputs.random_clifford_gates(N, 2000, 31)
     stream = torch.cuda.current_stream()
+    sre.apply_clifford_tdoped_circuit(psi, circ)
+    r2_before = sre.sre_mc(psi, sre.SRE_MC_UNIFORM, 512, 1, seed=41)["r2"]
     g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     g0.record(stream)
-    sre.apply_clifford_tdoped_circuit(psi, circ)
     sre.apply_clifford_tdoped_circuit(psi, pre)
     g1.record(stream)
     torch.cuda.synchronize()
     ms_gates = g0.elapsed_time(g1)
+    r2_after = sre.sre_mc(psi, sre.SRE_MC_UNIFORM, 512, 1, seed=41)["r2"]
     pilot = sre.sre_mc(psi, sre.SRE_MC_MARGINAL, 256, zpx, seed=30, counter0=1 << 40)
-    need = max(max(pilot["err_rb"][0], pilot["err_rb"][1]) / 1e-3, 1.0) ** 2 * 256
-    n_x = int(min(a.nx, max(256, 256 * math.ceil(need / 256))))    # the timed run stays within a minute
+    need = [max(pilot["err_rb"][k] / 1e-3, 1.0) ** 2 * 256 for k in (0, 1)]
+    n_x = int(min(a.nx, max(256, 256 * math.ceil(max(need) / 256))))    # the timed run stays within a minute
     for _ in range(a.warmup):
         sre.sre_mc(psi, sre.SRE_MC_MARGINAL, 32, zpx, seed=30, counter0=2 << 40)
     torch.cuda.synchronize()
@@ -823,12 +826,14 @@ def run_n30(a):
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded T-doped circuit eta=16, n_T=60, then 2000 random Clifford gates)",
             "config": {"workload": "N=30 T-doped state, 2000-gate Clifford preconditioner, marginal MC",
-                       "N": N, "n_x": n_x, "n_x_for_1e-3": int(math.ceil(need)), "z_per_x": zpx,
-                       "passes": plan["n_passes"],
+                       "N": N, "n_x": n_x, "n_x_for_1e-3": {"M1": int(math.ceil(need[0])), "M2_at_least": int(math.ceil(need[1]))},
+                       "z_per_x": zpx, "passes": plan["n_passes"],
                        "x_batch": plan["x_batch"], "gates": int(len(circ) + len(pre)), "ms_gates": ms_gates},
             "clocks": clk, "gpu_launches": int(launches),
+            "r2_sampled": {"before": r2_before, "after": r2_after, "uniform_x": 512},
             "estimates": {"M": r["M"], "err_M": r["err_M"], "M_rb": r["M_rb"], "err_rb": r["err_rb"],
-                          "pilot_err_rb": pilot["err_rb"]},
+                          "pilot_err_rb": pilot["err_rb"],
+                          "reached_1e-3": {"M1": r["err_rb"][0] <= 1e-3, "M2": r["err_rb"][1] <= 1e-3}},
             "tensor_core_form": {"precision": "split-BF16 x3", "n_x": 256,
                                  "value": 256 * 2.0 ** N / (ms_tc / 1e3), "M_rb": rtc["M_rb"], "err_rb": rtc["err_rb"]}}
     print(json.dumps(line), flush=True)
