@@ -89,6 +89,10 @@ typedef struct {
     int radix_log2;     /* bits of the last (contiguous) transform pass; 0 = planned/tuned */
     int tile_log2;      /* bits per strided pass; 0 = planned/tuned */
     int x_batch;        /* X-mask families in flight per launch; 0 = planned/tuned */
+    int batch_queue;    /* sre_exact_batched, FP32 only: 0 (default) = one persistent launch over the
+                           single-pass states (N <= 14), chunked launches for the others; 1 = every
+                           family of every state (N <= 20) in one persistent launch through a
+                           dependency queue with bounded waits; other values: SRE_EINVAL */
 } sre_opts;
 
 typedef struct {
@@ -326,6 +330,18 @@ SRE_API unsigned long long sre_device_allocations(void);
  * (about a second), SRE_OK if the wait completed (a broken barrier), or
  * SRE_ECUDA. Synchronises the stream. */
 SRE_API sre_status sre_selftest_bounded_wait(void *stream);
+
+/* Self-test of the bounded dependency waits of the persistent batched sweep
+ * (no counterpart in the paper). With sre_opts.batch_queue = 1,
+ * sre_exact_batched runs every family of every state as one queue of work
+ * items in one launch; an item that needs earlier items (the row pass of a
+ * family batch after its strided pass, a ring slot after its previous batch)
+ * waits on a device counter for at most about a second of the global timer,
+ * then raises SRE_ERR_TIMEOUT and an abort flag that ends the launch. This
+ * test launches one row item whose strided items never run, so its wait can
+ * only end by the bound: it returns SRE_ETIMEOUT (about a second) and leaves
+ * the context usable. Synchronises the stream. */
+SRE_API sre_status sre_selftest_queue_wait(void *stream);
 
 /* Pass timing inside sre_mc: enable = 1 clears the counters and starts
  * recording CUDA events around every full-batch family-transform pass launch

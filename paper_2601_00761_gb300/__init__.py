@@ -20,7 +20,7 @@ __all__ = ["sre_version", "sre_last_error", "sre_default_opts", "sre_make_plan",
            "sre_release_workspace", "sre_norm2", "sre_exact", "sre_exact_batched", "sre_mc",
            "pauli_x_marginal", "stabilizer_nullity", "apply_clifford_tdoped_circuit",
            "sre_family_spectrum", "sre_family_spectrum_f64", "sre_philox_blocks", "sre_kernel_launches", "sre_device_allocations", "sre_tc_gemm_selftest",
-           "sre_selftest_bounded_wait",
+           "sre_selftest_bounded_wait", "sre_selftest_queue_wait",
            "sre_profile_passes", "sre_pass_timing", "sre_exact_noalloc", "sre_autotune", "SreError",
            "SRE_FP32_SIMT", "SRE_BF16X2_TC", "SRE_BF16X3_TC", "SRE_MC_UNIFORM", "SRE_MC_MARGINAL",
            "lib_path", "load"]
@@ -44,7 +44,7 @@ class SreError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("eps_null", ctypes.c_double), ("radix_log2", ctypes.c_int),
-                ("tile_log2", ctypes.c_int), ("x_batch", ctypes.c_int)]
+                ("tile_log2", ctypes.c_int), ("x_batch", ctypes.c_int), ("batch_queue", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -125,6 +125,7 @@ def load():
         "sre_tc_gemm_selftest": ([_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp],
                                  st),
         "sre_selftest_bounded_wait": ([_vp], st),
+        "sre_selftest_queue_wait": ([_vp], st),
         "sre_autotune": ([_vp, ctypes.c_int, _vp, ctypes.POINTER(Opts)], st),
         "sre_exact_noalloc": ([_vp, ctypes.c_int, ctypes.POINTER(Opts), _vp, ctypes.POINTER(Result)], st),
         "sre_pass_timing": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
@@ -172,12 +173,13 @@ def _psi_ptr(psi, N=None):
     return ctypes.c_void_p(psi.data_ptr()), Nq
 
 
-def _opts(precision=SRE_FP32_SIMT, eps_null=1e-6, radix_log2=0, tile_log2=0, x_batch=0, opts=None):
+def _opts(precision=SRE_FP32_SIMT, eps_null=1e-6, radix_log2=0, tile_log2=0, x_batch=0, batch_queue=0, opts=None):
     if opts is not None:
         return opts
     o = Opts()
     load().sre_default_opts(ctypes.byref(o))
     o.precision, o.eps_null, o.radix_log2, o.tile_log2, o.x_batch = precision, eps_null, radix_log2, tile_log2, x_batch
+    o.batch_queue = batch_queue
     return o
 
 
@@ -373,6 +375,12 @@ def sre_philox_blocks(ctr_key):
     _check(load().sre_philox_blocks(ctypes.c_void_p(ctr_key.data_ptr()), ctypes.c_void_p(out.data_ptr()), n,
                                     _stream()))
     return out
+
+
+def sre_selftest_queue_wait() -> int:
+    """Run the persistent-queue wait self-test on the current stream; returns
+    the status (SRE_ETIMEOUT when the bound works)."""
+    return int(load().sre_selftest_queue_wait(_stream()))
 
 
 def sre_selftest_bounded_wait() -> int:

@@ -356,6 +356,7 @@ sre_status check_opts(const sre_opts *o, sre_opts &out) {
         return fail(SRE_EINVAL, "unknown precision %d", out.precision);
     if (out.x_batch < 0 || out.radix_log2 < 0 || out.tile_log2 < 0)
         return fail(SRE_EINVAL, "negative tiling option");
+    if (out.batch_queue != 0 && out.batch_queue != 1) return fail(SRE_EINVAL, "batch_queue must be 0 or 1");
     return SRE_OK;
 }
 
@@ -715,72 +716,156 @@ struct BatchWS {
     TilePartial *tiles;
     void *inter, *inter64;
     NullWS nw;
-    // the persistent launch over the single-pass buckets (k_batch.cu)
-    FamMoments *fm_all;                  // family sums of every state of those buckets, bucket by bucket
+    // the persistent launch (k_batch.cu)
+    FamMoments *fm_all;                  // family sums of every state it sweeps, bucket by bucket
     BatchBucket *pbuckets;
     BatchSeg *psegs;
     unsigned long long *next;
+    // with two-pass items (the dependency queue)
+    unsigned *need, *done;               // per global batch: [need_str, need_row], [done_str, done_row]
+    int *abort_flag, *err;
+    void *ring;
+    TilePartial *ring_tiles;
 };
 
-// The persistent launch's work layout, built on the host (k_batch.cuh): the
-// families of every single-pass bucket (N <= PERSIST_NMAX), one segment per
-// bucket, G families per item (the tile's groups). Two-pass buckets keep the
-// chunked launch sequence (batch_main).
-constexpr int PERSIST_NMAX = 14;
+// The persistent launch's work layout, built on the host (k_batch.cuh). By
+// default it holds the families of every single-pass FP32 bucket (N <= 14),
+// one segment per bucket, G families per item (the tile's groups), and the
+// two-pass buckets keep the chunked launch sequence (batch_main). With
+// sre_opts.batch_queue it holds every bucket: the two-pass ones (N = 15 .. 20)
+// as batches of strided items (a pass of N - 14 rows) and row items (13-bit
+// rows with the fused moments) through an intermediate ring, in dependency
+// order.
+constexpr int PERSIST_SINGLE_NMAX = 14;
+constexpr int PERSIST_NMAX = 20;
+constexpr int PERSIST_AHEAD = 1;                      // strided batches issued ahead of a batch's row items
+constexpr int PERSIST_RING = PERSIST_AHEAD + 2;       // intermediate ring slots
+constexpr size_t PERSIST_SLOT_BYTES = 1ull << 30;    // intermediate bytes per ring slot (4096 families at N = 16)
+constexpr int PERSIST_FPC = 8;                        // families per strided item
+constexpr int PERSIST_RPI = 2;                        // families per row item
 
 struct PersistLayout {
-    std::vector<BatchBucket> buckets;
+    bool dep = false;                                 // two-pass items queued
+    std::vector<BatchBucket> buckets;                 // one per bucket of the batch (unused when not swept)
     std::vector<BatchSeg> segs;
-    std::vector<int> of;                // B index of every persistent bucket
-    std::vector<size_t> fm_off;         // its first family in fm_all
+    std::vector<size_t> fm_off;                       // first family of each bucket in fm_all
+    std::vector<unsigned> need_str, need_row;         // per global batch
     long long n_items = 0;
-    size_t fm_total = 0;
+    int batches = 0;
+    size_t fm_total = 0, tiles_slot = 0;
 };
 
-bool persist_bucket(const BucketPlan &b, int prec) {
-    return prec == 0 && b.N <= PERSIST_NMAX && b.P.npass == 1;
+// Whether the persistent launch sweeps bucket b (all: the dependency queue).
+bool persist_bucket(const BucketPlan &b, int prec, bool all) {
+    if (prec != 0) return false;
+    if (all) return b.N <= PERSIST_NMAX;
+    return b.N <= PERSIST_SINGLE_NMAX && b.P.npass == 1;
 }
 
-void persist_plan(const std::vector<BucketPlan> &B, int prec, PersistLayout &L) {
+long long persist_batch_families(int N) {
+    const long long slot = 8LL << (N - 1);            // complex FP32 intermediate per family
+    return std::max(1LL, (long long)PERSIST_SLOT_BYTES / slot);
+}
+
+// Segments in dependency order: two-pass buckets first (largest N first), each
+// batch's strided items before the previous batch's row items; then the
+// single-pass buckets. Marks the swept buckets (BucketPlan::persistent).
+void persist_plan(std::vector<BucketPlan> &B, int prec, bool all, PersistLayout &L) {
     L = PersistLayout();
+    L.buckets.resize(B.size());
+    L.fm_off.assign(B.size(), 0);
     for (size_t bi = 0; bi < B.size(); ++bi) {
-        if (!persist_bucket(B[bi], prec)) continue;
-        const int M = B[bi].N - 1;
-        const int RB = M < 5 ? M : 5, TB = M - RB, G = TB >= 8 ? 1 : (256 >> TB);
-        const long long fams = (long long)B[bi].idx.size() << B[bi].N;
+        B[bi].persistent = persist_bucket(B[bi], prec, all);
+        if (!B[bi].persistent) continue;
+        L.fm_off[bi] = L.fm_total;
+        L.fm_total += (size_t)B[bi].idx.size() << B[bi].N;
+    }
+    auto push = [&](int kind, int bucket, int batch, int aux, long long count) {
+        if (count <= 0) return;
         BatchSeg g;
-        g.bucket = (int)L.buckets.size();
-        g.per_cta = G;
-        g.start = L.n_items;
-        g.count = (fams + G - 1) / G;
+        g.kind = kind; g.bucket = bucket; g.batch = batch; g.aux = aux; g.start = L.n_items; g.count = count;
         L.segs.push_back(g);
-        L.n_items += g.count;
-        L.buckets.push_back(BatchBucket());
-        L.of.push_back((int)bi);
-        L.fm_off.push_back(L.fm_total);
-        L.fm_total += (size_t)fams;
+        L.n_items += count;
+    };
+    // a batch's row items follow the strided items of the PERSIST_AHEAD
+    // batches after it, so that they rarely wait
+    struct RowSeg { int bucket, batch; long long nf; };
+    std::vector<RowSeg> pending;
+    for (size_t bi = 0; bi < B.size(); ++bi) {
+        const int N = B[bi].N;
+        if (!B[bi].persistent || N <= PERSIST_SINGLE_NMAX) continue;
+        L.dep = true;
+        const long long fams = (long long)B[bi].idx.size() << N;
+        const long long Bf = persist_batch_families(N);
+        const int tiles = 1 << (N - 1 - 13);
+        L.buckets[bi].first_batch = L.batches;
+        L.tiles_slot = std::max(L.tiles_slot, (size_t)(Bf * tiles));
+        for (long long fb = 0; fb < fams; fb += Bf) {
+            const long long nf = std::min(Bf, fams - fb);
+            const int groups = (int)((nf + PERSIST_FPC - 1) / PERSIST_FPC);
+            const int k = L.batches++;
+            push(BI_STRIDED, (int)bi, k, groups, (long long)tiles * groups);
+            pending.push_back({(int)bi, k, nf});
+            if ((int)pending.size() > PERSIST_AHEAD) {
+                push(BI_ROW, pending.front().bucket, pending.front().batch, PERSIST_RPI,
+                     (pending.front().nf + PERSIST_RPI - 1) / PERSIST_RPI);
+                pending.erase(pending.begin());
+            }
+            L.need_str.push_back((unsigned)((long long)tiles * groups));
+            L.need_row.push_back((unsigned)nf);
+        }
+    }
+    for (const RowSeg &r : pending) push(BI_ROW, r.bucket, r.batch, PERSIST_RPI, (r.nf + PERSIST_RPI - 1) / PERSIST_RPI);
+    for (size_t bi = 0; bi < B.size(); ++bi) {
+        const int N = B[bi].N;
+        if (!B[bi].persistent || N > PERSIST_SINGLE_NMAX) continue;
+        const int M = N - 1;
+        const int RB = M < 5 ? M : 5, TB = M - RB, G = TB >= 8 ? 1 : (256 >> TB);
+        const long long fams = (long long)B[bi].idx.size() << N;
+        push(BI_SINGLE, (int)bi, 0, G, (fams + G - 1) / G);
     }
 }
 
 // Device tables of the layout, pointing into the workspace.
 void persist_tables(const std::vector<BucketPlan> &B, const BatchWS &w, float cand_thr, PersistLayout &L) {
-    for (size_t k = 0; k < L.buckets.size(); ++k) {
-        const BucketPlan &b = B[L.of[k]];
+    for (size_t bi = 0; bi < B.size(); ++bi) {
+        const BucketPlan &b = B[bi];
+        BatchBucket &k = L.buckets[bi];
+        const int first_batch = k.first_batch;          // set by persist_plan
+        memset(&k, 0, sizeof k);
+        if (!b.persistent) continue;
+        const int N = b.N;
+        const long long fams = (long long)b.idx.size() << N;
         PassArgs a;
         memset(&a, 0, sizeof a);
-        a.N = b.N;
-        a.n = b.N - 1;
-        a.slot_elems = 1LL << (b.N - 1);
+        a.N = N;
+        a.n = N - 1;
+        a.slot_elems = 1LL << (N - 1);
         a.cand_thr = cand_thr;
         a.want_cand = 1;
         a.psi_list = w.psi_list + b.off;
         a.s_list = w.s_list + b.off;
         a.s_ptr = w.s_list + b.off;
-        a.fam_base = 0;
-        a.n_fam = (long long)b.idx.size() << b.N;
-        a.fam_out = w.fm_all + L.fm_off[k];
-        L.buckets[k].single = a;
-        L.buckets[k].M = b.N - 1;
+        k.fm = w.fm_all + L.fm_off[bi];
+        k.fam_total = fams;
+        if (N > PERSIST_SINGLE_NMAX) {
+            k.M = 13;
+            k.K = N - 14;
+            k.B = persist_batch_families(N);
+            k.tiles_row = 1 << (N - 1 - 13);
+            k.first_batch = first_batch;
+            k.strided = a;
+            k.strided.lo_g = 13;                // the strided rows are the packed bits 13 .. N - 2
+            k.row = a;
+            k.row.lo_g = 0;
+        } else {
+            k.M = N - 1;
+            k.tiles_row = 1;
+            k.single = a;
+            k.single.fam_base = 0;
+            k.single.n_fam = fams;
+            k.single.fam_out = k.fm;
+        }
     }
 }
 
@@ -802,8 +887,8 @@ struct BatchGraph {
 // change them for the same batch shape).
 std::vector<long long> plan_signature(const std::vector<BucketPlan> &B) {
     std::vector<long long> v;
-    v.push_back(PERSIST_NMAX);
     for (const BucketPlan &b : B) {
+        v.push_back(b.persistent ? 1 : 0);
         v.insert(v.end(), {(long long)b.N, (long long)b.P.npass, (long long)b.P.M_last, b.P.B, b.P.tiles_last,
                            (long long)b.states_per_chunk});
         for (int i = 0; i < b.P.nstrided; ++i) v.insert(v.end(), {(long long)b.P.K[i], (long long)b.P.lo[i]});
@@ -828,7 +913,10 @@ void layout_batch(Arena &A, int count, std::vector<BucketPlan> &B, BatchWS &w, c
         b.flag_cap = fams;
         counts_n = std::max(counts_n, (size_t)fams);
         if (b.persistent) {
-            // the FP64 recount still runs through the chunked buffers
+            // the nullity recount of the flagged families still runs through
+            // the chunked intermediates (its FP32 candidate pass and the FP64
+            // transform)
+            if (b.P.npass > 1) inter_b = std::max(inter_b, b.P.slot_bytes * (size_t)b.P.B);
             if (b.P64.npass > 1) inter64_b = std::max(inter64_b, b.P64.slot_bytes * (size_t)b.P64.B);
             continue;
         }
@@ -847,16 +935,27 @@ void layout_batch(Arena &A, int count, std::vector<BucketPlan> &B, BatchWS &w, c
     w.inter = inter_b ? (void *)A.take<char>(inter_b) : nullptr;
     w.inter64 = inter64_b ? (void *)A.take<char>(inter64_b) : nullptr;
     w.counts = A.take<unsigned long long>(counts_n);
+    w.fm_all = nullptr;
+    w.pbuckets = nullptr;
+    w.psegs = nullptr;
+    w.next = nullptr;
+    w.need = w.done = nullptr;
+    w.abort_flag = w.err = nullptr;
+    w.ring = nullptr;
+    w.ring_tiles = nullptr;
     if (L && L->n_items) {
         w.fm_all = A.take<FamMoments>(L->fm_total);
         w.pbuckets = A.take<BatchBucket>(L->buckets.size());
         w.psegs = A.take<BatchSeg>(L->segs.size());
         w.next = A.take<unsigned long long>(1);
-    } else {
-        w.fm_all = nullptr;
-        w.pbuckets = nullptr;
-        w.psegs = nullptr;
-        w.next = nullptr;
+        if (L->dep) {
+            w.need = A.take<unsigned>(2 * (size_t)L->batches + 2);
+            w.done = A.take<unsigned>(2 * (size_t)L->batches + 2);
+            w.abort_flag = A.take<int>(1);
+            w.err = A.take<int>(1);
+            w.ring = (void *)A.take<char>((size_t)PERSIST_RING * PERSIST_SLOT_BYTES);
+            w.ring_tiles = A.take<TilePartial>((size_t)PERSIST_RING * L->tiles_slot + 1);
+        }
     }
     layout_null(A, (long long)counts_n, w.nw);
     w.nw.counts = w.counts;
@@ -876,8 +975,8 @@ int sm_count() {
 }
 
 // The main launch sequence (captured into the graph): per-bucket norms, one
-// persistent launch over every family of the single-pass buckets (k_batch.cu)
-// with their per-state totals, then every two-pass bucket chunk by chunk. The
+// persistent launch over every family of the buckets it sweeps (k_batch.cu)
+// with their per-state totals, then every other bucket chunk by chunk. The
 // tables the persistent launch reads (L) are uploaded before every run.
 sre_status batch_main(const std::vector<BucketPlan> &B, const BatchWS &w, const PersistLayout &L, int count, int prec,
                       float cand_thr, cudaStream_t st) {
@@ -892,17 +991,35 @@ sre_status batch_main(const std::vector<BucketPlan> &B, const BatchWS &w, const 
     if (L.n_items > 0) {
         CK(cudaMemsetAsync(w.next, 0, sizeof(unsigned long long), st));
         BatchQueue q;
+        memset(&q, 0, sizeof q);
         q.segs = w.psegs;
         q.n_segs = (int)L.segs.size();
         q.n_items = L.n_items;
         q.buckets = w.pbuckets;
         q.next = w.next;
-        CK(launch_batch_persistent(q, 2 * sm_count(), st));
+        if (L.dep) {
+            CK(cudaMemsetAsync(w.done, 0, sizeof(unsigned) * (2 * (size_t)L.batches + 2), st));
+            CK(cudaMemsetAsync(w.abort_flag, 0, sizeof(int), st));
+            CK(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+            q.done_str = w.done;
+            q.done_row = w.done + L.batches;
+            q.need_str = w.need;
+            q.need_row = w.need + L.batches;
+            q.inter = w.ring;
+            q.inter_slot_bytes = PERSIST_SLOT_BYTES;
+            q.tiles = w.ring_tiles;
+            q.tiles_slot = L.tiles_slot;
+            q.ring = PERSIST_RING;
+            q.fpc = PERSIST_FPC;
+            q.err = w.err;
+            q.abort_flag = w.abort_flag;
+        }
+        CK(launch_batch_persistent(q, L.dep, 2 * sm_count(), st));
         count_launches(1);
-        for (size_t k = 0; k < L.buckets.size(); ++k) {
-            const int bi = L.of[k];
+        for (size_t bi = 0; bi < B.size(); ++bi) {
             const BucketPlan &b = B[bi];
-            CK(launch_state_totals(w.fm_all + L.fm_off[k], 0, b.N, 0, (int)b.idx.size(),
+            if (!b.persistent) continue;
+            CK(launch_state_totals(w.fm_all + L.fm_off[bi], 0, b.N, 0, (int)b.idx.size(),
                                    w.totals + TOT_N * (size_t)b.off, b.flags, w.nflag + bi, st));
             count_launches(1);
         }
@@ -959,13 +1076,14 @@ sre_status batched_impl(const void *const *psi_ptrs, const int *Ns, int count, c
             b.states_per_chunk = (int)std::max(1LL, BATCH_CHUNK_FAMILIES >> N);
             b.flags = nullptr;
             b.flag_cap = 0;
-            b.persistent = persist_bucket(b, prec_code(o));
+            b.persistent = false;
             B.push_back(b);
         }
     }
     // one persistent launch over the single-pass buckets of the FP32 sweep
+    // (with opts.batch_queue: over every bucket)
     PersistLayout L;
-    persist_plan(B, prec_code(o), L);
+    persist_plan(B, prec_code(o), o.batch_queue != 0, L);
     Arena dry(nullptr);
     BatchWS w;
     layout_batch(dry, count, B, w, &L);
@@ -977,6 +1095,11 @@ sre_status batched_impl(const void *const *psi_ptrs, const int *Ns, int count, c
         persist_tables(B, w, cand_threshold(o.eps_null), L);
         CK(cudaMemcpyAsync(w.pbuckets, L.buckets.data(), sizeof(BatchBucket) * L.buckets.size(), cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(w.psegs, L.segs.data(), sizeof(BatchSeg) * L.segs.size(), cudaMemcpyHostToDevice, st));
+        if (L.dep) {
+            CK(cudaMemcpyAsync(w.need, L.need_str.data(), sizeof(unsigned) * L.batches, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(w.need + L.batches, L.need_row.data(), sizeof(unsigned) * L.batches,
+                               cudaMemcpyHostToDevice, st));
+        }
     }
 
     // psi pointers in slot (bucket) order
@@ -1035,7 +1158,10 @@ sre_status batched_impl(const void *const *psi_ptrs, const int *Ns, int count, c
 
     std::vector<unsigned long long> nflag(B.size());
     CK(cudaMemcpyAsync(nflag.data(), w.nflag, sizeof(unsigned long long) * B.size(), cudaMemcpyDeviceToHost, st));
+    int perr = 0;
+    if (L.dep) CK(cudaMemcpyAsync(&perr, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (perr & SRE_ERR_TIMEOUT) return fail(SRE_ETIMEOUT, "a bounded wait of the persistent batched sweep expired");
 
     // FP64 recount of the candidate families, per bucket
     for (size_t bi = 0; bi < B.size(); ++bi) {
@@ -1814,6 +1940,61 @@ unsigned long long sre_device_allocations(void) { return g_allocs.load(); }
 
 // 16 source bytes and the error word of the bounded-wait self-test
 __device__ __align__(16) int g_selftest_words[8];
+
+sre_status sre_selftest_queue_wait(void *stream) {
+    // one row item whose strided items never run: its dependency wait can
+    // only end by its bound
+    cudaStream_t st = (cudaStream_t)stream;
+    Arena dry(nullptr);
+    auto lay = [](Arena &A, BatchBucket *&bk, BatchSeg *&sg, unsigned *&u, unsigned long long *&nx, int *&fl) {
+        bk = A.take<BatchBucket>(1);
+        sg = A.take<BatchSeg>(1);
+        u = A.take<unsigned>(8);
+        nx = A.take<unsigned long long>(1);
+        fl = A.take<int>(2);
+    };
+    BatchBucket *bk;
+    BatchSeg *sg;
+    unsigned *u;
+    unsigned long long *nx;
+    int *fl;
+    lay(dry, bk, sg, u, nx, fl);
+    void *base = nullptr;
+    CS(own_workspace(dry.off, &base));
+    Arena A(base);
+    lay(A, bk, sg, u, nx, fl);
+    CK(cudaMemsetAsync(base, 0, dry.off, st));
+    BatchSeg h;
+    memset(&h, 0, sizeof h);
+    h.kind = BI_ROW;
+    h.aux = 1;
+    h.count = 1;
+    const unsigned need[2] = {1u, 1u};      // need_str[0] = 1 with no strided item
+    CK(cudaMemcpyAsync(sg, &h, sizeof h, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(u, need, sizeof need, cudaMemcpyHostToDevice, st));
+    BatchQueue q;
+    memset(&q, 0, sizeof q);
+    q.segs = sg;
+    q.n_segs = 1;
+    q.n_items = 1;
+    q.buckets = bk;
+    q.next = nx;
+    q.need_str = u;
+    q.need_row = u + 1;
+    q.done_str = u + 2;
+    q.done_row = u + 3;
+    q.ring = PERSIST_RING;
+    q.fpc = PERSIST_FPC;
+    q.err = fl;
+    q.abort_flag = fl + 1;
+    CK(launch_batch_persistent(q, true, 1, st));
+    count_launches(1);
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, fl, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (err & SRE_ERR_TIMEOUT) return fail(SRE_ETIMEOUT, "queue dependency wait expired (self-test: expected)");
+    return SRE_OK;
+}
 
 sre_status sre_selftest_bounded_wait(void *stream) {
     cudaStream_t st = (cudaStream_t)stream;

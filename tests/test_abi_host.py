@@ -108,6 +108,8 @@ def test_argument_errors_do_not_touch_the_gpu(L):
     assert L.sre_exact(_fake_ptr(0x1000), 10, ctypes.byref(bad), None, 0, None, ctypes.byref(r)) == sre.SRE_EINVAL
     neg = sre.Opts(0, 1e-6, 0, 0, -1)
     assert L.sre_exact(_fake_ptr(0x1000), 10, ctypes.byref(neg), None, 0, None, ctypes.byref(r)) == sre.SRE_EINVAL
+    queue = sre.Opts(0, 1e-6, 0, 0, 0, 2)     # batch_queue is 0 or 1
+    assert L.sre_exact(_fake_ptr(0x1000), 10, ctypes.byref(queue), None, 0, None, ctypes.byref(r)) == sre.SRE_EINVAL
     for eps in (0.5, 2.0, float("nan")):     # nullity tolerance outside (0, 0.5)
         wide = sre.Opts(0, eps, 0, 0, 0)
         assert L.sre_exact(_fake_ptr(0x1000), 10, ctypes.byref(wide), None, 0, None, ctypes.byref(r)) == sre.SRE_EINVAL
@@ -150,6 +152,7 @@ def test_mixed_workspace_bytes(L):
 def test_structs_match_header_layout():
     # sre_gate is a packed 3-byte row; sre_opts / sre_result field order as declared
     assert ctypes.sizeof(sre.Gate) == 3
+    assert sre.Opts.eps_null.offset == 8 and sre.Opts.batch_queue.offset == 28 and ctypes.sizeof(sre.Opts) == 32
     assert sre.Result.M.offset == 0 and sre.Result.parseval.offset == 15 * 8
     assert sre.Result.stab_count.offset == 16 * 8
     assert sre.Result.r2.offset == 22 * 8 and ctypes.sizeof(sre.Result) == 23 * 8

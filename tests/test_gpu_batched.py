@@ -45,6 +45,26 @@ def test_batched_uneven_matches_per_state(sre):
     res = sre.sre_exact_batched(states)
     _check(sre, states, res)
     assert res[-2]["nullity"] == 5 and abs(res[-2]["M"][1] - 5 * np.log2(4 / 3)) < TOL_M
+    # the same batch with every family in one persistent launch (dependency queue)
+    resq = sre.sre_exact_batched(states, batch_queue=1)
+    _check(sre, states, resq)
+
+
+def test_batched_queue_mode_has_its_own_graph(sre):
+    """The dependency-queue mode (batch_queue=1) sweeps the two-pass states in
+    the persistent launch too, so its launch sequence is shorter; the cached
+    graphs of the two modes for the same batch shape stay apart."""
+    states = [torch.from_numpy(inputs.haar_state(N, 500 + N)).cuda() for N in (10, 15, 16, 16)]
+    counts, results = [], []
+    for q in (0, 1, 0, 1):
+        k0 = sre.sre_kernel_launches()
+        results.append(sre.sre_exact_batched(states, batch_queue=q))
+        counts.append(sre.sre_kernel_launches() - k0)
+    assert counts[0] == counts[2] and counts[1] == counts[3] and counts[1] < counts[0]
+    for a, b in zip(results[0], results[1]):
+        assert np.max(np.abs(np.array(a["M"]) - np.array(b["M"]))) < TOL_M and a["nullity"] == b["nullity"]
+    for a, b in zip(results[1], results[3]):
+        assert a["M"] == b["M"]
 
 
 def test_batched_graph_replay_with_new_states(sre):

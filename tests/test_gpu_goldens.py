@@ -100,3 +100,7 @@ def test_batched_vs_oracle_golden(sre):
     res = sre.sre_exact_batched(mixed)
     for k, rec in zip(where, recs):
         _agree(res[k], rec)
+    # every family of every state in one persistent launch (dependency queue)
+    res = sre.sre_exact_batched(mixed, batch_queue=1)
+    for k, rec in zip(where, recs):
+        _agree(res[k], rec)
