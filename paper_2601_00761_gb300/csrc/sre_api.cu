@@ -47,6 +47,12 @@ sre_status fail(sre_status st, const char *fmt, ...) {
     } while (0)
 
 constexpr size_t BATCH_BYTES = 8ULL << 30;   // intermediate budget per launch sequence
+// FP32 states whose families exceed a quarter of that budget (N >= 29) still
+// take BATCH_MIN_LARGE families per launch, within BATCH_BYTES_LARGE: the
+// families of a launch share psi's reads (N = 30 MC: 5.81 ms per family at 2
+// per launch, 4.94 at 8, 4.87 at 16)
+constexpr long long BATCH_MIN_LARGE = 8;
+constexpr size_t BATCH_BYTES_LARGE = 32ULL << 30;
 
 // kernels issued by this library since load (all entry points)
 std::atomic<unsigned long long> g_launches{0};
@@ -182,6 +188,8 @@ sre_status plan_for(int N, const sre_opts *o, int prec, Plan &P) {
     P.tiles_last = 1LL << (P.n - nlo);
     P.slot_bytes = (size_t)(prec == 32 ? 8 : 16) << P.n;
     long long B = (long long)(BATCH_BYTES / P.slot_bytes);
+    if (prec == 32 && B < BATCH_MIN_LARGE)
+        B = std::min(BATCH_MIN_LARGE, (long long)(BATCH_BYTES_LARGE / P.slot_bytes));
     if (B < 1) B = 1;
     if (B > 4096) B = 4096;
     if (prec == 32 && o && o->x_batch > 0) B = o->x_batch;

@@ -72,6 +72,13 @@ def test_plan_options(L):
     p = sre.sre_make_plan(16, radix_log2=10, tile_log2=2)
     assert p["pass_bits"] == [2, 3, 10]
     assert sre.sre_make_plan(24, x_batch=3)["x_batch"] == 3
+    # batches stay within 8 GiB of FP32 intermediate, except that states of
+    # N >= 29 still take 8 families per launch within 32 GiB
+    assert sre.sre_make_plan(24)["x_batch"] == 128
+    assert sre.sre_make_plan(28)["x_batch"] == 8
+    assert sre.sre_make_plan(30)["x_batch"] == 8
+    assert sre.sre_make_plan(31)["x_batch"] == 4
+    assert sre.sre_make_plan(32)["x_batch"] == 2
 
 
 def test_workspace_sizes(L):
