@@ -448,6 +448,46 @@ def test_mc_n24_full_size_sampled(sre):
     assert abs(r["M"][1] - m2_haar) < 5 * r["err_M"][1] + 1e-3
 
 
+def test_mc_n24_bench_launch_configuration(sre):
+    """The benchmark's own configuration: N = 24 Haar (seed 24), 4096 x from
+    p(x), 256 z per x, the default plan (128 families per launch, 32 launches
+    in the sorted x order). Sampled outputs from the first, a middle and the
+    last launch against the oracle: x draws bit-exact, z draws within the
+    propagated bound, sampled c against the direct sum; the estimate against
+    the Haar closed form."""
+    N = 24
+    psi = inputs.haar_state(N, 24)
+    assert sre.sre_make_plan(N)["x_batch"] == 128
+    n_x, zpx = 4096, 256
+    r = sre.sre_mc(dev(psi), sre.SRE_MC_MARGINAL, n_x, zpx, seed=24, return_samples=True)
+    xs = r["xs"].cpu().numpy().astype(np.uint64)
+    zs = r["zs"].cpu().numpy().astype(np.uint64)
+    c = r["c"].cpu().numpy()
+    p = oracle.x_marginal(psi)
+    p[0] = 0.0
+    assert xs[0] == 0
+    for i in list(range(1, 40)) + list(range(2040, 2060)) + list(range(4070, 4096)):
+        assert int(xs[i]) == oracle.inverse_cdf(p, oracle.mc_draw(24, 0, i, 0)), i
+    rl = sre.sre_make_plan(N)["range_log2"]
+    n_exact = n_total = 0
+    for i in (3, 2049, 4095):
+        x = int(xs[i])
+        cf = oracle.family_spectrum(psi, x)
+        cg = sre.sre_family_spectrum(dev(psi), x).cpu().numpy().astype(np.float64)
+        for k in range(0, zpx, 8):
+            u = oracle.mc_draw(24, 0, i, 1 + k)
+            zo = oracle.inverse_cdf(cf * cf, u)
+            ok, exact = draw_within_bound(int(zs[i, k]), zo, cf * cf, cg * cg, u, rl)
+            assert ok, (i, k, int(zs[i, k]), zo)
+            n_exact += exact
+            n_total += 1
+        for k in (0, 101, 255):
+            assert abs(c[i, k] - oracle.pauli_expectation(psi, x, int(zs[i, k]))) < TOL_C
+    assert n_exact >= 0.85 * n_total
+    m2_haar = math.log2(2**N + 3) - 2
+    assert abs(r["M_rb"][1] - m2_haar) < 4 * r["err_rb"][1] + 1e-4
+
+
 @pytest.mark.parametrize("k_low", [16, 12, 8])
 def test_mc_marginal_fine_ranges(sre, k_low):
     """Multi-pass plan (N=16: a 13-bit last pass, z-ranges of 2^10): a Haar
