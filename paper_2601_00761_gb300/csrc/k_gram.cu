@@ -27,6 +27,7 @@
 //    summed in FP64 per entry.
 #include "k_tc05.cuh"
 #include "sre_internal.cuh"
+#include "k_fp64.cuh"
 
 #include <cuda_bf16.h>
 
@@ -277,20 +278,24 @@ __global__ void __launch_bounds__(256) gram_simt_kernel(const float2 *psi, int N
 // dominate the moments of a strongly mixed rho_A; the tensor cores' FP32
 // accumulation leaves them about 1e-6 off, summed in FP64 they carry only
 // the final FP32 rounding.
-__global__ void __launch_bounds__(256) gram_diag_kernel(const float2 *psi, int NA, int NB, float2 *C) {
+constexpr int GRAM_DIAG_WARPS = 32;
+__global__ void __launch_bounds__(32 * GRAM_DIAG_WARPS) gram_diag_kernel(const float2 *psi, int NA, int NB, float2 *C) {
     // one block per 32 consecutive a (coalesced 256-byte rows of Psi); warp
-    // w sums e = w, w + 8, ...; the eight partial sums are added in a fixed
-    // order, so the result does not depend on scheduling
-    __shared__ double part[8][32];
+    // w sums e = w, w + 32, ... (exact FP64 squares, widened in integer
+    // operations); the partial sums are added in a fixed order, so the result
+    // does not depend on scheduling
+    __shared__ double part[GRAM_DIAG_WARPS][32];
     const unsigned long long dA = 1ULL << NA, dB = 1ULL << NB;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned long long a = (unsigned long long)blockIdx.x * 32 + lane;
     double acc = 0.0;
     if (a < dA) {
 #pragma unroll 4
-        for (unsigned long long e = (unsigned long long)w; e < dB; e += 8) {
+        for (unsigned long long e = (unsigned long long)w; e < dB; e += GRAM_DIAG_WARPS) {
             const float2 v = psi[a + dA * e];
-            acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+            const double vx = f2d(v.x), vy = f2d(v.y);
+            acc = fma(vx, vx, acc);
+            acc = fma(vy, vy, acc);
         }
     }
     part[w][lane] = acc;
@@ -298,7 +303,7 @@ __global__ void __launch_bounds__(256) gram_diag_kernel(const float2 *psi, int N
     if (w == 0 && a < dA) {
         double t = 0.0;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) t += part[i][lane];
+        for (int i = 0; i < GRAM_DIAG_WARPS; ++i) t += part[i][lane];
         C[a + dA * a] = make_float2((float)t, 0.0f);
     }
 }
@@ -347,7 +352,7 @@ cudaError_t launch_gram(const float2 *psi, int N, int NA, float2 *C, void *plane
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    gram_diag_kernel<<<(unsigned)((dA + 31) / 32), 256, 0, st>>>(psi, NA, NB, C);
+    gram_diag_kernel<<<(unsigned)((dA + 31) / 32), 32 * GRAM_DIAG_WARPS, 0, st>>>(psi, NA, NB, C);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -2,6 +2,7 @@
 // the two-level z sampler and the MC statistics.
 #include "k_misc.cuh"
 #include "k_pass_dispatch.cuh"
+#include "k_fp64.cuh"
 
 namespace sre {
 
@@ -60,8 +61,9 @@ __global__ void __launch_bounds__(256) norm2_partial_kernel(const float2 *psi, u
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; b < d; b += stride) {
         const float2 u = __ldg(psi + b);
-        acc = fma((double)u.x, (double)u.x, acc);
-        acc = fma((double)u.y, (double)u.y, acc);
+        const double ux = f2d(u.x), uy = f2d(u.y);
+        acc = fma(ux, ux, acc);
+        acc = fma(uy, uy, acc);
     }
     acc = block_sum<256>(acc, red);
     if (threadIdx.x == 0) partial[blockIdx.x] = acc;
@@ -540,8 +542,9 @@ __global__ void __launch_bounds__(256) norm2_multi_partial(const float2 *const *
     const unsigned long long stride = (unsigned long long)nb * blockDim.x;
     for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; b < d; b += stride) {
         const float2 u = __ldg(psi + b);
-        acc = fma((double)u.x, (double)u.x, acc);
-        acc = fma((double)u.y, (double)u.y, acc);
+        const double ux = f2d(u.x), uy = f2d(u.y);
+        acc = fma(ux, ux, acc);
+        acc = fma(uy, uy, acc);
     }
     acc = block_sum<256>(acc, red);
     if (threadIdx.x == 0) partial[(size_t)st * nb + blockIdx.x] = acc;

@@ -23,6 +23,7 @@
 // Points of a coset that were not listed lie below the threshold and count
 // nothing, so every route counts exactly the FP64 decisions.
 #include "k_misc.cuh"
+#include "k_fp64.cuh"
 
 namespace sre {
 
@@ -36,17 +37,6 @@ constexpr int NB_MAXBITS = 6;    // span dimension up to which the coset route i
 // v with its sign bit flipped when sgn = 1u << 31
 __device__ __forceinline__ double flip(double v, unsigned sgn) {
     return __hiloint2double(__double2hiint(v) ^ (int)sgn, __double2loint(v));
-}
-
-// binary32 -> binary64 by re-packing the fields (exact: every float is a
-// double). Normal numbers and zeros in integer operations; subnormals, inf
-// and NaN, rare here, by the conversion instruction.
-__device__ __forceinline__ double f2d(float f) {
-    const unsigned u = __float_as_uint(f);
-    const unsigned e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu, sg = u & 0x80000000u;
-    if (e == 0u && m == 0u) return __hiloint2double((int)sg, 0);
-    if (e - 1u >= 254u) return (double)f;
-    return __hiloint2double((int)(sg | ((e + 896u) << 20) | (m >> 3)), (int)(m << 29));
 }
 
 // h(g) in FP64 (exact products of the FP32 amplitudes, one rounding per sum)
