@@ -351,9 +351,9 @@ __device__ __forceinline__ void fine_range_weights(float2 s2, unsigned long long
 __host__ __device__ constexpr bool ranges_accumulate(int E) { return (1 << ZR_FINE) / E > 32; }
 
 // Families a CTA of a psi-reading strided pass transforms in turn, on the
-// same tile. Neighbouring families in the sorted order share their own-half
-// rows, so the later ones find them in L1 (N = 24: 2.79 ms per 128-family
-// launch with 4, 2.83 with 2, 2.97 with 1; 8 gains nothing over 4).
+// same tile: fewer, longer CTAs (their L1 hit rate stays near zero; N = 24:
+// 2.79 ms per 128-family launch with 4 families per CTA, 2.83 with 2, 2.97
+// with 1; 8 gains nothing over 4).
 #ifndef SRE_STRIDED_FPC
 #define SRE_STRIDED_FPC 4
 #endif
