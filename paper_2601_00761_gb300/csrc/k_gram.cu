@@ -84,6 +84,11 @@ constexpr int GRAM_NS = 4;                     // stages in the ring
 constexpr int GRAM_EPI = 256;                  // epilogue threads (8 warps)
 constexpr int GRAM_THREADS = GRAM_EPI + 32;    // + one warp issuing TMA and MMA
 constexpr size_t GRAM_SMEM = 1024 + GRAM_NS * (size_t)GRAM_STAGE + 256;
+// K blocks accumulated in one TMEM buffer before the epilogue warps drain it
+#ifndef SRE_GRAM_R
+#define SRE_GRAM_R 1
+#endif
+constexpr int GRAM_R = SRE_GRAM_R;
 
 // tile index -> (I, J) with I <= J over nt x nt tiles (row-major upper triangle)
 __device__ __forceinline__ void tri_tile(int idx, int nt, int &I, int &J) {
@@ -163,9 +168,13 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) gram_tc_kernel(const __grid_c
             bool ok = true;
             for (int kb = 0; kb < nk && kb < GRAM_NS; ++kb) load_stage(kb, kb);
             for (int kb = 0; kb < nk && ok; ++kb) {
-                const int s = kb % GRAM_NS, b = kb & 1;
+                // K block kb goes into TMEM buffer b of accumulation group gi
+                const int s = kb % GRAM_NS, gi = kb / GRAM_R, pos = kb - gi * GRAM_R, b = gi & 1;
                 if (!mbar_wait(full + s, (uint32_t)((kb / GRAM_NS) & 1), deadline)) { ok = false; break; }
-                if (kb >= 2 && !mbar_wait(tfree + b, (uint32_t)(((kb - 2) >> 1) & 1), deadline)) { ok = false; break; }
+                if (pos == 0 && gi >= 2 && !mbar_wait(tfree + b, (uint32_t)(((gi - 2) >> 1) & 1), deadline)) {
+                    ok = false;
+                    break;
+                }
                 fence_after_sync();
                 const uint32_t sb = smem_u32(base + s * GRAM_STAGE);
                 const uint32_t dre = tmem + 256u * (uint32_t)b, dim = dre + 128u;
@@ -175,14 +184,14 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) gram_tc_kernel(const __grid_c
 #pragma unroll
                 for (int u = 0; u < 6; ++u) {
                     const int p = PP[u], q = QQ[u];
-                    const uint32_t acc = u > 0 ? 1u : 0u;
+                    const uint32_t acc = (u > 0 || pos > 0) ? 1u : 0u;
                     mma_bf16(dre, slot(0, p), slot(2, q), id_pos, acc);     // X_I X_J^T
                     mma_bf16(dre, slot(1, p), slot(3, q), id_pos, 1u);      // + Y_I Y_J^T
                     mma_bf16(dim, slot(1, p), slot(2, q), id_pos, acc);     // Y_I X_J^T
                     mma_bf16(dim, slot(0, p), slot(3, q), id_neg, 1u);      // - X_I Y_J^T
                 }
                 mma_commit(sfree + s);
-                mma_commit(tready + b);
+                if (pos == GRAM_R - 1 || kb == nk - 1) mma_commit(tready + b);
                 // refill the stage of the previous block (its MMAs ran while this block's were queued)
                 if (kb >= 1 && kb - 1 + GRAM_NS < nk) {
                     const int sp = (kb - 1) % GRAM_NS;
@@ -203,10 +212,11 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) gram_tc_kernel(const __grid_c
         const uint32_t lrow = (uint32_t)(32 * (warp & 3)) << 16;
         const uint32_t c0 = 64u * (uint32_t)(warp >> 2);
         bool ok = true;
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb & 1;
+        const int ng = (nk + GRAM_R - 1) / GRAM_R;
+        for (int g = 0; g < ng; ++g) {
+            const int s = g & 1;
             bool ready = false;
-            while (!(ready = mbar_test(tready + s, (uint32_t)((kb >> 1) & 1)))) {
+            while (!(ready = mbar_test(tready + s, (uint32_t)((g >> 1) & 1)))) {
                 if (clock64() > deadline || *(volatile int *)abort_flag) break;
             }
             if (!__all_sync(0xffffffffu, ready)) { ok = false; break; }
