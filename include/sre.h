@@ -194,6 +194,11 @@ SRE_API sre_status sre_exact_batched(const void *const *psi_ptrs_host, const int
  * 2..26. */
 SRE_API sre_status sre_autotune(const void *psi_c64_dev, int N, void *stream, sre_opts *best);
 
+/* Drops the autotuner's choice for N (N = 0: for every N), so that plans go
+ * back to the planned defaults; rewrites SRE_TUNE_FILE when it is set. N in
+ * 0..32, else SRE_EINVAL. Host only. */
+SRE_API sre_status sre_autotune_clear(int N);
+
 /* Monte Carlo over X-mask families (N in 2..30).
  * mode SRE_MC_UNIFORM: the SM Sec. I estimator -- x = 0 always and n_x - 1
  *   draws of x uniform on {1..d-1}; S_hat = m_0 + (d-1)/(n_x-1) sum m_x;

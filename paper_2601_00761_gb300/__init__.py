@@ -21,7 +21,7 @@ __all__ = ["sre_version", "sre_last_error", "sre_default_opts", "sre_make_plan",
            "pauli_x_marginal", "stabilizer_nullity", "apply_clifford_tdoped_circuit",
            "sre_family_spectrum", "sre_family_spectrum_f64", "sre_philox_blocks", "sre_kernel_launches", "sre_device_allocations", "sre_tc_gemm_selftest",
            "sre_selftest_bounded_wait", "sre_selftest_queue_wait",
-           "sre_profile_passes", "sre_pass_timing", "sre_exact_noalloc", "sre_autotune", "SreError",
+           "sre_profile_passes", "sre_pass_timing", "sre_exact_noalloc", "sre_autotune", "sre_autotune_clear", "SreError",
            "SRE_FP32_SIMT", "SRE_BF16X2_TC", "SRE_BF16X3_TC", "SRE_MC_UNIFORM", "SRE_MC_MARGINAL",
            "lib_path", "load"]
 
@@ -127,6 +127,7 @@ def load():
         "sre_selftest_bounded_wait": ([_vp], st),
         "sre_selftest_queue_wait": ([_vp], st),
         "sre_autotune": ([_vp, ctypes.c_int, _vp, ctypes.POINTER(Opts)], st),
+        "sre_autotune_clear": ([ctypes.c_int], st),
         "sre_exact_noalloc": ([_vp, ctypes.c_int, ctypes.POINTER(Opts), _vp, ctypes.POINTER(Result)], st),
         "sre_pass_timing": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                              ctypes.POINTER(ctypes.c_double)], st),
@@ -246,6 +247,11 @@ def sre_autotune(psi) -> dict:
     o = Opts()
     _check(load().sre_autotune(p, N, _stream(), ctypes.byref(o)))
     return {"radix_log2": o.radix_log2, "tile_log2": o.tile_log2, "x_batch": o.x_batch}
+
+
+def sre_autotune_clear(N: int = 0) -> None:
+    """Drop the autotuner's choice for N (0: every N); plans return to the defaults."""
+    _check(load().sre_autotune_clear(N))
 
 
 def sre_exact_batched(psis, **kw) -> list:

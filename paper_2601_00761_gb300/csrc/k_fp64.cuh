@@ -1,4 +1,4 @@
-// k_fp64.cuh -- FP64 helpers for sums of FP32 data.
+// k_fp64.cuh -- FP64 helpers: exact widening of FP32 data, compensated sums.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -17,5 +17,18 @@ __device__ __forceinline__ double f2d(float f) {
     if (e - 1u >= 254u) return (double)f;
     return __hiloint2double((int)(sg | ((e + 896u) << 20) | (m >> 3)), (int)(m << 29));
 }
+
+// Neumaier's compensated summation (Neumaier 1974, the Kahan-Babuska form):
+// s is the running sum and c gathers the rounding error of every addition,
+// so s + c carries a sum of many terms to about one rounding of the result.
+struct NeuSum {
+    double s = 0.0, c = 0.0;
+    __device__ __forceinline__ void add(double x) {
+        const double t = s + x;
+        c += (fabs(s) >= fabs(x)) ? ((s - t) + x) : ((x - t) + s);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return s + c; }
+};
 
 }  // namespace sre

@@ -102,6 +102,8 @@ __global__ void __launch_bounds__(256) fam_reduce_kernel(const TilePartial *tp, 
     unsigned long long x = xs ? xs[fam_base + f] : (unsigned long long)(fam_base + f);
     x &= (1ULL << N) - 1ULL;
     const int j = x ? 63 - __clzll((long long)x) : n;
+    // plain FP64: a family's tile partials are FP32 sums (relative error about
+    // 1e-7), far above this sum's rounding
     double m0 = 0, m1 = 0, m2 = 0, m3 = 0, c = 0;
     for (int t = lane; t < tiles; t += 32) {
         const TilePartial &p = tp[(size_t)f * tiles + t];
@@ -146,16 +148,18 @@ __global__ void __launch_bounds__(256) exact_partial_kernel(const FamMoments *fm
     __shared__ double red[8];
     const long long per = (n_fam + gridDim.x - 1) / gridDim.x;
     const long long lo = (long long)blockIdx.x * per, hi = lo + per < n_fam ? lo + per : n_fam;
-    double a0 = 0, a1 = 0, a2 = 0, a3 = 0, c = 0, q = 0;
+    NeuSum s0, s1, s2, s3, sq;
+    double c = 0;
     for (long long f = lo + threadIdx.x; f < hi; f += 256) {
         const FamMoments &m = fm[f];
-        a0 += m.m[0]; a1 += m.m[1]; a2 += m.m[2]; a3 += m.m[3]; c += (double)m.cand;
-        if (f > 0) q += m.m[1] * m.m[1];
+        s0.add(m.m[0]); s1.add(m.m[1]); s2.add(m.m[2]); s3.add(m.m[3]); c += (double)m.cand;
+        if (f > 0) sq.add(m.m[1] * m.m[1]);
         if (m.cand && flag_list) {
             unsigned long long pos = atomicAdd(n_flag, 1ULL);
             flag_list[pos] = (unsigned long long)f;
         }
     }
+    double a0 = s0.value(), a1 = s1.value(), a2 = s2.value(), a3 = s3.value(), q = sq.value();
     a0 = block_sum<256>(a0, red);
     a1 = block_sum<256>(a1, red);
     a2 = block_sum<256>(a2, red);
@@ -172,9 +176,9 @@ __global__ void __launch_bounds__(256) exact_final_kernel(const double *partial,
                                                           double *out) {
     __shared__ double red[8];
     for (int a = 0; a < 6; ++a) {
-        double s = 0.0;
-        for (int i = threadIdx.x; i < n_part; i += 256) s += partial[6 * i + a];
-        s = block_sum<256>(s, red);
+        NeuSum ns;
+        for (int i = threadIdx.x; i < n_part; i += 256) ns.add(partial[6 * i + a]);
+        const double s = block_sum<256>(ns.value(), red);
         if (threadIdx.x == 0) out[a] = s;
     }
     if (threadIdx.x == 0) out[6] = fm0[0].m[1];
@@ -507,19 +511,19 @@ __global__ void __launch_bounds__(256) mc_totals_kernel(const double *y, long lo
                                                         const FamMoments *fm, double *out) {
     __shared__ double red[8];
     for (int a = 0; a < 6; ++a) {
-        double s = 0.0, q = 0.0;
+        NeuSum ns, nq;
         for (long long i = first + threadIdx.x; i < n_x; i += 256) {
             const double v = y[6 * i + a];
-            s += v;
-            q += v * v;
+            ns.add(v);
+            nq.add(v * v);
         }
-        s = block_sum<256>(s, red);
-        q = block_sum<256>(q, red);
+        const double s = block_sum<256>(ns.value(), red);
+        const double q = block_sum<256>(nq.value(), red);
         if (threadIdx.x == 0) { out[a] = s; out[6 + a] = q; out[12 + a] = y[a]; }
     }
-    double p = 0.0;
-    for (long long i = threadIdx.x; i < n_x; i += 256) p += fm[i].m[0];
-    p = block_sum<256>(p, red);
+    NeuSum np_;
+    for (long long i = threadIdx.x; i < n_x; i += 256) np_.add(fm[i].m[0]);
+    const double p = block_sum<256>(np_.value(), red);
     if (threadIdx.x == 0) out[18] = p;
 }
 
@@ -579,16 +583,18 @@ __global__ void __launch_bounds__(256) state_totals_kernel(const FamMoments *fm,
     const int st = s0 + blockIdx.x;
     const long long nf = 1LL << N;
     const long long f0 = ((long long)st << N) - fm_first_family;
-    double a0 = 0, a1 = 0, a2 = 0, a3 = 0, c = 0, q = 0;
+    NeuSum n0, n1, n2, n3, nq;
+    double c = 0;
     for (long long f = threadIdx.x; f < nf; f += 256) {
         const FamMoments &m = fm[f0 + f];
-        a0 += m.m[0]; a1 += m.m[1]; a2 += m.m[2]; a3 += m.m[3]; c += (double)m.cand;
-        if (f > 0) q += m.m[1] * m.m[1];
+        n0.add(m.m[0]); n1.add(m.m[1]); n2.add(m.m[2]); n3.add(m.m[3]); c += (double)m.cand;
+        if (f > 0) nq.add(m.m[1] * m.m[1]);
         if (m.cand) {
             const unsigned long long pos = atomicAdd(n_flag, 1ULL);
             flags[pos] = ((unsigned long long)st << N) | (unsigned long long)f;
         }
     }
+    double a0 = n0.value(), a1 = n1.value(), a2 = n2.value(), a3 = n3.value(), q = nq.value();
     a0 = block_sum<256>(a0, red);
     a1 = block_sum<256>(a1, red);
     a2 = block_sum<256>(a2, red);

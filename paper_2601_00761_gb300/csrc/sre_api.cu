@@ -587,12 +587,17 @@ double fluctuation_ratio(double sum_all, double sq_nz, double m_x0, double d) {
 }
 
 // T: the TOT_N totals of an exact sweep (k_misc.cuh)
+// pi_P = c_P^2 / (d P) with P = sum_P c_P^2 / d the measured Parseval sum (1
+// in exact arithmetic for the normalised state): normalising by it cancels
+// the common scale error of the FP32 (or split-BF16) spectrum, which Eq.
+// SRE-def would otherwise carry N-fold into M_1 and twofold into M_2.
 void finalize_exact(const double *T, int N, sre_result *r) {
     const double d = std::ldexp(1.0, N);
-    const double H = N * (T[0] / d) - T[3] / d;
+    const double P = T[0] / d;
+    const double H = N + std::log2(P) - T[3] / (d * P);
     r->S[0] = H;
-    r->S[1] = T[1] / (d * d);
-    r->S[2] = T[2] / (d * d * d);
+    r->S[1] = T[1] / (d * d * P * P);
+    r->S[2] = T[2] / (d * d * d * P * P * P);
     r->M[0] = H - N;
     r->M[1] = -std::log2(r->S[1]) - N;
     r->M[2] = -0.5 * std::log2(r->S[2]) - N;
@@ -1609,6 +1614,16 @@ sre_status sre_autotune(const void *psi, int N, void *stream, sre_opts *best) {
     CS(check_psi(psi, N, 2, 26));
     if (!best) return fail(SRE_EINVAL, "best is NULL");
     return autotune_impl(psi, N, (cudaStream_t)stream, best);
+}
+
+sre_status sre_autotune_clear(int N) {
+    if (N < 0 || N > 32) return fail(SRE_EINVAL, "N=%d outside 0..32", N);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    for (int n = 1; n <= 32; ++n)
+        if (N == 0 || n == N) g_tune[n] = TuneEntry();
+    tune_save_locked();
+    return SRE_OK;
 }
 
 sre_status sre_mc(const void *psi, int N, int mode, long long n_x, int z_per_x, unsigned long long seed,

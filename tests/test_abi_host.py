@@ -62,6 +62,13 @@ def test_plans(L, N, passes, bits):
     assert top == 0
 
 
+def test_autotune_clear_arguments(L):
+    assert L.sre_autotune_clear(33) == sre.SRE_EINVAL
+    assert L.sre_autotune_clear(-1) == sre.SRE_EINVAL
+    assert L.sre_autotune_clear(0) == sre.SRE_OK
+    assert L.sre_autotune_clear(18) == sre.SRE_OK
+
+
 def test_plan_options(L):
     p = sre.sre_make_plan(24, radix_log2=11, tile_log2=6)
     assert p["pass_bits"] == [6, 6, 11]

@@ -144,3 +144,6 @@ def test_autotune_keeps_results(sre):
     assert np.max(np.abs(np.array(after["M"]) - np.array(before["M"]))) < TOL_M
     c = sre.sre_family_spectrum(psi, 12345).cpu().numpy()
     assert np.max(np.abs(c - oracle.family_spectrum(inputs.haar_state(18, 9), 12345))) < 1e-6
+    # clearing the choice restores the planned default, and later tests see it
+    sre.sre_autotune_clear(18)
+    assert sre.sre_make_plan(18)["pass_bits"][-1] == 13
