@@ -62,6 +62,24 @@ def test_plans(L, N, passes, bits):
     assert top == 0
 
 
+def test_batched_argument_errors_do_not_touch_the_gpu(L):
+    r = (sre.Result * 2)()
+    o = sre.sre_default_opts()
+    ptrs = (ctypes.c_void_p * 2)(0x1000, 0x2000)
+    ns = (ctypes.c_int * 2)(10, 12)
+    assert L.sre_exact_batched(ptrs, ns, 0, ctypes.byref(o), None, 0, None, r) == sre.SRE_OK      # empty batch
+    assert L.sre_exact_batched(ptrs, ns, -1, ctypes.byref(o), None, 0, None, r) == sre.SRE_EINVAL
+    assert L.sre_exact_batched(None, ns, 2, ctypes.byref(o), None, 0, None, r) == sre.SRE_EINVAL
+    assert L.sre_exact_batched(ptrs, ns, 2, ctypes.byref(o), None, 0, None, None) == sre.SRE_EINVAL
+    big = (ctypes.c_int * 2)(10, 21)                                                          # N in 1..20
+    assert L.sre_exact_batched(ptrs, big, 2, ctypes.byref(o), None, 0, None, r) == sre.SRE_EINVAL
+    odd = (ctypes.c_void_p * 2)(0x1000, 0x2004)                                               # 8-byte aligned psi
+    assert L.sre_exact_batched(odd, ns, 2, ctypes.byref(o), None, 0, None, r) == sre.SRE_EINVAL
+    assert L.sre_exact_batched(ptrs, ns, 2, ctypes.byref(o), _fake_ptr(0x3000), 1 << 20, None, r) == sre.SRE_ENOTSUP
+    q = sre.Opts(0, 1e-6, 0, 0, 0, 3)
+    assert L.sre_exact_batched(ptrs, ns, 2, ctypes.byref(q), None, 0, None, r) == sre.SRE_EINVAL
+
+
 def test_autotune_clear_arguments(L):
     assert L.sre_autotune_clear(33) == sre.SRE_EINVAL
     assert L.sre_autotune_clear(-1) == sre.SRE_EINVAL
