@@ -120,6 +120,15 @@ def test_batched_single_pass_states_share_one_launch(sre):
     assert c1 == c2
 
 
+def test_batched_queue_mode_large_states(sre):
+    """The dependency queue at its largest states: the strided items of N = 18,
+    19 and 20 (4, 5 and 6 rows; 256 to 1024 families per 1 GB ring slot),
+    among single-pass states, against per-state sweeps."""
+    states = [torch.from_numpy(inputs.haar_state(N, 900 + N)).cuda() for N in (20, 9, 19, 13, 18)]
+    res = sre.sre_exact_batched(states, batch_queue=1)
+    _check(sre, states, res)
+
+
 def test_batched_small_vs_oracle(sre):
     specs = inputs.workload_batched_specs(count=6, seed0=77, n_min=3, n_max=8)
     states, refs = [], []
