@@ -335,7 +335,7 @@ def run_cuda(a):
     shares = [timing["ms_sum"][p] for p in range(npass)]
     dom = int(np.argmax(shares))
     avg_ms = timing["ms_sum"][dom] / max(1, timing["launches"][dom])
-    survey_bytes = timing["bytes_per_launch"][dom]          # 8 B psi per string per family (+ 4 B out)
+    algo_bytes = timing["bytes_per_launch"][dom]            # 8 B psi per string per family (+ 4 B out)
     fam_launch = max(1, round(n_x / max(1, timing["launches"][dom] / a.steps)))
     min_bytes = dram_min_bytes(N, dom, npass, fam_launch)
     step_bytes = sum(timing["bytes_per_launch"][p] * timing["launches"][p] for p in range(npass)) / a.steps
@@ -353,8 +353,8 @@ def run_cuda(a):
                                   "DRAM-minimal bytes per launch (no ncu capture for the current kernel sources)",
                 "dram_min_bytes_per_launch": min_bytes,
                 "frac_dram_min": min_bytes / (avg_ms / 1e3) / 1e9 / hbm,
-                "survey_bytes_per_launch": survey_bytes,
-                "frac_algorithmic": survey_bytes / (avg_ms / 1e3) / 1e9 / hbm,
+                "algorithmic_bytes_per_launch": algo_bytes,
+                "frac_algorithmic": algo_bytes / (avg_ms / 1e3) / 1e9 / hbm,
                 "frac_algorithmic_note": "16 B per string counted with psi read from DRAM by every family; "
                                          "the families of a launch share psi in L2, so this exceeds 1",
                 "traffic_capture": tp[1].get("capture") if tp else None,
